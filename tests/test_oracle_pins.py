@@ -1,0 +1,339 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle function against something other than itself: a closed
+form, an invariant, a LAPACK definition, a planted answer or a published test vector.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import torch
+
+import oracle.chfsi_oracle as O
+from paper_1206_3768_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small_problem(n=96, nev=8, blk=14, name="c1", N=1, spectrum=None, seed_offset=0):
+    seq = inputs.planted_sequence(name, n=n, N=N, nev=nev, blk=blk, spectrum=spectrum,
+                                  seed_offset=seed_offset)
+    return seq
+
+
+def _np(t):
+    return t.numpy() if isinstance(t, torch.Tensor) else t
+
+
+# ---------------------------------------------------------------- generator (R12)
+def test_splitmix64_published_outputs():
+    want = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+            if l.strip() and not l.startswith("#")]
+    got = O.splitmix64(0, np.arange(4, dtype=np.uint64))
+    assert [int(x) for x in got] == want
+
+
+def test_uniform_and_gaussian_moments():
+    u = O.uniform01(123, np.arange(200000, dtype=np.uint64))
+    assert 0.0 <= u.min() and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 5e-3 and abs(u.var() - 1.0 / 12.0) < 2e-3
+    z = O.cold_start_block(400, 50, 7)
+    assert z.shape == (400, 50)
+    assert abs(np.mean(np.abs(z) ** 2) - 1.0) < 0.02
+    assert abs(np.mean(z)) < 0.02
+
+
+# ---------------------------------------------------------------- definition (Eq. 1)
+def test_definition_matches_planted_spectrum():
+    seq = _small_problem()
+    p = seq.problems[0]
+    A, B = _np(p.A), _np(p.B)
+    w, X = O.definition_eigenpairs(np.tril(A), np.tril(B), 8)
+    scale = np.max(np.abs(p.lam))
+    assert np.max(np.abs(w - p.lam[:8])) <= 1e-12 * scale
+    assert np.allclose(X.conj().T @ B @ X, np.eye(8), atol=1e-12)
+    # Planted vectors agree up to phase (isolated eigenvalues of the draw).
+    Xp = _np(p.X)[:, :8]
+    ov = np.abs(np.sum(X.conj() * (B @ Xp), axis=0))
+    assert np.all(np.abs(ov - 1.0) < 1e-8)
+
+
+def test_hermitian_from_lower_uses_lower_triangle_only():
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((5, 5)) + 1j * rng.standard_normal((5, 5))
+    H = O.hermitian_from_lower(M)
+    assert np.allclose(H, H.conj().T)
+    assert np.allclose(np.tril(H, -1), np.tril(M, -1))
+    M2 = M.copy()
+    M2[np.triu_indices(5, 1)] = 99.0
+    assert np.allclose(O.hermitian_from_lower(M2), H)
+
+
+# ---------------------------------------------------------------- reduction (Section 4.1)
+def test_reduction_invariants_and_planted_spectrum():
+    seq = _small_problem(n=80)
+    p = seq.problems[0]
+    A, B = _np(p.A), _np(p.B)
+    L = O.cholesky_lower(np.tril(B))
+    assert np.allclose(np.triu(L, 1), 0.0)
+    assert np.linalg.norm(L @ L.conj().T - B) <= 1e-14 * np.linalg.norm(B)
+    Hs = O.reduce_standard(np.tril(A), L)
+    assert np.linalg.norm(L @ Hs @ L.conj().T - A) <= 1e-13 * np.linalg.norm(A)
+    assert np.max(np.abs(np.linalg.eigvalsh(Hs) - p.lam)) <= 1e-12 * np.max(np.abs(p.lam))
+    # y = L^H x maps B-orthonormal x to orthonormal y and back.
+    X = _np(p.X)[:, :5]
+    Y = O.to_standard_vectors(L, X)
+    assert np.allclose(Y.conj().T @ Y, np.eye(5), atol=1e-12)
+    assert np.allclose(O.to_generalized_vectors(L, Y), X, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Chebyshev filter
+def _diag_case(n=60, seed=3):
+    rng = np.random.default_rng(seed)
+    lam = np.sort(rng.uniform(-2.0, 2.0, n))
+    Z = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Q, _ = np.linalg.qr(Z)
+    H = (Q * lam) @ Q.conj().T
+    return lam, Q, 0.5 * (H + H.conj().T)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 7, 10, 25, 40])
+def test_filter_on_eigenvectors_matches_closed_form(d):
+    lam, Q, H = _diag_case()
+    a0, a, b = lam[0], lam[12], lam[-1] + 0.05
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    X = Q[:, :20]
+    Y = O.chebyshev_filter(H, X, np.full(20, d), a0, a, b)
+    p = O.chebyshev_T(d, (lam[:20] - c) / e) / O.chebyshev_T(d, np.array([(a0 - c) / e]))[0]
+    ref = X * p[None, :]
+    assert np.max(np.abs(Y - ref)) <= 1e-12 * max(1.0, np.max(np.abs(p)))
+    # normalisation point: p(a0) = 1
+    assert abs(p[0] - 1.0) < 1e-12
+
+
+def test_filter_per_column_degrees():
+    lam, Q, H = _diag_case()
+    a0, a, b = lam[0], lam[15], lam[-1] + 0.1
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    degs = np.array([0, 1, 5, 9, 9, 3, 12, 2])
+    X = Q[:, :8] * (1.0 + 0.5j)
+    Y = O.chebyshev_filter(H, X, degs, a0, a, b)
+    t0 = (a0 - c) / e
+    for i, d in enumerate(degs):
+        p = 1.0 if d == 0 else (O.chebyshev_T(d, np.array([(lam[i] - c) / e]))[0]
+                                / O.chebyshev_T(d, np.array([t0]))[0])
+        assert np.max(np.abs(Y[:, i] - p * X[:, i])) <= 1e-12 * max(1, abs(p))
+
+
+def test_chebyshev_closed_form_trig_identity():
+    th = np.linspace(0.0, math.pi, 41)
+    for k in (0, 1, 2, 5, 13):
+        assert np.allclose(O.chebyshev_T(k, np.cos(th)), np.cos(k * th), atol=1e-13)
+    # three-term recurrence outside [-1, 1]
+    x = np.array([-3.0, -1.5, 1.2, 4.0])
+    T0, T1 = np.ones_like(x), x.copy()
+    for k in range(2, 12):
+        T0, T1 = T1, 2 * x * T1 - T0
+        assert np.allclose(O.chebyshev_T(k, x), T1, rtol=1e-12)
+
+
+def test_filter_mutation_is_caught(monkeypatch):
+    """A sign slip in the recurrence must fail the closed-form pin."""
+    lam, Q, H = _diag_case()
+    a0, a, b = lam[0], lam[12], lam[-1] + 0.05
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    real = O.filter_coefficients
+
+    def broken(*args):
+        return [(al, be, -ga) for (al, be, ga) in real(*args)]
+
+    monkeypatch.setattr(O, "filter_coefficients", broken)
+    Y = O.chebyshev_filter(H, Q[:, :5], np.full(5, 6), a0, a, b)
+    p = O.chebyshev_T(6, (lam[:5] - c) / e) / O.chebyshev_T(6, np.array([(a0 - c) / e]))[0]
+    assert np.max(np.abs(Y - Q[:, :5] * p)) > 1e-3
+
+
+# ---------------------------------------------------------------- Lanczos (R5)
+def test_lanczos_bound_is_safe_and_exact_at_full_dimension():
+    lam, Q, H = _diag_case(n=50)
+    v0 = O.lanczos_start_vector(50, 99)
+    up, tmin, a, bta = O.lanczos(H, v0, 10)
+    assert up >= lam[-1] - 1e-12
+    assert tmin >= lam[0] - 1e-12
+    up_full, tmin_full, a, bta = O.lanczos(H, v0, 50)
+    T = np.diag(a) + np.diag(bta[:-1], 1) + np.diag(bta[:-1], -1)
+    th = np.linalg.eigvalsh(T)
+    assert np.max(np.abs(th - lam)) < 1e-10
+    assert abs(tmin_full - lam[0]) < 1e-10
+
+
+# ---------------------------------------------------------------- re-orthonormalisation
+def test_orthonormalize_span_and_deflation():
+    rng = np.random.default_rng(5)
+    n, m, k = 70, 9, 4
+    YL, _ = np.linalg.qr(rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k)))
+    Y = rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))
+    Q = O.orthonormalize(Y, YL)
+    assert np.allclose(Q.conj().T @ Q, np.eye(m), atol=1e-13)
+    assert np.max(np.abs(YL.conj().T @ Q)) < 1e-13
+    # span(Q) = span((I - P_L) Y)
+    Z = Y - YL @ (YL.conj().T @ Y)
+    Pz = Z @ np.linalg.pinv(Z)
+    assert np.linalg.norm(Pz - Q @ Q.conj().T) < 1e-11
+
+
+# ---------------------------------------------------------------- Rayleigh-Ritz, residuals
+def test_rayleigh_ritz_on_invariant_subspace_is_exact():
+    lam, Q, H = _diag_case(n=40)
+    rng = np.random.default_rng(1)
+    U, _ = np.linalg.qr(rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6)))
+    S = Q[:, 3:9] @ U
+    theta, Y, W = O.rayleigh_ritz(H, S)
+    assert np.max(np.abs(theta - lam[3:9])) < 1e-13
+    r = O.residual_norms(W, Y, theta)
+    assert np.max(r) < 1e-13
+
+
+def test_rayleigh_ritz_interlacing():
+    lam, Q, H = _diag_case(n=40)
+    rng = np.random.default_rng(2)
+    S, _ = np.linalg.qr(rng.standard_normal((40, 7)) + 1j * rng.standard_normal((40, 7)))
+    theta, Y, W = O.rayleigh_ritz(H, S)
+    # Cauchy interlacing: lam_i <= theta_i <= lam_{n-m+i}
+    assert np.all(theta >= lam[:7] - 1e-13)
+    assert np.all(theta <= lam[-7:] + 1e-13)
+
+
+def test_residual_closed_form_two_level():
+    lam, Q, H = _diag_case(n=30)
+    d = 1e-3
+    y = (Q[:, 0] + d * Q[:, 5])[:, None]
+    theta = np.array([lam[0]])
+    r = O.residual_norms(H @ y, y, theta)
+    assert abs(r[0] - d * abs(lam[5] - lam[0]) / math.sqrt(1 + d * d)) < 1e-14
+
+
+# ---------------------------------------------------------------- locking (Algorithm 1)
+def test_lock_count_contiguous_prefix():
+    r = np.array([1e-12, 1e-13, 5e-9, 1e-14, 1e-14])
+    assert O.lock_count(r, 1e-10, 0, 10) == 2
+    assert O.lock_count(r, 1e-10, 9, 10) == 1          # only nev - converged allowed
+    assert O.lock_count(r, 1e-8, 0, 10) == 5
+    assert O.lock_count(np.array([1.0]), 1e-10, 0, 5) == 0
+
+
+# ---------------------------------------------------------------- degree rule (R8)
+def test_adaptive_degree_bounds_from_closed_form():
+    a, b = -0.5, 10.0
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    theta = np.array([-1.0, -0.9, -0.7, -0.55, 3.0, -0.95])
+    r = np.array([1e-3, 1e-5, 1e-2, 1e-4, 1e-1, 1e-12])
+    tau = 1e-10
+    d = O.adaptive_degrees(theta, r, a, b, tau, 4, 60, 5)
+    assert d[5] == 60  # past the wanted columns: largest wanted degree
+    assert d[4] == 60  # inside [a, b]: no damping, maximum degree
+    for i in range(4):
+        t = abs((theta[i] - c) / e)
+        if 4 < d[i] < 60:
+            # T_d(t) >= rho^d / 2 >= r/(2 tau) and T_{d-1}(t) <= rho^{d-1} < r/tau
+            assert O.chebyshev_T(int(d[i]), np.array([t]))[0] >= r[i] / (2 * tau)
+            assert O.chebyshev_T(int(d[i]) - 1, np.array([t]))[0] < r[i] / tau
+    d2 = O.adaptive_degrees(np.array([-1.0]), np.array([1e-12]), a, b, 1e-10, 8, 25, 1)
+    assert d2[0] == 8
+
+
+def test_filter_reduces_residual_as_the_degree_rule_predicts():
+    """Brute force on a planted spectrum: measured reduction vs 1/|T_d(t)| within 10x."""
+    lam, Q, H = _diag_case(n=80, seed=11)
+    a, b = lam[20], lam[-1] + 0.01
+    a0 = lam[0]
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    i = 2
+    rng = np.random.default_rng(4)
+    coef = np.zeros(80, dtype=np.complex128)
+    coef[i] = 1.0
+    coef[21:] = 1e-4 * (rng.standard_normal(59) + 1j * rng.standard_normal(59))
+    y = Q @ coef
+    d = 12
+    y2 = O.chebyshev_filter(H, y[:, None], [d], a0, a, b)[:, 0]
+
+    def res(v):
+        th = np.real(np.vdot(v, H @ v) / np.vdot(v, v))
+        return np.linalg.norm(H @ v - th * v) / np.linalg.norm(v)
+
+    measured = res(y2) / res(y)
+    predicted = 1.0 / abs(O.chebyshev_T(d, np.array([(lam[i] - c) / e]))[0])
+    assert predicted / 10 <= measured <= predicted * 10
+
+
+# ---------------------------------------------------------------- full method
+def _check_solution(p, lam, X, nev, tol=1e-10):
+    A, B = _np(p.A), _np(p.B)
+    a2 = np.linalg.norm(A, 2)
+    scale = max(np.max(np.abs(p.lam)), 1.0)
+    assert np.all(np.isfinite(lam))
+    assert np.max(np.abs(lam - p.lam[:nev]) / np.maximum(np.abs(p.lam[:nev]), scale)) <= tol
+    R = A @ X - (B @ X) * lam[None, :]
+    res = np.linalg.norm(R, axis=0) / (a2 * np.linalg.norm(X, axis=0))
+    assert res.max() <= tol
+    assert np.allclose(X.conj().T @ B @ X, np.eye(nev), atol=1e-10)
+
+
+def test_full_solve_small_c1_shape_fixed_degree():
+    seq = _small_problem(n=192, nev=10, blk=16, N=3)
+    As = [np.tril(_np(p.A)) for p in seq.problems]
+    Bs = [np.tril(_np(p.B)) for p in seq.problems]
+    out = O.chfsi_solve_sequence(As, Bs, 10, 16, 1e-10, deg=10)
+    for p, (lam, X, st) in zip(seq.problems, out):
+        _check_solution(p, lam, X, 10)
+        assert st.loops < 50
+        assert st.filtered_vectors >= 16
+
+
+def test_full_solve_adaptive_ill_conditioned_overlap():
+    seq = inputs.planted_sequence("c2", n=260, N=2, nev=10, blk=14)
+    As = [np.tril(_np(p.A)) for p in seq.problems]
+    Bs = [np.tril(_np(p.B)) for p in seq.problems]
+    assert np.linalg.cond(_np(seq.problems[0].B)) > 5e3
+    out = O.chfsi_solve_sequence(As, Bs, 10, 14, 1e-10, deg=0, deg_min=8, deg_max=25)
+    for p, (lam, X, st) in zip(seq.problems, out):
+        _check_solution(p, lam, X, 10)
+
+
+def test_clustered_wanted_eigenvalues_projector():
+    seq = _small_problem(n=160, nev=12, blk=20, spectrum="cluster_low")
+    p = seq.problems[0]
+    lam, X, state, st = O.chfsi_solve(np.tril(_np(p.A)), np.tril(_np(p.B)), 12, 20, deg=12)
+    _check_solution(p, lam, X, 12)
+    # The cluster of 8 values near -2 is resolved as a subspace (Davis-Kahan).
+    B = _np(p.B)
+    Xp = _np(p.X)[:, :12]
+    P1 = X @ X.conj().T @ B
+    P2 = Xp @ Xp.conj().T @ B
+    assert np.linalg.norm(P1 - P2) < 1e-6
+
+
+def test_warm_start_needs_fewer_matvecs_than_cold():
+    seq = _small_problem(n=256, nev=12, blk=20, N=4)
+    As = [np.tril(_np(p.A)) for p in seq.problems]
+    Bs = [np.tril(_np(p.B)) for p in seq.problems]
+    _, _, warm, _ = O.chfsi_solve(As[2], Bs[2], 12, 20, deg=10)
+    _, _, _, st_w = O.chfsi_solve(As[3], Bs[3], 12, 20, deg=10, warm=warm)
+    _, _, _, st_c = O.chfsi_solve(As[3], Bs[3], 12, 20, deg=10)
+    assert st_w.matvecs < st_c.matvecs
+    assert st_w.loops <= st_c.loops
+
+
+def test_table3_defaults_golden():
+    vals = {}
+    for l in open(os.path.join(GOLDEN, "table3_parameters.txt")):
+        if l.strip() and not l.startswith("#"):
+            k, v = l.split()
+            vals[k] = float(v)
+    import inspect
+    sig = inspect.signature(O.chfsi_solve)
+    assert sig.parameters["deg"].default == vals["degree"]
+    assert sig.parameters["tol"].default == vals["tol"]
+    assert sig.parameters["lanczos_k_warm"].default == vals["lanczos_iter_min"]

@@ -1,0 +1,183 @@
+/*
+ * chfsi.h -- C ABI of the GB300 (sm_103a) Chebyshev-filtered subspace iteration library.
+ *
+ * The library solves sequences of correlated generalized Hermitian eigenproblems
+ *     A^(l) x = lambda B^(l) x,   l = 1..N                              (Eq. 1, Section 1)
+ * for the nev lowest eigenpairs of each problem, with Chebyshev-filtered subspace
+ * iteration with locking (Algorithm 1, Section 3), after reduction to standard form
+ * B = L L^H, Hs = L^{-1} A L^{-H}, y = L^H x (Section 4.1), each problem warm-started
+ * from the Ritz vectors of the previous one (Section 4.1, stages 1-4).
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are interleaved complex128 (chfsi_z), matrices column-major with a
+ *     leading dimension ld >= rows.  Only the LOWER triangles of A and B are read.
+ *   - The caller owns every buffer it passes; the library never frees or keeps caller
+ *     memory.  The context owns its device workspace (allocated by chfsi_create).
+ *   - The solve entry points accept host or device pointers for A, B, V0, evals and
+ *     evecs (the kind is detected per pointer; host data is staged through the
+ *     context's workspace on the context's stream).  The step entry points take DEVICE
+ *     pointers only.
+ *   - Every function returns a status code (chfsi_status); on failure the message is
+ *     available from chfsi_last_error(ctx).  No entry point aborts the process.
+ *   - One context serves one host thread at a time; all work is queued on the
+ *     context's CUDA stream and the solve entry points return after it has finished.
+ */
+#ifndef CHFSI_H
+#define CHFSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } chfsi_z;
+typedef struct chfsi_ctx chfsi_ctx;
+
+typedef enum {
+  CHFSI_OK = 0,
+  CHFSI_EINVAL = 1,    /* bad sizes (blk < nev, blk > n, n > n_max, ...), NULL, NaN input */
+  CHFSI_ENOTPD = 2,    /* B (or a Gram matrix beyond repair) is not positive definite */
+  CHFSI_ENOCONV = 3,   /* max_loops reached: locked prefix returned, the rest NaN */
+  CHFSI_ECUDA = 4,     /* a CUDA runtime call failed */
+  CHFSI_ETIMEOUT = 5,  /* a bounded device-side wait expired (kernel returned early) */
+  CHFSI_ENOMEM = 6     /* workspace allocation failed */
+} chfsi_status;
+
+/* Solver options.  Defaults (chfsi_default_opts) follow Table 3 of the paper for ChFSI:
+ * polynomial degree 25, TOL 1e-10; lanczos-iter 10 (warm) / 40 (cold) within the
+ * table's range "10 : 3 x blk". */
+typedef struct {
+  int32_t deg_min;          /* adaptive degree range (deg == 0 in a solve call) */
+  int32_t deg_max;
+  int32_t max_loops;        /* filter loops per problem before CHFSI_ENOCONV (default 50) */
+  int32_t lanczos_k_warm;   /* Lanczos steps for the spectral upper bound, warm start */
+  int32_t lanczos_k_cold;   /* ... cold start */
+  int32_t reuse_factor;     /* 1: reuse L when B is bitwise equal to the previous B */
+  uint64_t seed;            /* SplitMix64 seed of the Lanczos start vector / cold block */
+  void* cuda_stream;        /* cudaStream_t to run on; NULL = a stream owned by the context */
+} chfsi_opts;
+
+/* Per-problem statistics (Table 4 of the paper reports loops and filtered vectors). */
+typedef struct {
+  int32_t loops;             /* filter loops (outer repeat of Algorithm 1) */
+  int32_t filtered_vectors;  /* sum over loops of the active block width */
+  int32_t converged;         /* locked pairs returned */
+  int32_t accept_rounds;     /* times the locking threshold was tightened */
+  int64_t matvecs;           /* column products Hs*y (filter + Rayleigh-Ritz + Lanczos) */
+  double max_resid;          /* max_i ||A x_i - lambda_i B x_i|| / (||A||_est ||x_i||) */
+  double lanczos_upper;      /* spectral upper bound b used by the filter */
+  double t_reduce_ms, t_lanczos_ms, t_filter_ms, t_qr_ms, t_rr_ms, t_resid_ms, t_total_ms;
+} chfsi_stats;
+
+/* ---------------------------------------------------------------- context */
+void chfsi_default_opts(chfsi_opts* opts);
+
+/* Create a context able to solve problems with n <= n_max and blk <= blk_max; allocates
+ * all device workspace (about 6 n_max^2 + 12 n_max blk_max complex entries).
+ * opts may be NULL (defaults).  Errors: EINVAL, ENOMEM, ECUDA. */
+int chfsi_create(chfsi_ctx** out, int64_t n_max, int32_t blk_max, const chfsi_opts* opts);
+void chfsi_destroy(chfsi_ctx* ctx);
+const char* chfsi_last_error(const chfsi_ctx* ctx);
+/* Drop the carried Ritz vectors and the cached factor of B: the next solve starts cold. */
+int chfsi_reset_warm_state(chfsi_ctx* ctx);
+
+/* ---------------------------------------------------------------- solves */
+/* Solve one problem of the sequence (Algorithm 1 with the reduction of Section 4.1).
+ *   A, B   n x n (lower triangles read), leading dimensions lda, ldb.
+ *   V0     optional n x blk start block (ld n) used when the context has no warm state;
+ *          NULL = SplitMix64 complex Gaussian block.  Ignored when warm state exists.
+ *   deg    > 0: fixed filter degree; 0: adaptive per-vector degree in [deg_min, deg_max].
+ *   tol    residual tolerance (paper: 1e-10).
+ *   evals  nev ascending eigenvalues (host or device, double).
+ *   evecs  n x nev B-orthonormal eigenvectors, ld n (host or device), may be NULL.
+ *   st     optional statistics (host).
+ * The Ritz vectors (all blk of them, in x-coordinates) and the bounds are kept in the
+ * context as the warm start of the next call.
+ * Errors: EINVAL, ENOTPD, ENOCONV (partial: evals of the locked prefix, rest NaN),
+ *         ECUDA, ETIMEOUT. */
+int chfsi_solve_next(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda,
+                     const chfsi_z* B, int64_t ldb, const chfsi_z* V0, int32_t nev,
+                     int32_t blk, int32_t deg, double tol, double* evals, chfsi_z* evecs,
+                     chfsi_stats* st);
+
+/* Solve N problems in order, problem l warm-started from problem l-1 (Section 4.1,
+ * stages 1-4).  A[l], B[l]: pointers to the l-th matrices (ld = ld).  V0 as above for
+ * the first problem.  evals: N x nev (row l at evals + l*nev).  evecs: N pointers to
+ * n x nev outputs, or NULL.  st: N entries or NULL.  Starts from the context's warm
+ * state if it has one (call chfsi_reset_warm_state first for a cold first problem). */
+int chfsi_solve_sequence(chfsi_ctx* ctx, int32_t N, int64_t n, const chfsi_z* const* A,
+                         const chfsi_z* const* B, int64_t ld, const chfsi_z* V0,
+                         int32_t nev, int32_t blk, int32_t deg, double tol, double* evals,
+                         chfsi_z* const* evecs, chfsi_stats* st);
+
+/* ---------------------------------------------------------------- steps (device pointers)
+ * Each step of the hot path is also exposed on its own, for testing and for callers that
+ * assemble their own loop.  All run on the context's stream and synchronise it before
+ * returning.  Workspace limits of the context apply (n <= n_max, m <= blk_max). */
+
+/* B = L L^H (Section 4.1).  L receives the lower factor, its strict upper part zeroed.
+ * Errors: ENOTPD (message names the failing pivot), EINVAL. */
+int chfsi_cholesky(chfsi_ctx* ctx, int64_t n, const chfsi_z* B, int64_t ldb, chfsi_z* L,
+                   int64_t ldl);
+
+/* Hs = L^{-1} A L^{-H}, exactly Hermitian in full storage (Section 4.1).  L lower. */
+int chfsi_reduce(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const chfsi_z* L,
+                 int64_t ldl, chfsi_z* Hs, int64_t ldh);
+
+/* k-step Lanczos with full re-orthogonalisation on the Hermitian H (full storage),
+ * starting from v0 (device, n) or, if v0 is NULL, from the SplitMix64 start vector of
+ * the context seed (Algorithm 1, first step).  upper = max eig(T_k) + |beta_k|,
+ * theta_min = min eig(T_k), theta_max = max eig(T_k) (host doubles). */
+int chfsi_lanczos(chfsi_ctx* ctx, int64_t n, const chfsi_z* H, int64_t ldh, int32_t k,
+                  const chfsi_z* v0, double* upper, double* theta_min, double* theta_max);
+
+/* Chebyshev filter in place on the n x m block Y (Algorithm 1, filtering step): column i
+ * becomes T_{d_i}((H - c)/e) y_i / T_{d_i}((a0 - c)/e), e = (b-a)/2, c = (b+a)/2, by the
+ * scaled three-term recurrence.  degrees: HOST array of m non-negative degrees. */
+int chfsi_filter(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,
+                 chfsi_z* Y, int64_t ldy, const int32_t* degrees, double a0, double a,
+                 double b);
+
+/* Re-orthonormalisation (Algorithm 1): Y <- orthonormal basis of (I - YL YL^H) Y, by two
+ * passes of classical Gram-Schmidt against the k locked columns YL (may be 0) and
+ * Cholesky QR repeated three times (shifted on breakdown).  In place, n x m. */
+int chfsi_orthonormalize(chfsi_ctx* ctx, int64_t n, int32_t m, chfsi_z* Y, int64_t ldy,
+                         int32_t k, const chfsi_z* YL, int64_t ldyl);
+
+/* Rayleigh-Ritz (Algorithm 1): G = Y^H H Y, G w = theta w (ascending), Y <- Y W,
+ * W_out <- H Y (the new Ritz vectors' products).  theta: device, m doubles. */
+int chfsi_rayleigh_ritz(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,
+                        chfsi_z* Y, int64_t ldy, chfsi_z* HY, int64_t ldhy, double* theta);
+
+/* Residual norms of the locking test (Algorithm 1): r_i = ||HY_i - theta_i Y_i|| / ||Y_i||.
+ * theta, r: device, m doubles. */
+int chfsi_residuals(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* HY, int64_t ldhy,
+                    const chfsi_z* Y, int64_t ldy, const double* theta, double* r);
+
+/* Closed-form per-vector degrees (not in the paper; the adaptive mode):
+ * d_i = clamp(ceil(ln(r_i/tau)/ln rho_i), dmin, dmax), rho_i = |t_i| + sqrt(t_i^2-1),
+ * t_i = (theta_i - c)/e; d_i = dmin when r_i <= tau, dmax when |t_i| <= 1; columns
+ * i >= n_wanted take the largest degree of the first n_wanted.  theta, r device;
+ * degrees: device, m int32. */
+int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* r, double a,
+                  double b, double tau, int32_t dmin, int32_t dmax, int32_t n_wanted,
+                  int32_t* degrees);
+
+/* Eigen-decomposition of the m x m Hermitian matrix G (full storage, device): ascending
+ * eigenvalues w (device) and orthonormal eigenvectors V (device, ld ldv), by cyclic
+ * parallel Jacobi.  G is not modified. */
+int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double* w,
+               chfsi_z* V, int64_t ldv);
+
+/* Complex FP64 GEMM used by every dense step, exposed for testing:
+ * C <- alpha op(A) op(B) + beta C, op = 'N' (as stored) or 'C' (conjugate transpose);
+ * C is M x N, op(A) M x K, op(B) K x N.  alpha, beta real. */
+int chfsi_zgemm(chfsi_ctx* ctx, char opa, char opb, int32_t M, int32_t N, int32_t K,
+                double alpha, const chfsi_z* A, int64_t lda, const chfsi_z* B, int64_t ldb,
+                double beta, chfsi_z* C, int64_t ldc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHFSI_H */

@@ -1,0 +1,336 @@
+"""Thin ctypes binding of the C ABI in include/chfsi.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Matrices are torch
+complex128 tensors in natural (row, column) indexing; they are handed to the library in
+column-major storage (``fortran`` makes a column-major copy only when needed).  Device
+tensors are passed as device pointers, CPU tensors as host pointers (the solve entry
+points accept both; the step entry points need CUDA tensors).
+
+The library is the in-tree ``_lib/libchfsi.so`` built by ``build.py``; if it is missing
+or cannot be loaded, every call raises: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char, c_char_p, c_double, c_int32, c_int64, c_uint64, c_void_p
+
+import torch
+
+from . import build as _build
+
+CHFSI_OK, CHFSI_EINVAL, CHFSI_ENOTPD, CHFSI_ENOCONV, CHFSI_ECUDA, CHFSI_ETIMEOUT, CHFSI_ENOMEM = range(7)
+_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOTPD", 3: "ENOCONV", 4: "ECUDA", 5: "ETIMEOUT", 6: "ENOMEM"}
+
+
+class ChfsiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"CHFSI_{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class chfsi_opts(ctypes.Structure):
+    _fields_ = [("deg_min", c_int32), ("deg_max", c_int32), ("max_loops", c_int32),
+                ("lanczos_k_warm", c_int32), ("lanczos_k_cold", c_int32),
+                ("reuse_factor", c_int32), ("seed", c_uint64), ("cuda_stream", c_void_p)]
+
+
+class chfsi_stats(ctypes.Structure):
+    _fields_ = [("loops", c_int32), ("filtered_vectors", c_int32), ("converged", c_int32),
+                ("accept_rounds", c_int32), ("matvecs", c_int64), ("max_resid", c_double),
+                ("lanczos_upper", c_double), ("t_reduce_ms", c_double), ("t_lanczos_ms", c_double),
+                ("t_filter_ms", c_double), ("t_qr_ms", c_double), ("t_rr_ms", c_double),
+                ("t_resid_ms", c_double), ("t_total_ms", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = c_void_p
+_SIGS = {
+    "chfsi_default_opts": (None, [POINTER(chfsi_opts)]),
+    "chfsi_create": (c_int32, [POINTER(c_void_p), c_int64, c_int32, POINTER(chfsi_opts)]),
+    "chfsi_destroy": (None, [_P]),
+    "chfsi_last_error": (c_char_p, [_P]),
+    "chfsi_reset_warm_state": (c_int32, [_P]),
+    "chfsi_solve_next": (c_int32, [_P, c_int64, _P, c_int64, _P, c_int64, _P, c_int32, c_int32,
+                                   c_int32, c_double, _P, _P, POINTER(chfsi_stats)]),
+    "chfsi_solve_sequence": (c_int32, [_P, c_int32, c_int64, _P, _P, c_int64, _P, c_int32,
+                                       c_int32, c_int32, c_double, _P, _P, POINTER(chfsi_stats)]),
+    "chfsi_cholesky": (c_int32, [_P, c_int64, _P, c_int64, _P, c_int64]),
+    "chfsi_reduce": (c_int32, [_P, c_int64, _P, c_int64, _P, c_int64, _P, c_int64]),
+    "chfsi_lanczos": (c_int32, [_P, c_int64, _P, c_int64, c_int32, _P, POINTER(c_double),
+                                POINTER(c_double), POINTER(c_double)]),
+    "chfsi_filter": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64, POINTER(c_int32),
+                               c_double, c_double, c_double]),
+    "chfsi_orthonormalize": (c_int32, [_P, c_int64, c_int32, _P, c_int64, c_int32, _P, c_int64]),
+    "chfsi_rayleigh_ritz": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64, _P, c_int64,
+                                      _P]),
+    "chfsi_residuals": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64, _P, _P]),
+    "chfsi_degrees": (c_int32, [_P, c_int32, _P, _P, c_double, c_double, c_double, c_int32,
+                                c_int32, c_int32, _P]),
+    "chfsi_heev": (c_int32, [_P, c_int32, _P, c_int64, _P, _P, c_int64]),
+    "chfsi_zgemm": (c_int32, [_P, c_char, c_char, c_int32, c_int32, c_int32, c_double, _P, c_int64,
+                              _P, c_int64, c_double, _P, c_int64]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libchfsi.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libchfsi.so not found at {path}; run paper_1206_3768_gb300.build")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------- helpers
+def fortran(t: torch.Tensor) -> torch.Tensor:
+    """Same matrix, column-major storage (no copy when it already is)."""
+    if t.dim() == 1:
+        return t.contiguous()
+    if t.stride(0) == 1 and t.stride(1) >= max(1, t.shape[0]):
+        return t
+    return t.mT.contiguous().mT
+
+
+def fortran_empty(rows: int, cols: int, device, dtype=torch.complex128) -> torch.Tensor:
+    return torch.empty((cols, rows), dtype=dtype, device=device).mT
+
+
+def _ld(t: torch.Tensor) -> int:
+    return max(1, t.stride(1)) if t.dim() == 2 else max(1, t.shape[0])
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check(ctx, rc: int):
+    if rc != CHFSI_OK:
+        msg = load().chfsi_last_error(ctx).decode() if ctx else ""
+        raise ChfsiError(rc, msg)
+
+
+def default_opts(**kw) -> chfsi_opts:
+    o = chfsi_opts()
+    load().chfsi_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------------- context
+def chfsi_create(n_max: int, blk_max: int, opts: chfsi_opts | None = None, stream=None, **kw):
+    lib = load()
+    o = opts if opts is not None else default_opts(**kw)
+    if stream is not None:
+        o.cuda_stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    ctx = ctypes.c_void_p()
+    rc = lib.chfsi_create(ctypes.byref(ctx), int(n_max), int(blk_max), ctypes.byref(o))
+    if rc != CHFSI_OK:
+        raise ChfsiError(rc, "chfsi_create failed")
+    return ctx
+
+
+def chfsi_destroy(ctx):
+    load().chfsi_destroy(ctx)
+
+
+def chfsi_last_error(ctx) -> str:
+    return load().chfsi_last_error(ctx).decode()
+
+
+def chfsi_reset_warm_state(ctx):
+    _check(ctx, load().chfsi_reset_warm_state(ctx))
+
+
+def chfsi_solve_next(ctx, A: torch.Tensor, B: torch.Tensor, nev: int, blk: int, deg: int,
+                     tol: float = 1e-10, V0: torch.Tensor | None = None, out_device=None,
+                     want_vectors: bool = True):
+    """One problem.  Returns (evals [nev] float64, evecs [n, nev] complex128, stats dict)."""
+    n = A.shape[0]
+    dev = A.device if out_device is None else torch.device(out_device)
+    Af, Bf = fortran(A), fortran(B)
+    V0f = fortran(V0) if V0 is not None else None
+    if V0f is not None and _ld(V0f) != n:
+        V0f = V0f.mT.contiguous().mT  # ld must equal n
+    evals = torch.empty(nev, dtype=torch.float64, device=dev)
+    evecs = fortran_empty(n, nev, dev) if want_vectors else None
+    st = chfsi_stats()
+    rc = load().chfsi_solve_next(ctx, n, _ptr(Af), _ld(Af), _ptr(Bf), _ld(Bf), _ptr(V0f), nev, blk,
+                                 deg, tol, _ptr(evals), _ptr(evecs), ctypes.byref(st))
+    if rc not in (CHFSI_OK, CHFSI_ENOCONV):
+        _check(ctx, rc)
+    out = (evals, evecs, st.as_dict())
+    if rc == CHFSI_ENOCONV:
+        err = ChfsiError(rc, chfsi_last_error(ctx))
+        err.partial = out
+        raise err
+    return out
+
+
+def chfsi_solve_sequence(ctx, As, Bs, nev: int, blk: int, deg: int, tol: float = 1e-10,
+                         V0: torch.Tensor | None = None, want_vectors: bool = True):
+    """N problems in order with warm starts.  As, Bs: lists of n x n tensors (same device,
+    column-major with a common leading dimension).  Returns (evals [N, nev], list of evecs,
+    list of stats dicts)."""
+    N = len(As)
+    n = As[0].shape[0]
+    Af = [fortran(a) for a in As]
+    Bf = [fortran(b) for b in Bs]
+    ld = _ld(Af[0])
+    if any(_ld(x) != ld for x in Af + Bf):
+        raise ValueError("all matrices must share one leading dimension")
+    dev = As[0].device
+    evals = torch.empty((N, nev), dtype=torch.float64, device="cpu")
+    evecs = [fortran_empty(n, nev, dev) for _ in range(N)] if want_vectors else None
+    Ap = (c_void_p * N)(*[a.data_ptr() for a in Af])
+    Bp = (c_void_p * N)(*[b.data_ptr() for b in Bf])
+    Ep = (c_void_p * N)(*[e.data_ptr() for e in evecs]) if evecs else None
+    V0f = fortran(V0) if V0 is not None else None
+    if V0f is not None and _ld(V0f) != n:
+        V0f = V0f.mT.contiguous().mT
+    sts = (chfsi_stats * N)()
+    rc = load().chfsi_solve_sequence(ctx, N, n, Ap, Bp, ld, _ptr(V0f), nev, blk, deg, tol,
+                                     _ptr(evals), Ep, sts)
+    _check(ctx, rc)
+    return evals, evecs, [s.as_dict() for s in sts]
+
+
+# ---------------------------------------------------------------------- steps
+def chfsi_cholesky(ctx, B: torch.Tensor) -> torch.Tensor:
+    n = B.shape[0]
+    Bf = fortran(B)
+    L = fortran_empty(n, n, B.device)
+    _check(ctx, load().chfsi_cholesky(ctx, n, _ptr(Bf), _ld(Bf), _ptr(L), _ld(L)))
+    return L
+
+
+def chfsi_reduce(ctx, A: torch.Tensor, L: torch.Tensor) -> torch.Tensor:
+    n = A.shape[0]
+    Af, Lf = fortran(A), fortran(L)
+    H = fortran_empty(n, n, A.device)
+    _check(ctx, load().chfsi_reduce(ctx, n, _ptr(Af), _ld(Af), _ptr(Lf), _ld(Lf), _ptr(H), _ld(H)))
+    return H
+
+
+def chfsi_lanczos(ctx, H: torch.Tensor, k: int, v0: torch.Tensor | None = None):
+    n = H.shape[0]
+    Hf = fortran(H)
+    up, tmin, tmax = c_double(), c_double(), c_double()
+    v = v0.contiguous() if v0 is not None else None
+    _check(ctx, load().chfsi_lanczos(ctx, n, _ptr(Hf), _ld(Hf), k, _ptr(v), ctypes.byref(up),
+                                     ctypes.byref(tmin), ctypes.byref(tmax)))
+    return up.value, tmin.value, tmax.value
+
+
+def chfsi_filter(ctx, H: torch.Tensor, Y: torch.Tensor, degrees, a0: float, a: float, b: float):
+    n, m = Y.shape
+    Hf = fortran(H)
+    Yf = fortran(Y).clone()
+    degs = (c_int32 * m)(*[int(d) for d in degrees])
+    _check(ctx, load().chfsi_filter(ctx, n, m, _ptr(Hf), _ld(Hf), _ptr(Yf), _ld(Yf), degs, a0, a, b))
+    return Yf
+
+
+def chfsi_orthonormalize(ctx, Y: torch.Tensor, YL: torch.Tensor | None = None):
+    n, m = Y.shape
+    Yf = fortran(Y.clone())
+    k = 0 if YL is None else YL.shape[1]
+    YLf = fortran(YL) if YL is not None else None
+    _check(ctx, load().chfsi_orthonormalize(ctx, n, m, _ptr(Yf), _ld(Yf), k, _ptr(YLf),
+                                            _ld(YLf) if YLf is not None else n))
+    return Yf
+
+
+def chfsi_rayleigh_ritz(ctx, H: torch.Tensor, Y: torch.Tensor):
+    n, m = Y.shape
+    Hf = fortran(H)
+    Yf = fortran(Y.clone())
+    HY = fortran_empty(n, m, Y.device)
+    theta = torch.empty(m, dtype=torch.float64, device=Y.device)
+    _check(ctx, load().chfsi_rayleigh_ritz(ctx, n, m, _ptr(Hf), _ld(Hf), _ptr(Yf), _ld(Yf),
+                                           _ptr(HY), _ld(HY), _ptr(theta)))
+    return theta, Yf, HY
+
+
+def chfsi_residuals(ctx, HY: torch.Tensor, Y: torch.Tensor, theta: torch.Tensor):
+    n, m = Y.shape
+    HYf, Yf = fortran(HY), fortran(Y)
+    r = torch.empty(m, dtype=torch.float64, device=Y.device)
+    _check(ctx, load().chfsi_residuals(ctx, n, m, _ptr(HYf), _ld(HYf), _ptr(Yf), _ld(Yf),
+                                       _ptr(theta.contiguous()), _ptr(r)))
+    return r
+
+
+def chfsi_degrees(ctx, theta: torch.Tensor, r: torch.Tensor, a: float, b: float, tau: float,
+                  dmin: int, dmax: int, n_wanted: int):
+    m = theta.shape[0]
+    d = torch.empty(m, dtype=torch.int32, device=theta.device)
+    _check(ctx, load().chfsi_degrees(ctx, m, _ptr(theta.contiguous()), _ptr(r.contiguous()), a, b,
+                                     tau, dmin, dmax, n_wanted, _ptr(d)))
+    return d
+
+
+def chfsi_heev(ctx, G: torch.Tensor):
+    m = G.shape[0]
+    Gf = fortran(G)
+    w = torch.empty(m, dtype=torch.float64, device=G.device)
+    V = fortran_empty(m, m, G.device)
+    _check(ctx, load().chfsi_heev(ctx, m, _ptr(Gf), _ld(Gf), _ptr(w), _ptr(V), _ld(V)))
+    return w, V
+
+
+def chfsi_zgemm(ctx, opa: str, opb: str, alpha: float, A: torch.Tensor, B: torch.Tensor,
+                beta: float = 0.0, C: torch.Tensor | None = None):
+    Af, Bf = fortran(A), fortran(B)
+    M = A.shape[0] if opa == "N" else A.shape[1]
+    K = A.shape[1] if opa == "N" else A.shape[0]
+    N = B.shape[1] if opb == "N" else B.shape[0]
+    if C is None:
+        C = fortran_empty(M, N, A.device)
+        C.zero_()
+    else:
+        C = fortran(C.clone())
+    _check(ctx, load().chfsi_zgemm(ctx, opa.encode(), opb.encode(), M, N, K, alpha, _ptr(Af),
+                                   _ld(Af), _ptr(Bf), _ld(Bf), beta, _ptr(C), _ld(C)))
+    return C
+
+
+class Solver:
+    """Context manager owning one chfsi context."""
+
+    def __init__(self, n_max: int, blk_max: int, stream=None, **opts):
+        self.ctx = chfsi_create(n_max, blk_max, stream=stream, **opts)
+
+    def close(self):
+        if self.ctx:
+            chfsi_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,999 @@
+// ChFSI engine and C ABI: context and workspace, reduction to standard form, Lanczos
+// bound, Chebyshev filter, re-orthonormalisation, Rayleigh-Ritz, locking, and the
+// sequence driver with warm starts (Algorithm 1 of Di Napoli & Berljafa, arXiv:1206.3768,
+// with the reduction of Section 4.1).
+//
+// All arithmetic runs in the kernels of gemm.cu, small.cu and vec.cu on the context's
+// stream.  The host only sequences launches and reads back, once per filter loop, the
+// locked count and the Ritz values and residuals of the active block (a few KB), from
+// which it sets the filter bounds and the per-step active widths.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+struct chfsi_ctx {
+  Workspace ws;
+  chfsi_opts opts;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  // warm state: Ritz vectors (x-coordinates) in ws.Xw and their values
+  bool has_warm = false;
+  int64_t warm_n = 0;
+  int warm_blk = 0;
+  std::vector<double> warm_lam;
+  // factor of B kept in ws.Lf / ws.Linv for ws.Bf
+  bool has_factor = false;
+  int64_t factor_n = 0;
+  // phase timing
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Mark { int phase; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+};
+
+namespace {
+
+enum Phase { PH_REDUCE = 0, PH_LANCZOS, PH_FILTER, PH_QR, PH_RR, PH_RESID, PH_N };
+
+int set_err(chfsi_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(expr)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return set_err(ctx, CHFSI_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));   \
+  } while (0)
+
+#define CKS(expr)                \
+  do {                           \
+    int s_ = (expr);             \
+    if (s_ != CHFSI_OK) return s_; \
+  } while (0)
+
+inline zd* Z(const chfsi_z* p) { return reinterpret_cast<zd*>(const_cast<chfsi_z*>(p)); }
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaEvent_t next_event(chfsi_ctx* ctx) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    ctx->ev_pool.push_back(e);
+  }
+  return ctx->ev_pool[ctx->ev_used++];
+}
+
+struct PhaseScope {
+  chfsi_ctx* ctx;
+  int phase;
+  cudaEvent_t a;
+  PhaseScope(chfsi_ctx* c, int ph) : ctx(c), phase(ph) {
+    a = next_event(c);
+    cudaEventRecord(a, c->stream);
+  }
+  ~PhaseScope() {
+    cudaEvent_t b = next_event(ctx);
+    cudaEventRecord(b, ctx->stream);
+    ctx->marks.push_back({phase, a, b});
+  }
+};
+
+void collect_times(chfsi_ctx* ctx, double* t) {
+  for (int i = 0; i < PH_N; ++i) t[i] = 0.0;
+  for (auto& m : ctx->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) t[m.phase] += ms;
+  }
+  ctx->marks.clear();
+  ctx->ev_used = 0;
+}
+
+template <class T>
+int read_back(chfsi_ctx* ctx, T* host, const T* dev, size_t count) {
+  if (count == 0) return CHFSI_OK;
+  CK(cudaMemcpyAsync(host, dev, count * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHFSI_OK;
+}
+
+int reset_status(chfsi_ctx* ctx) {
+  const int init[2] = {0, 0x7fffffff};
+  CK(cudaMemcpyAsync(ctx->ws.status, init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHFSI_OK;
+}
+
+// Translate the device status word into a return code (and clear it).
+int check_status(chfsi_ctx* ctx, const char* where) {
+  int st[2];
+  CKS(read_back(ctx, st, ctx->ws.status, 2));
+  if (st[0] == DEV_OK) return CHFSI_OK;
+  const int info = st[1];
+  CKS(reset_status(ctx));
+  if (st[0] & DEV_TIMEOUT)
+    return set_err(ctx, CHFSI_ETIMEOUT, "%s: a bounded device wait expired", where);
+  if (st[0] & DEV_NAN) return set_err(ctx, CHFSI_EINVAL, "%s: non-finite input", where);
+  if (st[0] & DEV_NOTPD)
+    return set_err(ctx, CHFSI_ENOTPD, "%s: matrix not positive definite (pivot %d)", where, info);
+  if (st[0] & DEV_NOCONV)
+    return set_err(ctx, CHFSI_ENOCONV, "%s: Jacobi eigensolver reached its sweep limit", where);
+  return set_err(ctx, CHFSI_ECUDA, "%s: device status %d", where, st[0]);
+}
+
+int gemm(chfsi_ctx* ctx, const GemmDesc& g) {
+  CK(zgemm_run(g, ctx->ws, ctx->stream));
+  return CHFSI_OK;
+}
+
+// C(MxN) = alpha op(A) op(B) [+ beta Cin]
+GemmDesc gd(int M, int N, int K, const zd* A, int64_t lda, int opA, const zd* B, int64_t ldb,
+            int opB, zd* C, int64_t ldc, double alpha = 1.0) {
+  GemmDesc g;
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.lda = lda; g.opA = opA;
+  g.B = B; g.ldb = ldb; g.opB = opB;
+  g.C = C; g.ldc = ldc;
+  g.alpha = alpha;
+  return g;
+}
+
+constexpr int NB = 128;  // panel width of the blocked factorisations
+
+// In-place blocked right-looking Cholesky on the lower triangle of L (n x n).
+int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n) {
+  Workspace& ws = ctx->ws;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    zd* L11 = L + k0 + (int64_t)k0 * ld;
+    CK(small_cholesky(L11, ld, kb, 0, 0, 0.0, nullptr, nullptr, ws.status, ws.status + 1, k0,
+                      ctx->stream));
+    const int r = n - k0 - kb;
+    if (r <= 0) break;
+    // L21 = A21 L11^{-H}
+    CK(trinv_lower(L11, ld, ws.Rt, ws.blk_max, kb, ctx->stream));
+    zd* A21 = L + (k0 + kb) + (int64_t)k0 * ld;
+    GemmDesc g = gd(r, kb, kb, A21, ld, OPN, ws.Rt, ws.blk_max, OPC, ws.Z, r);
+    g.triB = 1;
+    CKS(gemm(ctx, g));
+    CK(cudaMemcpy2DAsync(A21, ld * sizeof(zd), ws.Z, r * sizeof(zd), r * sizeof(zd), kb,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    // A22 -= L21 L21^H (lower)
+    zd* A22 = L + (k0 + kb) + (int64_t)(k0 + kb) * ld;
+    GemmDesc h = gd(r, r, kb, A21, ld, OPN, A21, ld, OPC, A22, ld, -1.0);
+    h.beta = 1.0; h.Cin = A22; h.ldcin = ld; h.lowerC = 1;
+    CKS(gemm(ctx, h));
+  }
+  CK(zero_upper(L, ld, n, ctx->stream));
+  return CHFSI_OK;
+}
+
+// X = L^{-1} (n x n, lower) by block rows: X_II = inv(L_II),
+// X[I, 0:I] = -X_II (L[I, 0:I] X[0:I, 0:I]).
+int blocked_trinv(chfsi_ctx* ctx, const zd* L, int64_t ld, zd* X, int64_t ldx, int n) {
+  Workspace& ws = ctx->ws;
+  CK(cudaMemset2DAsync(X, ldx * sizeof(zd), 0, n * sizeof(zd), n, ctx->stream));
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int kb = std::min(NB, n - k0);
+    CK(trinv_lower(L + k0 + (int64_t)k0 * ld, ld, X + k0 + (int64_t)k0 * ldx, ldx, kb, ctx->stream));
+    if (k0 == 0) continue;
+    // Zt = L[I, 0:k0] X[0:k0, 0:k0]  (kb x k0), X lower => op(B)(k, j) = 0 for k < j
+    GemmDesc g = gd(kb, k0, k0, L + k0, ld, OPN, X, ldx, OPN, ws.Z, kb);
+    g.triB = 2;
+    CKS(gemm(ctx, g));
+    // X[I, 0:k0] = -X_II Zt, X_II lower
+    GemmDesc h = gd(kb, k0, kb, X + k0 + (int64_t)k0 * ldx, ldx, OPN, ws.Z, kb, OPN, X + k0, ldx, -1.0);
+    h.triA = 1;
+    CKS(gemm(ctx, h));
+  }
+  return CHFSI_OK;
+}
+
+// Hs = Linv Af Linv^H (lower computed, mirrored)
+int reduce_to_standard(chfsi_ctx* ctx, const zd* Af, int64_t lda, const zd* Linv, int64_t ldl,
+                       zd* Hs, int64_t ldh, int n) {
+  Workspace& ws = ctx->ws;
+  GemmDesc g = gd(n, n, n, Linv, ldl, OPN, Af, lda, OPN, ws.T, ws.n_max);
+  g.triA = 1;
+  CKS(gemm(ctx, g));
+  GemmDesc h = gd(n, n, n, ws.T, ws.n_max, OPN, Linv, ldl, OPC, Hs, ldh);
+  h.triB = 1;
+  h.lowerC = 1;
+  CKS(gemm(ctx, h));
+  CK(mirror_lower(Hs, ldh, n, ctx->stream));
+  return CHFSI_OK;
+}
+
+// k-step Lanczos with full re-orthogonalisation (two classical Gram-Schmidt passes).
+// v0: device start vector or nullptr (SplitMix64 with `seed`).  out3 (device):
+// [theta_min, theta_max, theta_max + |beta_k|].
+int lanczos_run(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int k, const zd* v0,
+                uint64_t seed, double* out3) {
+  Workspace& ws = ctx->ws;
+  k = std::min(k, n);
+  k = std::min(k, ws.lanczos_kmax);
+  if (k <= 0) return set_err(ctx, CHFSI_EINVAL, "lanczos: k must be positive");
+  const int64_t ldv = ws.n_max;
+  zd* V = ws.lV;
+  if (v0) CK(cudaMemcpyAsync(ws.lw, v0, n * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream));
+  else CK(splitmix_start_vector(ws.lw, n, seed, ctx->stream));
+  double* nrm = ws.scal + 8;
+  CK(vec_norm(ws.lw, n, nrm, ctx->stream));
+  CK(vec_scale_into(ws.lw, n, nrm, V, ctx->stream));
+  for (int j = 0; j < k; ++j) {
+    CK(hemv_rows(H, ldh, V + (int64_t)j * ldv, ws.lw, n, ctx->stream));
+    CK(block_dots(V, ldv, j, ws.lw, n, ws.lc, ctx->stream));
+    CK(block_update(V, ldv, j, ws.lc, ws.lw, n, ctx->stream));
+    CK(block_dots(V, ldv, j, ws.lw, n, ws.lc + (ws.lanczos_kmax + 1), ctx->stream));
+    CK(block_update(V, ldv, j, ws.lc + (ws.lanczos_kmax + 1), ws.lw, n, ctx->stream));
+    CK(vec_norm(ws.lw, n, nrm, ctx->stream));
+    CK(lanczos_record(ws.lc, j, nrm, ws.lal, ws.lbe, ctx->stream));
+    if (j + 1 < k) CK(vec_scale_into(ws.lw, n, nrm, V + (int64_t)(j + 1) * ldv, ctx->stream));
+  }
+  CK(tridiag_extremes(ws.lal, ws.lbe, k, out3, ctx->stream));
+  return CHFSI_OK;
+}
+
+// Chebyshev filter on the first m columns of *Ya (ld n_max) with per-column degrees.
+// degs_sorted: host, descending; perm_dev: device permutation (column r of the permuted
+// block is column perm[r] of the input) or nullptr when all degrees are equal.  The result
+// (in permuted order) is left in *Ya.
+int filter_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya, zd** Yb,
+                 zd** Yf, const std::vector<int>& degs_sorted, const int* perm_dev, double a0,
+                 double a, double b, int64_t* matvecs) {
+  Workspace& ws = ctx->ws;
+  const int64_t ld = ws.n_max;
+  if (m <= 0 || degs_sorted.empty()) return CHFSI_OK;
+  const int dmax = degs_sorted[0];
+  if (dmax <= 0) return CHFSI_OK;
+  if (perm_dev) {
+    CK(gather_cols(*Ya, ld, *Yb, ld, n, m, perm_dev, ctx->stream));
+    std::swap(*Ya, *Yb);
+  }
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double s1 = e / (a0 - c);
+  double s = s1;
+  zd* buf[2] = {*Ya, *Yf};
+  int mk = m;
+  for (int k = 1; k <= dmax; ++k) {
+    while (mk > 0 && degs_sorted[mk - 1] < k) --mk;
+    if (mk <= 0) break;
+    double al, be, ga;
+    if (k == 1) {
+      al = s1 / e; be = -al * c; ga = 0.0;
+    } else {
+      const double sn = 1.0 / (2.0 / s1 - s);
+      al = 2.0 * sn / e; be = -al * c; ga = -s * sn;
+      s = sn;
+    }
+    zd* cur = buf[(k - 1) & 1];
+    zd* out = buf[k & 1];
+    GemmDesc g = gd(n, mk, n, H, ldh, OPN, cur, ld, OPN, out, ld, al);
+    g.beta = be; g.Cin = cur; g.ldcin = ld;
+    if (k >= 2) { g.gamma = ga; g.D = out; g.ldd = ld; }
+    CKS(gemm(ctx, g));
+    if (matvecs) *matvecs += mk;
+  }
+  // columns with odd degree ended in buf[1]
+  std::vector<int> odd(m);
+  int nodd = 0;
+  for (int j = 0; j < m; ++j) { odd[j] = degs_sorted[j] & 1; nodd += odd[j]; }
+  if (nodd == m) {
+    std::swap(*Ya, *Yf);
+  } else if (nodd > 0) {
+    CK(cudaMemcpyAsync(ws.flag, odd.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(select_cols(*Yf, ld, *Ya, ld, n, m, ws.flag, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // odd[] lives on the host stack
+  }
+  return CHFSI_OK;
+}
+
+// CGS2 against YL (k columns) then Cholesky QR three times (shifted on breakdown).
+int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const zd* YL, int64_t ldyl,
+                         int k) {
+  Workspace& ws = ctx->ws;
+  const int64_t ld = ws.n_max;
+  const int64_t ldm = ws.blk_max;
+  if (m <= 0) return CHFSI_OK;
+  if (k > 0) {
+    for (int pass = 0; pass < 2; ++pass) {
+      CKS(gemm(ctx, gd(k, m, n, YL, ldyl, OPC, *Ya, ld, OPN, ws.G, ldm)));
+      GemmDesc g = gd(n, m, k, YL, ldyl, OPN, ws.G, ldm, OPN, *Ya, ld, -1.0);
+      g.beta = 1.0; g.Cin = *Ya; g.ldcin = ld;
+      CKS(gemm(ctx, g));
+    }
+  }
+  const double u = 1.1102230246251565e-16;
+  const double shift_base = 11.0 * ((double)n * m + (double)m * (m + 1)) * u;
+  for (int pass = 0; pass < 3; ++pass) {
+    GemmDesc g = gd(m, m, n, *Ya, ld, OPC, *Ya, ld, OPN, ws.G, ldm);
+    g.lowerC = 1;
+    CKS(gemm(ctx, g));
+    CK(small_cholesky(ws.G, ldm, m, 1, 1, shift_base, ws.dscale, ws.jac, ws.status, ws.status + 1, 0,
+                      ctx->stream));
+    CK(trinv_lower(ws.G, ldm, ws.Rt, ldm, m, ctx->stream));
+    CK(cholqr_T(ws.Rt, ldm, m, ws.dscale, ws.V, ldm, ctx->stream));
+    GemmDesc h = gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld);
+    h.triB = 1;
+    CKS(gemm(ctx, h));
+    std::swap(*Ya, *Yb);
+  }
+  return CHFSI_OK;
+}
+
+// Rayleigh-Ritz on the m columns of *Ya: theta (device), *Ya <- Ritz vectors, *W <- H *Ya.
+int rayleigh_ritz_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya, zd** Yb,
+                        zd** W, zd** Zb, double* theta) {
+  Workspace& ws = ctx->ws;
+  const int64_t ld = ws.n_max;
+  const int64_t ldm = ws.blk_max;
+  CKS(gemm(ctx, gd(n, m, n, H, ldh, OPN, *Ya, ld, OPN, *W, ld)));
+  GemmDesc g = gd(m, m, n, *Ya, ld, OPC, *W, ld, OPN, ws.G, ldm);
+  g.lowerC = 1;
+  CKS(gemm(ctx, g));
+  CK(mirror_lower(ws.G, ldm, m, ctx->stream));
+  CK(jacobi_heev(ws.G, ldm, m, theta, ws.V, ldm, ws.jac, ws.barrier, ws.status, ctx->stream));
+  CKS(gemm(ctx, gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld)));
+  CKS(gemm(ctx, gd(n, m, m, *W, ld, OPN, ws.V, ldm, OPN, *Zb, ld)));
+  std::swap(*Ya, *Yb);
+  std::swap(*W, *Zb);
+  return CHFSI_OK;
+}
+
+int validate_sizes(chfsi_ctx* ctx, int64_t n, int32_t nev, int32_t blk) {
+  if (!ctx) return CHFSI_EINVAL;
+  if (n <= 0 || n > ctx->ws.n_max)
+    return set_err(ctx, CHFSI_EINVAL, "n=%lld outside (0, n_max=%lld]", (long long)n,
+                   (long long)ctx->ws.n_max);
+  if (nev <= 0 || blk < nev || blk > n || blk > ctx->ws.blk_max)
+    return set_err(ctx, CHFSI_EINVAL, "need 0 < nev <= blk <= min(n, blk_max): nev=%d blk=%d",
+                   nev, blk);
+  return CHFSI_OK;
+}
+
+// Stage an n x cols matrix (host or device, leading dimension ld) into a device buffer
+// (ld_dst) or return the device pointer itself when no copy is needed.
+int stage_in(chfsi_ctx* ctx, const chfsi_z* src, int64_t ld, int n, int cols, zd* staging,
+             int64_t ld_dst, const zd** out) {
+  if (is_device_ptr(src)) {
+    *out = Z(src);
+    return CHFSI_OK;
+  }
+  CK(cudaMemcpy2DAsync(staging, ld_dst * sizeof(zd), src, ld * sizeof(zd), n * sizeof(zd), cols,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  *out = staging;
+  return CHFSI_OK;
+}
+
+struct SolveArgs {
+  int n, nev, blk, deg;
+  double tol;
+  const chfsi_z *A, *B, *V0;
+  int64_t lda, ldb;
+  double* evals;
+  chfsi_z* evecs;
+  chfsi_stats* st;
+};
+
+int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
+  Workspace& ws = ctx->ws;
+  const int n = S.n, nev = S.nev, blk = S.blk;
+  const int64_t ld = ws.n_max, ldm = ws.blk_max;
+  chfsi_stats st{};
+  double tph[PH_N];
+  const chfsi_opts& o = ctx->opts;
+  const bool adaptive = S.deg <= 0;
+  if (adaptive && (o.deg_min < 1 || o.deg_max < o.deg_min))
+    return set_err(ctx, CHFSI_EINVAL, "bad adaptive degree range [%d, %d]", o.deg_min, o.deg_max);
+  if (!(S.tol > 0.0)) return set_err(ctx, CHFSI_EINVAL, "tol must be positive");
+  CKS(reset_status(ctx));
+  cudaEvent_t t_start = next_event(ctx), t_end = next_event(ctx);
+  CK(cudaEventRecord(t_start, ctx->stream));
+
+  // ---------------------------------------------------------------- a1, a2: reduction
+  {
+    PhaseScope ps(ctx, PH_REDUCE);
+    const zd* Bsrc = nullptr;
+    CKS(stage_in(ctx, S.B, S.ldb, n, n, ws.Hs, ld, &Bsrc));
+    bool refactor = true;
+    if (o.reuse_factor && ctx->has_factor && ctx->factor_n == n) {
+      CK(cudaMemsetAsync(ws.flag, 0, sizeof(int), ctx->stream));
+      CK(compare_equal(Bsrc, Bsrc == ws.Hs ? ld : S.ldb, ws.Bf, ld, n, n, ws.flag, ctx->stream));
+      int diff = 1;
+      CKS(read_back(ctx, &diff, ws.flag, 1));
+      refactor = diff != 0;
+    }
+    if (refactor) {
+      ctx->has_factor = false;
+      CK(herm_from_lower(Bsrc, Bsrc == ws.Hs ? ld : S.ldb, ws.Bf, ld, n, ws.status, ctx->stream));
+      CK(cudaMemcpy2DAsync(ws.Lf, ld * sizeof(zd), ws.Bf, ld * sizeof(zd), n * sizeof(zd), n,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+      CKS(blocked_cholesky(ctx, ws.Lf, ld, n));
+      CKS(check_status(ctx, "Cholesky of B"));
+      CKS(blocked_trinv(ctx, ws.Lf, ld, ws.Linv, ld, n));
+      ctx->has_factor = true;
+      ctx->factor_n = n;
+    }
+    const zd* Asrc = nullptr;
+    CKS(stage_in(ctx, S.A, S.lda, n, n, ws.Hs, ld, &Asrc));
+    CK(herm_from_lower(Asrc, Asrc == ws.Hs ? ld : S.lda, ws.Af, ld, n, ws.status, ctx->stream));
+    CKS(reduce_to_standard(ctx, ws.Af, ld, ws.Linv, ld, ws.Hs, ld, n));
+  }
+  CKS(check_status(ctx, "input"));
+
+  // ---------------------------------------------------------------- a3: Lanczos bounds
+  const bool warm = ctx->has_warm && ctx->warm_n == n && ctx->warm_blk == blk;
+  double lz[3], an[3];
+  {
+    PhaseScope ps(ctx, PH_LANCZOS);
+    const int k = warm ? o.lanczos_k_warm : o.lanczos_k_cold;
+    CKS(lanczos_run(ctx, ws.Hs, ld, n, k, nullptr, o.seed, ws.scal));
+    CKS(lanczos_run(ctx, ws.Af, ld, n, 20, nullptr, o.seed ^ 0x5A5A5A5Aull, ws.scal + 3));
+    st.matvecs += std::min(k, n);
+  }
+  CKS(read_back(ctx, lz, ws.scal, 3));
+  CKS(read_back(ctx, an, ws.scal + 3, 3));
+  const double b_up = lz[2];
+  const double a_norm = std::max(std::fabs(an[0]), std::fabs(an[1]));
+  CK(cudaMemcpyAsync(ws.scal + 6, &a_norm, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  st.lanczos_upper = b_up;
+
+  // ---------------------------------------------------------------- start block
+  zd *Ya = ws.Y0, *Yb = ws.Y1, *Yf = ws.F, *W = ws.W, *Zb = ws.Z;
+  if (warm) {
+    GemmDesc g = gd(n, blk, n, ws.Lf, ld, OPC, ws.Xw, ld, OPN, Ya, ld);
+    g.triA = 2;
+    CKS(gemm(ctx, g));
+  } else if (S.V0) {
+    const zd* v0 = nullptr;
+    CKS(stage_in(ctx, S.V0, n, n, blk, Yb, ld, &v0));
+    CK(cudaMemcpy2DAsync(Ya, ld * sizeof(zd), v0, (v0 == Yb ? ld : n) * sizeof(zd), n * sizeof(zd),
+                         blk, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    CK(splitmix_gaussian_block(Ya, ld, n, blk, o.seed + 1, ctx->stream));
+  }
+
+  std::vector<double> th(blk), rr(blk), lamL;
+  std::vector<double> rL;
+  double a0, a;
+  double* theta = ws.theta;
+  double* theta_alt = ws.theta2;
+  double* resid = ws.resid;
+  double* resid_alt = ws.resid2;
+  bool have_r = false;
+  if (!warm || adaptive) {
+    {
+      PhaseScope ps(ctx, PH_QR);
+      CKS(orthonormalize_block(ctx, n, blk, &Ya, &Yb, nullptr, 0, 0));
+    }
+    {
+      PhaseScope ps(ctx, PH_RR);
+      CKS(rayleigh_ritz_block(ctx, ws.Hs, ld, n, blk, &Ya, &Yb, &W, &Zb, theta));
+    }
+    {
+      PhaseScope ps(ctx, PH_RESID);
+      CK(column_residuals(W, ld, Ya, ld, theta, n, blk, resid, ctx->stream));
+    }
+    st.matvecs += blk;
+    CKS(read_back(ctx, th.data(), theta, blk));
+    CKS(read_back(ctx, rr.data(), resid, blk));
+    CKS(check_status(ctx, "initial Rayleigh-Ritz"));
+    have_r = true;
+    a0 = th[0];
+    a = warm ? th[blk - 1] : a0 + (b_up - a0) * (double)blk / (double)n;
+  } else {
+    th = ctx->warm_lam;
+    a0 = th[0];
+    a = th[blk - 1];
+  }
+  double tau = 0.25 * S.tol * std::max(std::fabs(a0), std::fabs(b_up));
+
+  int conv = 0;
+  int status = CHFSI_OK;
+  std::vector<int> degs;
+  double max_gres = NAN;
+  for (int accept = 0; accept < 4; ++accept) {
+    while (conv < nev && st.loops < o.max_loops) {
+      const int m = blk - conv;
+      // ---- a8: degrees
+      const int* perm_dev = nullptr;
+      degs.assign(m, S.deg);
+      if (adaptive) {
+        if (!have_r) return set_err(ctx, CHFSI_ECUDA, "internal: residuals missing");
+        CK(degrees_kernel_run(theta, resid, m, a, b_up, tau, o.deg_min, o.deg_max, nev - conv,
+                              ws.deg, ws.perm, ws.degs, ctx->stream));
+        CKS(read_back(ctx, degs.data(), ws.degs, m));
+        perm_dev = ws.perm;
+      }
+      // ---- a4: filter
+      {
+        PhaseScope ps(ctx, PH_FILTER);
+        CKS(filter_block(ctx, ws.Hs, ld, n, m, &Ya, &Yb, &Yf, degs, perm_dev, a0, a, b_up,
+                         &st.matvecs));
+      }
+      st.filtered_vectors += m;
+      // ---- a5: deflation + Cholesky QR
+      {
+        PhaseScope ps(ctx, PH_QR);
+        CKS(orthonormalize_block(ctx, n, m, &Ya, &Yb, ws.YL, ld, conv));
+      }
+      // ---- a6: Rayleigh-Ritz
+      {
+        PhaseScope ps(ctx, PH_RR);
+        CKS(rayleigh_ritz_block(ctx, ws.Hs, ld, n, m, &Ya, &Yb, &W, &Zb, theta));
+      }
+      st.matvecs += m;
+      // ---- a7: residuals and locking
+      {
+        PhaseScope ps(ctx, PH_RESID);
+        CK(column_residuals(W, ld, Ya, ld, theta, n, m, resid, ctx->stream));
+        CK(lock_scan(resid, m, tau, nev - conv, ws.ilist, ctx->stream));
+      }
+      int nlock = 0;
+      CKS(read_back(ctx, &nlock, ws.ilist, 1));
+      CKS(read_back(ctx, th.data(), theta, m));
+      CKS(read_back(ctx, rr.data(), resid, m));
+      CKS(check_status(ctx, "filter loop"));
+      have_r = true;
+      st.loops++;
+      if (nlock > 0) {
+        CK(copy_cols(Ya, ld, ws.YL + (int64_t)conv * ld, ld, n, nlock, ctx->stream));
+        CK(cudaMemcpyAsync(ws.lamL + conv, theta, nlock * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(ws.residL + conv, resid, nlock * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        lamL.insert(lamL.end(), th.begin(), th.begin() + nlock);
+        rL.insert(rL.end(), rr.begin(), rr.begin() + nlock);
+        const int rem = m - nlock;
+        CK(copy_cols(Ya + (int64_t)nlock * ld, ld, Yb, ld, n, rem, ctx->stream));
+        std::swap(Ya, Yb);
+        CK(cudaMemcpyAsync(theta_alt, theta + nlock, rem * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        CK(cudaMemcpyAsync(resid_alt, resid + nlock, rem * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        std::swap(theta, theta_alt);
+        std::swap(resid, resid_alt);
+        th.erase(th.begin(), th.begin() + nlock);
+        rr.erase(rr.begin(), rr.begin() + nlock);
+        conv += nlock;
+      }
+      th.resize(blk - conv);
+      rr.resize(blk - conv);
+      a0 = th[0];
+      a = th[blk - conv - 1];
+    }
+    if (conv < nev) {
+      status = set_err(ctx, CHFSI_ENOCONV, "%d of %d pairs converged after %d loops", conv, nev,
+                       st.loops);
+      break;
+    }
+    // ---- a9: back-transform and acceptance on the generalized residual
+    {
+      PhaseScope ps(ctx, PH_RESID);
+      GemmDesc g1 = gd(n, conv, n, ws.Linv, ld, OPC, ws.YL, ld, OPN, ws.Xw, ld);
+      g1.triA = 2;
+      CKS(gemm(ctx, g1));
+      CKS(gemm(ctx, gd(n, nev, n, ws.Af, ld, OPN, ws.Xw, ld, OPN, W, ld)));
+      CKS(gemm(ctx, gd(n, nev, n, ws.Bf, ld, OPN, ws.Xw, ld, OPN, Zb, ld)));
+      CK(generalized_residuals(W, ld, Zb, ld, ws.Xw, ld, ws.lamL, n, nev, ws.scal + 6, ws.gres,
+                               ctx->stream));
+    }
+    std::vector<double> gr(nev);
+    CKS(read_back(ctx, gr.data(), ws.gres, nev));
+    max_gres = *std::max_element(gr.begin(), gr.end());
+    if (max_gres <= S.tol || accept == 3) break;
+    // Tighten the locking threshold and iterate again on all blk columns.
+    st.accept_rounds++;
+    tau /= 10.0;
+    CK(copy_cols(ws.YL, ld, Yb, ld, n, conv, ctx->stream));
+    CK(copy_cols(Ya, ld, Yb + (int64_t)conv * ld, ld, n, blk - conv, ctx->stream));
+    std::swap(Ya, Yb);
+    std::vector<double> th2(lamL);
+    th2.insert(th2.end(), th.begin(), th.end());
+    std::vector<double> r2(rL);
+    r2.insert(r2.end(), rr.begin(), rr.end());
+    th = th2;
+    rr = r2;
+    CK(cudaMemcpyAsync(theta, th.data(), blk * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(resid, rr.data(), blk * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    lamL.clear();
+    rL.clear();
+    conv = 0;
+    a0 = th[0];
+    a = th[blk - 1];
+  }
+
+  // ---- outputs and warm state: X = L^{-H} [YL, Y_active]
+  {
+    GemmDesc g1 = gd(n, conv, n, ws.Linv, ld, OPC, ws.YL, ld, OPN, ws.Xw, ld);
+    g1.triA = 2;
+    CKS(gemm(ctx, g1));
+    GemmDesc g2 = gd(n, blk - conv, n, ws.Linv, ld, OPC, Ya, ld, OPN, ws.Xw + (int64_t)conv * ld, ld);
+    g2.triA = 2;
+    CKS(gemm(ctx, g2));
+  }
+  std::vector<double> lam_out(nev, NAN);
+  for (int i = 0; i < std::min(conv, nev); ++i) lam_out[i] = lamL[i];
+  if (S.evals) {
+    if (is_device_ptr(S.evals))
+      CK(cudaMemcpyAsync(S.evals, lam_out.data(), nev * sizeof(double), cudaMemcpyHostToDevice,
+                         ctx->stream));
+    else
+      std::memcpy(S.evals, lam_out.data(), nev * sizeof(double));
+  }
+  if (S.evecs) {
+    const cudaMemcpyKind kind =
+        is_device_ptr(S.evecs) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpy2DAsync(S.evecs, n * sizeof(zd), ws.Xw, ld * sizeof(zd), n * sizeof(zd), nev, kind,
+                         ctx->stream));
+  }
+  ctx->warm_lam = lamL;
+  ctx->warm_lam.insert(ctx->warm_lam.end(), th.begin(), th.end());
+  ctx->warm_lam.resize(blk);
+  ctx->has_warm = (conv == nev);
+  ctx->warm_n = n;
+  ctx->warm_blk = blk;
+  CK(cudaEventRecord(t_end, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  float tot = 0.f;
+  cudaEventElapsedTime(&tot, t_start, t_end);
+  collect_times(ctx, tph);
+  st.converged = conv;
+  st.max_resid = max_gres;
+  st.t_reduce_ms = tph[PH_REDUCE];
+  st.t_lanczos_ms = tph[PH_LANCZOS];
+  st.t_filter_ms = tph[PH_FILTER];
+  st.t_qr_ms = tph[PH_QR];
+  st.t_rr_ms = tph[PH_RR];
+  st.t_resid_ms = tph[PH_RESID];
+  st.t_total_ms = tot;
+  if (S.st) *S.st = st;
+  return status;
+}
+
+void release_stream(chfsi_ctx* ctx) {
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  ctx->stream = nullptr;
+}
+
+}  // namespace
+
+// ====================================================================== workspace
+cudaError_t workspace_alloc(Workspace& ws, int64_t n_max, int blk_max, int lanczos_kmax) {
+  ws.n_max = n_max;
+  ws.blk_max = std::max(blk_max, NB);
+  ws.lanczos_kmax = lanczos_kmax;
+  const int64_t nn = n_max * n_max;
+  const int64_t nb = n_max * (int64_t)std::max(blk_max, NB);
+  const int64_t mm = (int64_t)ws.blk_max * ws.blk_max;
+  const int64_t mp = (int64_t)(ws.blk_max + 1);
+  cudaError_t e;
+#define AL(ptr, count)                                                      \
+  do {                                                                      \
+    e = cudaMalloc((void**)&(ptr), sizeof(*(ptr)) * (size_t)(count));       \
+    if (e != cudaSuccess) return e;                                         \
+  } while (0)
+  AL(ws.Af, nn); AL(ws.Bf, nn); AL(ws.Lf, nn); AL(ws.Linv, nn); AL(ws.Hs, nn); AL(ws.T, nn);
+  AL(ws.Y0, nb); AL(ws.Y1, nb); AL(ws.F, nb); AL(ws.W, nb); AL(ws.YL, nb); AL(ws.Xw, nb); AL(ws.Z, nb);
+  AL(ws.G, mm); AL(ws.V, mm); AL(ws.Rt, mm); AL(ws.jac, 3 * mp * mp);
+  AL(ws.lv, n_max); AL(ws.lw, n_max); AL(ws.lV, n_max * (lanczos_kmax + 1));
+  AL(ws.lc, 2 * (lanczos_kmax + 1));
+  AL(ws.theta, ws.blk_max); AL(ws.theta2, ws.blk_max); AL(ws.resid, ws.blk_max);
+  AL(ws.resid2, ws.blk_max); AL(ws.lamL, ws.blk_max); AL(ws.residL, ws.blk_max);
+  AL(ws.gres, ws.blk_max); AL(ws.dscale, ws.blk_max); AL(ws.scal, 64);
+  AL(ws.lal, lanczos_kmax + 1); AL(ws.lbe, lanczos_kmax + 1);
+  AL(ws.deg, ws.blk_max); AL(ws.perm, ws.blk_max); AL(ws.degs, ws.blk_max);
+  AL(ws.flag, ws.blk_max + 64); AL(ws.ilist, 64);
+  AL(ws.status, 2); AL(ws.barrier, 4);
+  ws.splitk_elems = (size_t)std::max<int64_t>(8 * nb, 48 * mm);
+  AL(ws.splitk, ws.splitk_elems);
+#undef AL
+  e = cudaMemset(ws.status, 0, 2 * sizeof(int));
+  if (e != cudaSuccess) return e;
+  const int big = 0x7fffffff;
+  e = cudaMemcpy(ws.status + 1, &big, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+void workspace_free(Workspace& ws) {
+  void* ptrs[] = {ws.Af, ws.Bf, ws.Lf, ws.Linv, ws.Hs, ws.T, ws.Y0, ws.Y1, ws.F, ws.W, ws.YL,
+                  ws.Xw, ws.Z, ws.G, ws.V, ws.Rt, ws.jac, ws.lv, ws.lw, ws.lV, ws.lc, ws.theta,
+                  ws.theta2, ws.resid, ws.resid2, ws.lamL, ws.residL, ws.gres, ws.dscale,
+                  ws.scal, ws.lal, ws.lbe, ws.deg, ws.perm, ws.degs, ws.flag, ws.ilist,
+                  ws.status, ws.status + 1, ws.barrier, ws.splitk};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  ws = Workspace{};
+}
+
+// ====================================================================== C ABI
+extern "C" {
+
+void chfsi_default_opts(chfsi_opts* o) {
+  if (!o) return;
+  o->deg_min = 8;
+  o->deg_max = 25;
+  o->max_loops = 50;
+  o->lanczos_k_warm = 10;
+  o->lanczos_k_cold = 40;
+  o->reuse_factor = 1;
+  o->seed = 12063768ull;
+  o->cuda_stream = nullptr;
+}
+
+int chfsi_create(chfsi_ctx** out, int64_t n_max, int32_t blk_max, const chfsi_opts* opts) {
+  if (!out) return CHFSI_EINVAL;
+  *out = nullptr;
+  if (n_max <= 0 || blk_max <= 0 || blk_max > n_max || n_max > (int64_t)1 << 30)
+    return CHFSI_EINVAL;
+  chfsi_ctx* ctx = new chfsi_ctx;
+  chfsi_default_opts(&ctx->opts);
+  if (opts) ctx->opts = *opts;
+  if (cudaGetDevice(&ctx->ws.dev) != cudaSuccess) {
+    delete ctx;
+    return CHFSI_ECUDA;
+  }
+  if (ctx->opts.cuda_stream) {
+    ctx->stream = (cudaStream_t)ctx->opts.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return CHFSI_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  const int kmax = std::max({ctx->opts.lanczos_k_warm, ctx->opts.lanczos_k_cold, 20, 1});
+  cudaError_t e = workspace_alloc(ctx->ws, n_max, blk_max, kmax);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    workspace_free(ctx->ws);
+    release_stream(ctx);
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? CHFSI_ENOMEM : CHFSI_ECUDA;
+  }
+  *out = ctx;
+  return CHFSI_OK;
+}
+
+void chfsi_destroy(chfsi_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->ws.dev);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  workspace_free(ctx->ws);
+  release_stream(ctx);
+  delete ctx;
+}
+
+const char* chfsi_last_error(const chfsi_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int chfsi_reset_warm_state(chfsi_ctx* ctx) {
+  if (!ctx) return CHFSI_EINVAL;
+  ctx->has_warm = false;
+  ctx->has_factor = false;
+  ctx->warm_lam.clear();
+  return CHFSI_OK;
+}
+
+int chfsi_solve_next(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const chfsi_z* B,
+                     int64_t ldb, const chfsi_z* V0, int32_t nev, int32_t blk, int32_t deg,
+                     double tol, double* evals, chfsi_z* evecs, chfsi_stats* st) {
+  CKS(validate_sizes(ctx, n, nev, blk));
+  if (!A || !B || lda < n || ldb < n) return set_err(ctx, CHFSI_EINVAL, "bad A/B arguments");
+  if (deg < 0) return set_err(ctx, CHFSI_EINVAL, "deg must be >= 0");
+  cudaSetDevice(ctx->ws.dev);
+  SolveArgs S{(int)n, nev, blk, deg, tol, A, B, V0, lda, ldb, evals, evecs, st};
+  return solve_one(ctx, S);
+}
+
+int chfsi_solve_sequence(chfsi_ctx* ctx, int32_t N, int64_t n, const chfsi_z* const* A,
+                         const chfsi_z* const* B, int64_t ld, const chfsi_z* V0, int32_t nev,
+                         int32_t blk, int32_t deg, double tol, double* evals,
+                         chfsi_z* const* evecs, chfsi_stats* st) {
+  CKS(validate_sizes(ctx, n, nev, blk));
+  if (N <= 0 || !A || !B || !evals) return set_err(ctx, CHFSI_EINVAL, "bad sequence arguments");
+  for (int l = 0; l < N; ++l) {
+    const int rc = chfsi_solve_next(ctx, n, A[l], ld, B[l], ld, l == 0 ? V0 : nullptr, nev, blk,
+                                    deg, tol, evals + (int64_t)l * nev,
+                                    evecs ? evecs[l] : nullptr, st ? st + l : nullptr);
+    if (rc != CHFSI_OK) return rc;
+  }
+  return CHFSI_OK;
+}
+
+// ---------------------------------------------------------------- step entry points
+int chfsi_cholesky(chfsi_ctx* ctx, int64_t n, const chfsi_z* B, int64_t ldb, chfsi_z* L,
+                   int64_t ldl) {
+  if (!ctx || !B || !L || n <= 0 || ldb < n || ldl < n) return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (n > ctx->ws.n_max) return set_err(ctx, CHFSI_EINVAL, "n > n_max");
+  cudaSetDevice(ctx->ws.dev);
+  CKS(reset_status(ctx));
+  CK(cudaMemcpy2DAsync(L, ldl * sizeof(zd), B, ldb * sizeof(zd), n * sizeof(zd), n,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  CKS(blocked_cholesky(ctx, Z(L), ldl, (int)n));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx, "chfsi_cholesky");
+}
+
+int chfsi_reduce(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const chfsi_z* L,
+                 int64_t ldl, chfsi_z* Hs, int64_t ldh) {
+  if (!ctx || !A || !L || !Hs || n <= 0 || lda < n || ldl < n || ldh < n)
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (n > ctx->ws.n_max) return set_err(ctx, CHFSI_EINVAL, "n > n_max");
+  cudaSetDevice(ctx->ws.dev);
+  CKS(reset_status(ctx));
+  Workspace& ws = ctx->ws;
+  CKS(blocked_trinv(ctx, Z(L), ldl, ws.Linv, ws.n_max, (int)n));
+  CK(herm_from_lower(Z(A), lda, ws.Af, ws.n_max, (int)n, ws.status, ctx->stream));
+  CKS(reduce_to_standard(ctx, ws.Af, ws.n_max, ws.Linv, ws.n_max, Z(Hs), ldh, (int)n));
+  ctx->has_factor = false;  // ws.Linv no longer matches ws.Bf
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx, "chfsi_reduce");
+}
+
+int chfsi_lanczos(chfsi_ctx* ctx, int64_t n, const chfsi_z* H, int64_t ldh, int32_t k,
+                  const chfsi_z* v0, double* upper, double* theta_min, double* theta_max) {
+  if (!ctx || !H || n <= 0 || ldh < n || k <= 0) return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (n > ctx->ws.n_max) return set_err(ctx, CHFSI_EINVAL, "n > n_max");
+  if (k > ctx->ws.lanczos_kmax)
+    return set_err(ctx, CHFSI_EINVAL, "k=%d above the context's Lanczos limit %d", k,
+                   ctx->ws.lanczos_kmax);
+  cudaSetDevice(ctx->ws.dev);
+  double out[3];
+  CKS(lanczos_run(ctx, Z(H), ldh, (int)n, k, Z(v0), ctx->opts.seed, ctx->ws.scal));
+  CKS(read_back(ctx, out, ctx->ws.scal, 3));
+  if (theta_min) *theta_min = out[0];
+  if (theta_max) *theta_max = out[1];
+  if (upper) *upper = out[2];
+  return CHFSI_OK;
+}
+
+int chfsi_filter(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh, chfsi_z* Y,
+                 int64_t ldy, const int32_t* degrees, double a0, double a, double b) {
+  if (!ctx || !H || !Y || !degrees || n <= 0 || m <= 0 || ldh < n || ldy < n)
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (n > ctx->ws.n_max || m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "size > workspace");
+  if (!(b > a)) return set_err(ctx, CHFSI_EINVAL, "need b > a");
+  cudaSetDevice(ctx->ws.dev);
+  Workspace& ws = ctx->ws;
+  const int64_t ld = ws.n_max;
+  std::vector<int> idx(m);
+  std::iota(idx.begin(), idx.end(), 0);
+  for (int j = 0; j < m; ++j)
+    if (degrees[j] < 0) return set_err(ctx, CHFSI_EINVAL, "negative degree");
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return degrees[x] > degrees[y]; });
+  std::vector<int> ds(m), inv(m);
+  for (int r = 0; r < m; ++r) { ds[r] = degrees[idx[r]]; inv[idx[r]] = r; }
+  CK(cudaMemcpy2DAsync(ws.Y0, ld * sizeof(zd), Y, ldy * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ws.perm, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  zd *Ya = ws.Y0, *Yb = ws.Y1, *Yf = ws.F;
+  CKS(filter_block(ctx, Z(H), ldh, (int)n, m, &Ya, &Yb, &Yf, ds, ws.perm, a0, a, b, nullptr));
+  // undo the permutation: Y[:, j] = Ya[:, inv[j]]
+  CK(cudaMemcpyAsync(ws.deg, inv.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(gather_cols(Ya, ld, Yb, ld, (int)n, m, ws.deg, ctx->stream));
+  CK(cudaMemcpy2DAsync(Y, ldy * sizeof(zd), Yb, ld * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHFSI_OK;
+}
+
+int chfsi_orthonormalize(chfsi_ctx* ctx, int64_t n, int32_t m, chfsi_z* Y, int64_t ldy, int32_t k,
+                         const chfsi_z* YL, int64_t ldyl) {
+  if (!ctx || !Y || n <= 0 || m <= 0 || ldy < n || k < 0 || (k > 0 && (!YL || ldyl < n)))
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (n > ctx->ws.n_max || m > ctx->ws.blk_max || k > ctx->ws.blk_max || m + k > n)
+    return set_err(ctx, CHFSI_EINVAL, "size > workspace");
+  cudaSetDevice(ctx->ws.dev);
+  CKS(reset_status(ctx));
+  Workspace& ws = ctx->ws;
+  const int64_t ld = ws.n_max;
+  CK(cudaMemcpy2DAsync(ws.Y0, ld * sizeof(zd), Y, ldy * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  zd *Ya = ws.Y0, *Yb = ws.Y1;
+  CKS(orthonormalize_block(ctx, (int)n, m, &Ya, &Yb, Z(YL), ldyl, k));
+  CK(cudaMemcpy2DAsync(Y, ldy * sizeof(zd), Ya, ld * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx, "chfsi_orthonormalize");
+}
+
+int chfsi_rayleigh_ritz(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,
+                        chfsi_z* Y, int64_t ldy, chfsi_z* HY, int64_t ldhy, double* theta) {
+  if (!ctx || !H || !Y || !HY || !theta || n <= 0 || m <= 0 || ldh < n || ldy < n || ldhy < n)
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (n > ctx->ws.n_max || m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "size > workspace");
+  cudaSetDevice(ctx->ws.dev);
+  CKS(reset_status(ctx));
+  Workspace& ws = ctx->ws;
+  const int64_t ld = ws.n_max;
+  CK(cudaMemcpy2DAsync(ws.Y0, ld * sizeof(zd), Y, ldy * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  zd *Ya = ws.Y0, *Yb = ws.Y1, *W = ws.W, *Zb = ws.Z;
+  CKS(rayleigh_ritz_block(ctx, Z(H), ldh, (int)n, m, &Ya, &Yb, &W, &Zb, theta));
+  CK(cudaMemcpy2DAsync(Y, ldy * sizeof(zd), Ya, ld * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpy2DAsync(HY, ldhy * sizeof(zd), W, ld * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx, "chfsi_rayleigh_ritz");
+}
+
+int chfsi_residuals(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* HY, int64_t ldhy,
+                    const chfsi_z* Y, int64_t ldy, const double* theta, double* r) {
+  if (!ctx || !HY || !Y || !theta || !r || n <= 0 || m <= 0 || ldhy < n || ldy < n)
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  cudaSetDevice(ctx->ws.dev);
+  CK(column_residuals(Z(HY), ldhy, Z(Y), ldy, theta, (int)n, m, r, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHFSI_OK;
+}
+
+int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* r, double a,
+                  double b, double tau, int32_t dmin, int32_t dmax, int32_t n_wanted,
+                  int32_t* degrees) {
+  if (!ctx || !theta || !r || !degrees || m <= 0 || dmin < 0 || dmax < dmin || !(b > a) || n_wanted < 0)
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "m > blk_max");
+  cudaSetDevice(ctx->ws.dev);
+  CK(degrees_kernel_run(theta, r, m, a, b, tau, dmin, dmax, n_wanted, degrees, ctx->ws.perm,
+                        ctx->ws.degs, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHFSI_OK;
+}
+
+int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double* w, chfsi_z* V,
+               int64_t ldv) {
+  if (!ctx || !G || !w || !V || m <= 0 || ldg < m || ldv < m) return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "m > blk_max");
+  cudaSetDevice(ctx->ws.dev);
+  CKS(reset_status(ctx));
+  CK(jacobi_heev(Z(G), ldg, m, w, Z(V), ldv, ctx->ws.jac, ctx->ws.barrier, ctx->ws.status,
+                 ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx, "chfsi_heev");
+}
+
+int chfsi_zgemm(chfsi_ctx* ctx, char opa, char opb, int32_t M, int32_t N, int32_t K, double alpha,
+                const chfsi_z* A, int64_t lda, const chfsi_z* B, int64_t ldb, double beta,
+                chfsi_z* C, int64_t ldc) {
+  if (!ctx || !C || M < 0 || N < 0 || K < 0 || (K > 0 && (!A || !B)))
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  const int oA = (opa == 'C' || opa == 'c') ? OPC : OPN;
+  const int oB = (opb == 'C' || opb == 'c') ? OPC : OPN;
+  if ((oA == OPN && lda < M) || (oA == OPC && lda < K) || (oB == OPN && ldb < K) ||
+      (oB == OPC && ldb < N) || ldc < M)
+    return set_err(ctx, CHFSI_EINVAL, "bad leading dimension");
+  cudaSetDevice(ctx->ws.dev);
+  GemmDesc g = gd(M, N, K, Z(A), lda, oA, Z(B), ldb, oB, Z(C), ldc, alpha);
+  if (beta != 0.0) { g.beta = beta; g.Cin = Z(C); g.ldcin = ldc; }
+  CKS(gemm(ctx, g));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHFSI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Internal declarations of the ChFSI library (kernels, workspace, engine).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "chfsi.h"
+
+typedef double2 zd;  // complex double: x = real part, y = imaginary part
+
+#define CHFSI_HD __host__ __device__ __forceinline__
+
+CHFSI_HD zd zmk(double r, double i) { return make_double2(r, i); }
+CHFSI_HD zd zadd(zd a, zd b) { return make_double2(a.x + b.x, a.y + b.y); }
+CHFSI_HD zd zsub(zd a, zd b) { return make_double2(a.x - b.x, a.y - b.y); }
+CHFSI_HD zd zscale(zd a, double s) { return make_double2(a.x * s, a.y * s); }
+CHFSI_HD zd zconj(zd a) { return make_double2(a.x, -a.y); }
+CHFSI_HD zd zmul(zd a, zd b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// c + a * b
+CHFSI_HD zd zfma(zd a, zd b, zd c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// c + conj(a) * b
+CHFSI_HD zd zfma_cj(zd a, zd b, zd c) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+CHFSI_HD double zabs2(zd a) { return a.x * a.x + a.y * a.y; }
+
+// Status flags written by kernels into the context's device status word.
+enum : int {
+  DEV_OK = 0,
+  DEV_NOTPD = 1,       // non-positive pivot in a Cholesky factorisation
+  DEV_TIMEOUT = 2,     // a bounded grid barrier gave up
+  DEV_NOCONV = 4,      // Jacobi reached its sweep limit
+  DEV_NAN = 8,         // non-finite value met
+};
+
+// ------------------------------------------------------------------ GEMM
+enum { OPN = 0, OPC = 1 };
+
+struct GemmDesc {
+  int M = 0, N = 0, K = 0;
+  const zd* A = nullptr; int64_t lda = 0; int opA = OPN;
+  const zd* B = nullptr; int64_t ldb = 0; int opB = OPN;
+  zd* C = nullptr; int64_t ldc = 0;
+  double alpha = 1.0;
+  double beta = 0.0; const zd* Cin = nullptr; int64_t ldcin = 0;   // + beta * Cin (may alias C)
+  double gamma = 0.0; const zd* D = nullptr; int64_t ldd = 0;      // + gamma * D (may alias C)
+  int triA = 0;   // 1: op(A)(i,k) == 0 for k > i (lower); 2: == 0 for k < i (upper)
+  int triB = 0;   // 1: op(B)(k,j) == 0 for k > j (upper); 2: == 0 for k < j (lower)
+  int lowerC = 0; // 1: only C(i,j) with i >= j is computed and written
+};
+
+struct Workspace;
+// Queue one GEMM on `stream`.  Uses ws's split-K buffer.  Returns cudaError_t.
+cudaError_t zgemm_run(const GemmDesc& g, Workspace& ws, cudaStream_t stream);
+// Number of SMs of the current device (cached).
+int sm_count();
+
+// ------------------------------------------------------------------ small dense kernels
+// Cholesky of an m x m Hermitian block (lower triangle read), in place: lower factor,
+// strict upper zeroed.  scale: first scale to unit diagonal (D G D, dscale[i] = 1/sqrt(G_ii)).
+// shift_on_fail: retry a failed factorisation on G + s I, s = shift_base * trace (shifted
+// Cholesky QR); backup is an m x m scratch for the retry.  On failure sets DEV_NOTPD in
+// status and atomically lowers *info to info_base + the failing pivot.  One CTA.
+cudaError_t small_cholesky(zd* G, int64_t ldg, int m, int scale, int shift_on_fail,
+                           double shift_base, double* dscale, zd* backup, int* status, int* info,
+                           int info_base, cudaStream_t s);
+// X = L^{-1} for an m x m lower-triangular L (strict upper of X zeroed).  X != L.
+cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m, cudaStream_t s);
+// T = D X^H (upper triangular, zero below): the right factor of Cholesky QR, Q = Y T.
+cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* T, int64_t ldt,
+                     cudaStream_t s);
+// Jacobi eigensolver (cooperative multi-CTA).  G not modified.  work: 2*m'*m' + barrier.
+cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64_t ldv,
+                        zd* work, unsigned* barrier, int* status, cudaStream_t s);
+
+// ------------------------------------------------------------------ vector kernels
+cudaError_t herm_from_lower(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n,
+                            int* status, cudaStream_t s);
+cudaError_t mirror_lower(zd* H, int64_t ldh, int n, cudaStream_t s);
+cudaError_t zero_upper(zd* L, int64_t ldl, int n, cudaStream_t s);
+cudaError_t copy_cols(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m,
+                      cudaStream_t s);
+cudaError_t compare_equal(const zd* a, int64_t lda, const zd* b, int64_t ldb, int n, int m,
+                          int* diff_flag, cudaStream_t s);
+cudaError_t gather_cols(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m,
+                        const int* perm, cudaStream_t s);
+cudaError_t select_cols(const zd* src1, int64_t ld1, zd* dst, int64_t ldd, int n, int m,
+                        const int* flag, cudaStream_t s);
+cudaError_t column_residuals(const zd* HY, int64_t ldhy, const zd* Y, int64_t ldy,
+                             const double* theta, int n, int m, double* r, cudaStream_t s);
+cudaError_t generalized_residuals(const zd* AX, int64_t ldax, const zd* BX, int64_t ldbx,
+                                  const zd* X, int64_t ldx, const double* lam, int n, int m,
+                                  const double* a_norm, double* r, cudaStream_t s);
+cudaError_t splitmix_start_vector(zd* v, int n, uint64_t seed, cudaStream_t s);
+cudaError_t splitmix_gaussian_block(zd* Y, int64_t ldy, int n, int m, uint64_t seed,
+                                    cudaStream_t s);
+cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, double a, double b,
+                               double tau, int dmin, int dmax, int n_wanted, int* deg,
+                               int* perm_desc, int* deg_sorted, cudaStream_t s);
+cudaError_t lock_scan(const double* r, int m, double tau, int max_lock, int* nlock,
+                      cudaStream_t s);
+cudaError_t fill_nan(double* x, int m, cudaStream_t s);
+
+// Lanczos pieces
+cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s);
+cudaError_t block_dots(const zd* V, int64_t ldv, int j, const zd* w, int n, zd* c,
+                       cudaStream_t s);
+cudaError_t block_update(const zd* V, int64_t ldv, int j, const zd* c, zd* w, int n,
+                         cudaStream_t s);
+cudaError_t vec_norm(const zd* w, int n, double* out, cudaStream_t s);
+cudaError_t vec_scale_into(const zd* w, int n, const double* nrm, zd* dst, cudaStream_t s);
+cudaError_t lanczos_record(const zd* c, int j, const double* nrm, double* alpha, double* beta,
+                           cudaStream_t s);
+cudaError_t tridiag_extremes(const double* alpha, const double* beta, int k, double* out3,
+                             cudaStream_t s);
+
+// ------------------------------------------------------------------ workspace
+struct Workspace {
+  int dev = 0;
+  int64_t n_max = 0;
+  int blk_max = 0;
+  // n x n buffers
+  zd *Af = nullptr, *Bf = nullptr, *Lf = nullptr, *Linv = nullptr, *Hs = nullptr, *T = nullptr;
+  // n x blk buffers
+  zd *Y0 = nullptr, *Y1 = nullptr, *F = nullptr, *W = nullptr, *YL = nullptr, *Xw = nullptr,
+     *Z = nullptr;
+  // m x m buffers
+  zd *G = nullptr, *V = nullptr, *Rt = nullptr, *jac = nullptr;
+  // vectors
+  zd *lv = nullptr, *lw = nullptr, *lV = nullptr, *lc = nullptr;  // Lanczos: n, n, n*(kmax+1), kmax+1
+  int lanczos_kmax = 0;
+  double *theta = nullptr, *theta2 = nullptr, *resid = nullptr, *resid2 = nullptr;
+  double *lamL = nullptr, *residL = nullptr, *gres = nullptr;
+  double *dscale = nullptr, *scal = nullptr, *lal = nullptr, *lbe = nullptr;
+  int *deg = nullptr, *perm = nullptr, *degs = nullptr, *flag = nullptr, *ilist = nullptr;
+  int* status = nullptr;  // [0]: DEV_* flags, [1]: first failing pivot
+  unsigned* barrier = nullptr;
+  // split-K partials
+  zd* splitk = nullptr;
+  size_t splitk_elems = 0;
+  // pinned host mirror for small read-backs
+  void* host_pinned = nullptr;
+  size_t host_pinned_bytes = 0;
+};
+
+cudaError_t workspace_alloc(Workspace& ws, int64_t n_max, int blk_max, int lanczos_kmax);
+void workspace_free(Workspace& ws);

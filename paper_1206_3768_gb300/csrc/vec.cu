@@ -1,0 +1,492 @@
+// Bandwidth-bound and bookkeeping kernels of the solver: Hermitian completion of the
+// lower-triangle inputs, column copies and gathers, residual norms of the locking test,
+// locking prefix scan, per-vector degrees, the SplitMix64 start vectors, and the pieces
+// of the Lanczos bound (row-dot Hermitian matrix-vector product, block dot products,
+// tridiagonal extreme eigenvalues by Sturm bisection).
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TILE = 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (blockDim.x a multiple of 32, <= 1024).  All threads get the result.
+__device__ double block_sum(double v) {
+  __shared__ double sh[32];
+  __shared__ double total;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) total = t;
+  }
+  __syncthreads();
+  const double r = total;
+  __syncthreads();
+  return r;
+}
+
+// dst = Hermitian completion of the lower triangle of src (32 x 32 tiles through shared
+// memory so both the direct and the transposed reads are coalesced).
+__global__ void herm_from_lower_kernel(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n,
+                                       int* status) {
+  __shared__ zd tile[TILE][TILE + 1];
+  const int bi = blockIdx.x * TILE, bj = blockIdx.y * TILE;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  int bad = 0;
+  if (bi >= bj) {  // tile on or below the diagonal: copy (upper part of diagonal tiles below)
+    for (int r = ty; r < TILE; r += 8) {
+      const int i = bi + tx, j = bj + r;
+      if (i < n && j < n) {
+        zd v = src[i + (int64_t)j * lds];
+        bad |= (i >= j) && !(isfinite(v.x) && isfinite(v.y));
+        tile[r][tx] = v;
+      }
+    }
+    __syncthreads();
+    for (int r = ty; r < TILE; r += 8) {
+      const int i = bi + tx, j = bj + r;
+      if (i < n && j < n) {
+        zd v;
+        if (i > j) v = tile[r][tx];
+        else if (i == j) v = zmk(tile[r][tx].x, 0.0);
+        else v = zconj(tile[tx][r]);  // (i, j) upper within a diagonal tile: conj(src(j, i))
+        dst[i + (int64_t)j * ldd] = v;
+      }
+    }
+  } else {  // strictly upper tile: dst(i, j) = conj(src(j, i)); read the mirrored tile
+    for (int r = ty; r < TILE; r += 8) {
+      const int i = bj + tx, j = bi + r;  // src rows from column block bj... (j, i) pairs
+      if (i < n && j < n) tile[r][tx] = src[i + (int64_t)j * lds];
+    }
+    __syncthreads();
+    for (int r = ty; r < TILE; r += 8) {
+      const int i = bi + tx, j = bj + r;
+      if (i < n && j < n) dst[i + (int64_t)j * ldd] = zconj(tile[tx][r]);
+    }
+  }
+  if (bad) atomicOr(status, DEV_NAN);
+}
+
+// In place: H(i, j) = conj(H(j, i)) for i < j, imaginary part of the diagonal dropped.
+__global__ void mirror_lower_kernel(zd* H, int64_t ldh, int n) {
+  __shared__ zd tile[TILE][TILE + 1];
+  const int bi = blockIdx.x * TILE, bj = blockIdx.y * TILE;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (bi > bj) return;  // only tiles on or above the diagonal are written
+  // read the mirrored (lower) tile: rows bj.., cols bi..
+  for (int r = ty; r < TILE; r += 8) {
+    const int i = bj + tx, j = bi + r;
+    if (i < n && j < n) tile[r][tx] = H[i + (int64_t)j * ldh];
+  }
+  __syncthreads();
+  for (int r = ty; r < TILE; r += 8) {
+    const int i = bi + tx, j = bj + r;
+    if (i < n && j < n) {
+      if (i < j) H[i + (int64_t)j * ldh] = zconj(tile[tx][r]);
+      else if (i == j) H[i + (int64_t)j * ldh] = zmk(tile[tx][r].x, 0.0);
+    }
+  }
+}
+
+__global__ void zero_upper_kernel(zd* L, int64_t ldl, int n) {
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) L[i + (int64_t)j * ldl] = zmk(0.0, 0.0);
+  }
+}
+
+__global__ void copy_cols_kernel(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m,
+                                 const int* perm, const int* flag) {
+  const int64_t total = (int64_t)n * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (flag && !flag[j]) continue;
+    const int sj = perm ? perm[j] : j;
+    dst[i + (int64_t)j * ldd] = src[i + (int64_t)sj * lds];
+  }
+}
+
+__global__ void compare_kernel(const zd* a, int64_t lda, const zd* b, int64_t ldb, int n, int m,
+                               int* diff) {
+  const int64_t total = (int64_t)n * m;
+  int d = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) continue;  // lower triangle only
+    const zd x = a[i + (int64_t)j * lda], y = b[i + (int64_t)j * ldb];
+    d |= (__double_as_longlong(x.x) != __double_as_longlong(y.x)) ||
+         (__double_as_longlong(x.y) != __double_as_longlong(y.y));
+  }
+  if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) atomicOr(diff, 1);
+}
+
+// r_j = ||HY_j - theta_j Y_j|| / ||Y_j||, one CTA per column (fixed reduction order).
+__global__ void column_residuals_kernel(const zd* HY, int64_t ldhy, const zd* Y, int64_t ldy,
+                                        const double* theta, int n, double* r) {
+  const int j = blockIdx.x;
+  const double th = theta[j];
+  double num = 0.0, den = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const zd y = Y[i + (int64_t)j * ldy];
+    const zd h = HY[i + (int64_t)j * ldhy];
+    const zd d = zmk(h.x - th * y.x, h.y - th * y.y);
+    num += zabs2(d);
+    den += zabs2(y);
+  }
+  num = block_sum(num);
+  den = block_sum(den);
+  if (threadIdx.x == 0) r[j] = sqrt(num) / sqrt(den);
+}
+
+// ||AX_j - lam_j BX_j|| / (a_norm ||X_j||)
+__global__ void gen_residuals_kernel(const zd* AX, int64_t ldax, const zd* BX, int64_t ldbx,
+                                     const zd* X, int64_t ldx, const double* lam, int n,
+                                     const double* a_norm, double* r) {
+  const int j = blockIdx.x;
+  const double l = lam[j];
+  double num = 0.0, den = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const zd a = AX[i + (int64_t)j * ldax], b = BX[i + (int64_t)j * ldbx];
+    const zd x = X[i + (int64_t)j * ldx];
+    const zd d = zmk(a.x - l * b.x, a.y - l * b.y);
+    num += zabs2(d);
+    den += zabs2(x);
+  }
+  num = block_sum(num);
+  den = block_sum(den);
+  if (threadIdx.x == 0) r[j] = sqrt(num) / (a_norm[0] * sqrt(den));
+}
+
+// ---------------------------------------------------------------- SplitMix64
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
+                                                         unsigned long long idx) {
+  unsigned long long z = seed + (idx + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double u01(unsigned long long seed, unsigned long long idx) {
+  return (double)(splitmix64(seed, idx) >> 11) * 0x1.0p-53;
+}
+
+__global__ void start_vector_kernel(zd* v, int n, unsigned long long seed) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    v[j] = zmk(u01(seed, 2ull * j) - 0.5, u01(seed, 2ull * j + 1) - 0.5);
+}
+
+__global__ void gaussian_block_kernel(zd* Y, int64_t ldy, int n, int m, unsigned long long seed) {
+  const int64_t total = (int64_t)n * m;
+  const double pi2 = 6.283185307179586476925286766559;
+  const double rs2 = 0.70710678118654752440084436210485;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double u1 = u01(seed, 2ull * t), u2 = u01(seed, 2ull * t + 1);
+    const double rr = sqrt(-2.0 * log1p(-u1));
+    double sn, cs;
+    sincos(pi2 * u2, &sn, &cs);
+    const int i = (int)(t % n), j = (int)(t / n);
+    Y[i + (int64_t)j * ldy] = zmk(rr * cs * rs2, rr * sn * rs2);
+  }
+}
+
+// ---------------------------------------------------------------- degrees and locking
+__global__ void degrees_kernel(const double* theta, const double* r, int m, double a, double b,
+                               double tau, int dmin, int dmax, int n_wanted, int* deg, int* perm,
+                               int* degs) {
+  extern __shared__ int sd[];
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    int d = dmax;
+    const double ri = r[i];
+    if (ri <= tau) {
+      d = dmin;
+    } else {
+      const double t = fabs((theta[i] - c) / e);
+      if (t > 1.0) {
+        const double rho = t + sqrt(t * t - 1.0);
+        const double need = log(ri / tau) / log(rho);
+        if (isfinite(need) && need < (double)dmax) d = min(dmax, max(dmin, (int)ceil(need)));
+      }
+    }
+    sd[i] = d;
+  }
+  __syncthreads();
+  __shared__ int top;
+  if (threadIdx.x == 0) {
+    int t = dmin;
+    for (int i = 0; i < min(n_wanted, m); ++i) t = max(t, sd[i]);
+    top = t;
+  }
+  __syncthreads();
+  for (int i = n_wanted + threadIdx.x; i < m; i += blockDim.x) sd[i] = top;
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int di = sd[i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) rank += (sd[j] > di) || (sd[j] == di && j < i);
+    deg[i] = di;
+    perm[rank] = i;
+    degs[rank] = di;
+  }
+}
+
+__global__ void lock_scan_kernel(const double* r, int m, double tau, int max_lock, int* nlock) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int c = 0;
+    const int lim = min(m, max_lock);
+    while (c < lim && r[c] < tau) ++c;
+    *nlock = c;
+  }
+}
+
+__global__ void fill_nan_kernel(double* x, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    x[i] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// ---------------------------------------------------------------- Lanczos pieces
+// w_i = sum_j H(i, j) v_j = sum_j conj(H(j, i)) v_j (H Hermitian): one warp per row reads
+// column i contiguously.
+__global__ void hemv_rows_kernel(const zd* H, int64_t ldh, const zd* v, zd* w, int n) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (blockDim.x >> 5) * gridDim.x;
+  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+    const zd* col = H + (int64_t)i * ldh;
+    double sr = 0.0, si = 0.0;
+    for (int j = lane; j < n; j += 32) {
+      const zd h = col[j], x = v[j];
+      sr += h.x * x.x + h.y * x.y;
+      si += h.x * x.y - h.y * x.x;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) w[i] = zmk(sr, si);
+  }
+}
+
+// c_l = V_l^H w for l = 0..j  (one CTA per l)
+__global__ void block_dots_kernel(const zd* V, int64_t ldv, const zd* w, int n, zd* c) {
+  const int l = blockIdx.x;
+  double sr = 0.0, si = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const zd a = V[i + (int64_t)l * ldv], b = w[i];
+    sr += a.x * b.x + a.y * b.y;
+    si += a.x * b.y - a.y * b.x;
+  }
+  sr = block_sum(sr);
+  si = block_sum(si);
+  if (threadIdx.x == 0) c[l] = zmk(sr, si);
+}
+
+// w -= V c  (V: n x (j+1))
+__global__ void block_update_kernel(const zd* V, int64_t ldv, int jp1, const zd* c, zd* w, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    zd s = w[i];
+    for (int l = 0; l < jp1; ++l) {
+      const zd a = V[i + (int64_t)l * ldv], cl = c[l];
+      s.x -= a.x * cl.x - a.y * cl.y;
+      s.y -= a.x * cl.y + a.y * cl.x;
+    }
+    w[i] = s;
+  }
+}
+
+__global__ void vec_norm_kernel(const zd* w, int n, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += zabs2(w[i]);
+  s = block_sum(s);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+__global__ void vec_scale_into_kernel(const zd* w, int n, const double* nrm, zd* dst) {
+  const double inv = 1.0 / nrm[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = zscale(w[i], inv);
+}
+
+__global__ void lanczos_record_kernel(const zd* c, int j, const double* nrm, double* alpha,
+                                      double* beta) {
+  if (threadIdx.x == 0) {
+    alpha[j] = c[j].x;
+    beta[j] = nrm[0];
+  }
+}
+
+// Number of eigenvalues of the symmetric tridiagonal T (alpha, beta) below x (Sturm).
+__device__ int sturm_count(const double* al, const double* be, int k, double x) {
+  int cnt = 0;
+  double q = al[0] - x;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < k; ++i) {
+    if (q == 0.0) q = 1e-300;
+    q = (al[i] - x) - be[i - 1] * be[i - 1] / q;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// out[0] = min eig(T_k), out[1] = max eig(T_k), out[2] = max eig + |beta_{k-1}|.
+__global__ void tridiag_extremes_kernel(const double* al, const double* be, int k, double* out) {
+  if (threadIdx.x != 0) return;
+  double lo = al[0], hi = al[0];
+  for (int i = 0; i < k; ++i) {
+    const double rad = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < k - 1 ? fabs(be[i]) : 0.0);
+    lo = fmin(lo, al[i] - rad);
+    hi = fmax(hi, al[i] + rad);
+  }
+  const double pad = 1e-12 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+  lo -= pad;
+  hi += pad;
+  // smallest: largest x with count(x) == 0
+  double a = lo, b = hi;
+  for (int it = 0; it < 200 && b - a > 0.0; ++it) {
+    const double mid = 0.5 * (a + b);
+    if (mid <= a || mid >= b) break;
+    if (sturm_count(al, be, k, mid) >= 1) b = mid; else a = mid;
+  }
+  out[0] = 0.5 * (a + b);
+  // largest: smallest x with count(x) == k
+  a = lo; b = hi;
+  for (int it = 0; it < 200 && b - a > 0.0; ++it) {
+    const double mid = 0.5 * (a + b);
+    if (mid <= a || mid >= b) break;
+    if (sturm_count(al, be, k, mid) >= k) b = mid; else a = mid;
+  }
+  out[1] = 0.5 * (a + b);
+  out[2] = out[1] + fabs(be[k - 1]);
+}
+
+inline int grid_for(int64_t total, int threads = 256) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(8 * sm_count(), (total + threads - 1) / threads));
+}
+
+}  // namespace
+
+cudaError_t herm_from_lower(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int* status,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = (n + TILE - 1) / TILE;
+  herm_from_lower_kernel<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(src, lds, dst, ldd, n, status);
+  return cudaGetLastError();
+}
+cudaError_t mirror_lower(zd* H, int64_t ldh, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = (n + TILE - 1) / TILE;
+  mirror_lower_kernel<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(H, ldh, n);
+  return cudaGetLastError();
+}
+cudaError_t zero_upper(zd* L, int64_t ldl, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  zero_upper_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(L, ldl, n);
+  return cudaGetLastError();
+}
+cudaError_t copy_cols(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m, cudaStream_t s) {
+  if (n <= 0 || m <= 0) return cudaSuccess;
+  copy_cols_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(src, lds, dst, ldd, n, m, nullptr, nullptr);
+  return cudaGetLastError();
+}
+cudaError_t gather_cols(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m,
+                        const int* perm, cudaStream_t s) {
+  if (n <= 0 || m <= 0) return cudaSuccess;
+  copy_cols_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(src, lds, dst, ldd, n, m, perm, nullptr);
+  return cudaGetLastError();
+}
+cudaError_t select_cols(const zd* src1, int64_t ld1, zd* dst, int64_t ldd, int n, int m,
+                        const int* flag, cudaStream_t s) {
+  if (n <= 0 || m <= 0) return cudaSuccess;
+  copy_cols_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(src1, ld1, dst, ldd, n, m, nullptr, flag);
+  return cudaGetLastError();
+}
+cudaError_t compare_equal(const zd* a, int64_t lda, const zd* b, int64_t ldb, int n, int m,
+                          int* diff_flag, cudaStream_t s) {
+  if (n <= 0 || m <= 0) return cudaSuccess;
+  compare_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(a, lda, b, ldb, n, m, diff_flag);
+  return cudaGetLastError();
+}
+cudaError_t column_residuals(const zd* HY, int64_t ldhy, const zd* Y, int64_t ldy,
+                             const double* theta, int n, int m, double* r, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  column_residuals_kernel<<<m, 256, 0, s>>>(HY, ldhy, Y, ldy, theta, n, r);
+  return cudaGetLastError();
+}
+cudaError_t generalized_residuals(const zd* AX, int64_t ldax, const zd* BX, int64_t ldbx,
+                                  const zd* X, int64_t ldx, const double* lam, int n, int m,
+                                  const double* a_norm, double* r, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  gen_residuals_kernel<<<m, 256, 0, s>>>(AX, ldax, BX, ldbx, X, ldx, lam, n, a_norm, r);
+  return cudaGetLastError();
+}
+cudaError_t splitmix_start_vector(zd* v, int n, uint64_t seed, cudaStream_t s) {
+  start_vector_kernel<<<grid_for(n), 256, 0, s>>>(v, n, (unsigned long long)seed);
+  return cudaGetLastError();
+}
+cudaError_t splitmix_gaussian_block(zd* Y, int64_t ldy, int n, int m, uint64_t seed, cudaStream_t s) {
+  gaussian_block_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(Y, ldy, n, m,
+                                                                 (unsigned long long)seed);
+  return cudaGetLastError();
+}
+cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, double a, double b,
+                               double tau, int dmin, int dmax, int n_wanted, int* deg,
+                               int* perm_desc, int* deg_sorted, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  degrees_kernel<<<1, 1024, m * sizeof(int), s>>>(theta, r, m, a, b, tau, dmin, dmax, n_wanted,
+                                                  deg, perm_desc, deg_sorted);
+  return cudaGetLastError();
+}
+cudaError_t lock_scan(const double* r, int m, double tau, int max_lock, int* nlock, cudaStream_t s) {
+  lock_scan_kernel<<<1, 32, 0, s>>>(r, m, tau, max_lock, nlock);
+  return cudaGetLastError();
+}
+cudaError_t fill_nan(double* x, int m, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  fill_nan_kernel<<<grid_for(m), 256, 0, s>>>(x, m);
+  return cudaGetLastError();
+}
+cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s) {
+  const int warps_per_block = 8;
+  const int blocks = std::max(1, std::min((n + warps_per_block - 1) / warps_per_block, 16 * sm_count()));
+  hemv_rows_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(H, ldh, v, w, n);
+  return cudaGetLastError();
+}
+cudaError_t block_dots(const zd* V, int64_t ldv, int j, const zd* w, int n, zd* c, cudaStream_t s) {
+  block_dots_kernel<<<j + 1, 256, 0, s>>>(V, ldv, w, n, c);
+  return cudaGetLastError();
+}
+cudaError_t block_update(const zd* V, int64_t ldv, int j, const zd* c, zd* w, int n, cudaStream_t s) {
+  block_update_kernel<<<grid_for(n), 256, 0, s>>>(V, ldv, j + 1, c, w, n);
+  return cudaGetLastError();
+}
+cudaError_t vec_norm(const zd* w, int n, double* out, cudaStream_t s) {
+  vec_norm_kernel<<<1, 1024, 0, s>>>(w, n, out);
+  return cudaGetLastError();
+}
+cudaError_t vec_scale_into(const zd* w, int n, const double* nrm, zd* dst, cudaStream_t s) {
+  vec_scale_into_kernel<<<grid_for(n), 256, 0, s>>>(w, n, nrm, dst);
+  return cudaGetLastError();
+}
+cudaError_t lanczos_record(const zd* c, int j, const double* nrm, double* alpha, double* beta,
+                           cudaStream_t s) {
+  lanczos_record_kernel<<<1, 32, 0, s>>>(c, j, nrm, alpha, beta);
+  return cudaGetLastError();
+}
+cudaError_t tridiag_extremes(const double* alpha, const double* beta, int k, double* out3,
+                             cudaStream_t s) {
+  tridiag_extremes_kernel<<<1, 32, 0, s>>>(alpha, beta, k, out3);
+  return cudaGetLastError();
+}

@@ -1,0 +1,351 @@
+"""Parity of the sm_103a library (called through its C ABI) with the CPU oracle.
+
+Each test feeds the same seeded inputs to one entry point of libchfsi.so and to the
+oracle function that restates the same step, and compares element by element within
+an FP64 tolerance derived from the arithmetic (a few hundred ulps of the operands'
+scale for one product; 1e-10 relative for eigenvalues and residuals of a whole solve,
+the target of Table 3).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.chfsi_oracle as O
+from paper_1206_3768_gb300 import binding as cb
+from paper_1206_3768_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    s = cb.Solver(700, 160)
+    yield s.ctx
+    s.close()
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _cgauss(rng, *shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2)
+
+
+def _herm(rng, n, spread=1.0):
+    M = _cgauss(rng, n, n)
+    return spread * 0.5 * (M + M.conj().T)
+
+
+def _hpd(rng, n):
+    G = _cgauss(rng, n, n)
+    return np.eye(n) + 0.3 * (G.conj().T @ G) / n
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# ---------------------------------------------------------------------------- GEMM
+@pytest.mark.parametrize("opa,opb", [("N", "N"), ("N", "C"), ("C", "N"), ("C", "C")])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (70, 33, 45), (129, 130, 700), (64, 32, 16),
+                                   (200, 5, 3000 // 5)])
+def test_zgemm_matches_exact_product(ctx, opa, opb, M, N, K):
+    rng = _rng(M * 7 + N * 3 + K)
+    A = _cgauss(rng, M, K) if opa == "N" else _cgauss(rng, K, M)
+    B = _cgauss(rng, K, N) if opb == "N" else _cgauss(rng, N, K)
+    C0 = _cgauss(rng, M, N)
+    opA = A if opa == "N" else A.conj().T
+    opB = B if opb == "N" else B.conj().T
+    ref = 0.75 * (opA @ opB) - 0.5 * C0
+    got = _np(cb.chfsi_zgemm(ctx, opa, opb, 0.75, _t(A), _t(B), beta=-0.5, C=_t(C0)))
+    scale = np.abs(opA) @ np.abs(opB) + np.abs(C0)
+    assert np.max(np.abs(got - ref) / scale) < 64 * K * 2.2e-16
+
+
+# ---------------------------------------------------------------------------- reduction
+@pytest.mark.parametrize("n", [1, 37, 128, 300, 513])
+def test_cholesky_matches_oracle(ctx, n):
+    rng = _rng(n)
+    B = _hpd(rng, n)
+    Bl = np.tril(B) + np.triu(_cgauss(rng, n, n), 1) * 1e3  # upper triangle must be ignored
+    L = _np(cb.chfsi_cholesky(ctx, _t(Bl)))
+    Lo = O.cholesky_lower(np.tril(B))
+    assert np.allclose(np.triu(L, 1), 0.0)
+    assert _rel(L, Lo) < 1e-12
+
+
+def test_cholesky_reports_not_positive_definite(ctx):
+    rng = _rng(3)
+    n = 200
+    B = _hpd(rng, n)
+    B[150, 150] = -5.0
+    with pytest.raises(cb.ChfsiError) as ei:
+        cb.chfsi_cholesky(ctx, _t(B))
+    assert ei.value.code == cb.CHFSI_ENOTPD
+    # the context stays usable
+    L = _np(cb.chfsi_cholesky(ctx, _t(_hpd(rng, 50))))
+    assert np.all(np.isfinite(L))
+
+
+@pytest.mark.parametrize("n", [64, 257, 640])
+def test_reduce_matches_oracle(ctx, n):
+    rng = _rng(n + 1)
+    A = _herm(rng, n, 3.0)
+    B = _hpd(rng, n)
+    Lo = O.cholesky_lower(np.tril(B))
+    H = _np(cb.chfsi_reduce(ctx, _t(np.tril(A)), _t(Lo)))
+    Ho = O.reduce_standard(np.tril(A), Lo)
+    assert np.allclose(H, H.conj().T, atol=0)
+    assert _rel(H, Ho) < 1e-12
+
+
+# ---------------------------------------------------------------------------- Lanczos
+@pytest.mark.parametrize("n,k", [(300, 10), (300, 40), (513, 20)])
+def test_lanczos_matches_oracle(ctx, n, k):
+    rng = _rng(k)
+    lam = np.sort(rng.uniform(-1, 5, n))
+    Q, _ = np.linalg.qr(_cgauss(rng, n, n))
+    H = (Q * lam) @ Q.conj().T
+    H = 0.5 * (H + H.conj().T)
+    v0 = _cgauss(rng, n)
+    up, tmin, tmax = cb.chfsi_lanczos(ctx, _t(H), k, _t(v0))
+    up_o, tmin_o, a, bta = O.lanczos(H, v0, k)
+    assert abs(up - up_o) < 1e-10 * abs(up_o)
+    assert abs(tmin - tmin_o) < 1e-10 * max(1, abs(tmin_o))
+    assert up >= lam[-1] - 1e-12
+
+
+def test_lanczos_default_start_vector_is_splitmix(ctx):
+    n = 200
+    rng = _rng(9)
+    H = _herm(rng, n)
+    up, tmin, _ = cb.chfsi_lanczos(ctx, _t(H), 12, None)
+    up_o, tmin_o, _, _ = O.lanczos(H, O.lanczos_start_vector(n, 12063768), 12)
+    assert abs(up - up_o) < 1e-11 * abs(up_o)
+
+
+# ---------------------------------------------------------------------------- filter
+@pytest.mark.parametrize("n,m", [(300, 30), (513, 17), (640, 130)])
+def test_filter_matches_oracle_per_column_degrees(ctx, n, m):
+    rng = _rng(n + m)
+    lam = np.sort(rng.uniform(-2, 2, n))
+    Q, _ = np.linalg.qr(_cgauss(rng, n, n))
+    H = (Q * lam) @ Q.conj().T
+    H = 0.5 * (H + H.conj().T)
+    Y = _cgauss(rng, n, m)
+    degs = rng.integers(0, 26, m)
+    degs[0] = 25
+    a0, a, b = lam[0], lam[m + 5], lam[-1] + 0.01
+    got = _np(cb.chfsi_filter(ctx, _t(H), _t(Y), degs, a0, a, b))
+    ref = O.chebyshev_filter(H, Y, degs, a0, a, b)
+    for j in range(m):
+        assert np.max(np.abs(got[:, j] - ref[:, j])) <= 1e-11 * np.max(np.abs(ref[:, j])), j
+
+
+def test_filter_fixed_degree_closed_form(ctx):
+    n, m, d = 400, 24, 11
+    rng = _rng(77)
+    lam = np.sort(rng.uniform(-1, 3, n))
+    Q, _ = np.linalg.qr(_cgauss(rng, n, n))
+    H = (Q * lam) @ Q.conj().T
+    H = 0.5 * (H + H.conj().T)
+    a0, a, b = lam[0], lam[40], lam[-1] + 0.05
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    X = Q[:, :m]
+    got = _np(cb.chfsi_filter(ctx, _t(H), _t(X), [d] * m, a0, a, b))
+    p = O.chebyshev_T(d, (lam[:m] - c) / e) / O.chebyshev_T(d, np.array([(a0 - c) / e]))[0]
+    assert np.max(np.abs(got - X * p[None, :])) < 1e-11
+
+
+# ---------------------------------------------------------------------------- QR, RR
+@pytest.mark.parametrize("n,m,k", [(300, 20, 0), (513, 40, 12), (640, 130, 30)])
+def test_orthonormalize_matches_oracle_span(ctx, n, m, k):
+    rng = _rng(n + m + k)
+    YL = np.linalg.qr(_cgauss(rng, n, k))[0] if k else None
+    # an ill-conditioned block (column scales spread over 1e6, as after filtering)
+    Y = _cgauss(rng, n, m) * np.logspace(0, -6, m)[None, :]
+    got = _np(cb.chfsi_orthonormalize(ctx, _t(Y), _t(YL) if k else None))
+    ref = O.orthonormalize(Y, YL)
+    assert np.max(np.abs(got.conj().T @ got - np.eye(m))) < 1e-13
+    if k:
+        assert np.max(np.abs(YL.conj().T @ got)) < 1e-13
+    assert np.linalg.norm(got @ got.conj().T - ref @ ref.conj().T) < 1e-9
+
+
+def test_orthonormalize_survives_near_rank_deficiency(ctx):
+    """A Gram matrix beyond plain Cholesky QR takes the shifted path."""
+    n, m = 400, 16
+    rng = _rng(5)
+    base = _cgauss(rng, n, m)
+    Y = base.copy()
+    Y[:, 5] = base[:, 4] + 1e-9 * _cgauss(rng, n)
+    got = _np(cb.chfsi_orthonormalize(ctx, _t(Y)))
+    assert np.max(np.abs(got.conj().T @ got - np.eye(m))) < 1e-12
+
+
+@pytest.mark.parametrize("n,m", [(300, 25), (640, 130), (513, 131)])
+def test_rayleigh_ritz_matches_oracle(ctx, n, m):
+    rng = _rng(n * m)
+    lam = np.sort(rng.uniform(-1, 4, n))
+    Q, _ = np.linalg.qr(_cgauss(rng, n, n))
+    H = (Q * lam) @ Q.conj().T
+    H = 0.5 * (H + H.conj().T)
+    S = np.linalg.qr(Q[:, :m] + 1e-3 * _cgauss(rng, n, m))[0]
+    theta, Y, HY = cb.chfsi_rayleigh_ritz(ctx, _t(H), _t(S))
+    th_o, Y_o, W_o = O.rayleigh_ritz(H, S)
+    theta, Y, HY = _np(theta), _np(Y), _np(HY)
+    assert np.max(np.abs(theta - th_o)) < 1e-12 * np.max(np.abs(lam))
+    assert np.max(np.abs(HY - H @ Y)) < 1e-12 * np.max(np.abs(lam))
+    assert np.max(np.abs(Y.conj().T @ Y - np.eye(m))) < 1e-12
+    # Ritz vectors agree up to phase where the Ritz values are separated
+    gaps = np.minimum(np.diff(np.r_[-np.inf, th_o]), np.diff(np.r_[th_o, np.inf]))
+    ov = np.abs(np.sum(Y.conj() * Y_o, axis=0))
+    assert np.all(np.abs(ov[gaps > 1e-6] - 1) < 1e-8)
+    r = _np(cb.chfsi_residuals(ctx, _t(HY), _t(Y), _t(theta)))
+    r_o = O.residual_norms(H @ Y, Y, theta)
+    assert np.max(np.abs(r - r_o)) < 1e-12 * np.max(np.abs(lam))
+
+
+@pytest.mark.parametrize("m", [1, 2, 7, 64, 130, 131, 160])
+def test_heev_matches_lapack(ctx, m):
+    rng = _rng(m + 100)
+    G = _herm(rng, m, 2.0)
+    w, V = cb.chfsi_heev(ctx, _t(G))
+    w, V = _np(w), _np(V)
+    w_ref = np.linalg.eigvalsh(G)
+    nrm = np.linalg.norm(G, 2)
+    assert np.max(np.abs(w - w_ref)) < 1e-13 * nrm * max(1, math.sqrt(m))
+    assert np.max(np.abs(V.conj().T @ V - np.eye(m))) < 1e-13 * max(1, math.sqrt(m))
+    assert np.max(np.abs(G @ V - V * w[None, :])) < 1e-13 * nrm * max(1, math.sqrt(m))
+
+
+def test_heev_clustered_spectrum(ctx):
+    m = 48
+    rng = _rng(4)
+    lam = np.r_[np.full(10, -1.0) + 1e-12 * rng.standard_normal(10), np.linspace(0, 3, 38)]
+    U = np.linalg.qr(_cgauss(rng, m, m))[0]
+    G = (U * lam) @ U.conj().T
+    G = 0.5 * (G + G.conj().T)
+    w, V = cb.chfsi_heev(ctx, _t(G))
+    w, V = _np(w), _np(V)
+    assert np.max(np.abs(w - np.sort(lam))) < 1e-13
+    assert np.max(np.abs(G @ V - V * w[None, :])) < 1e-13
+
+
+# ---------------------------------------------------------------------------- degrees
+def test_degrees_bit_exact_with_oracle(ctx):
+    rng = _rng(11)
+    m = 130
+    a, b = -0.5, 30.0
+    theta = np.sort(np.r_[rng.uniform(-1.0, -0.55, 100), rng.uniform(-0.55, 2.0, 30)])
+    r = 10.0 ** rng.uniform(-12, -1, m)
+    tau = 1e-10
+    for nw in (0, 37, 100, 130):
+        got = _np(cb.chfsi_degrees(ctx, _t(theta), _t(r), a, b, tau, 8, 25, nw))
+        ref = O.adaptive_degrees(theta, r, a, b, tau, 8, 25, nw)
+        assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------------------- whole solve
+def _check_solution(p, lam, X, nev, tol=1e-10):
+    A, B = p.A.numpy(), p.B.numpy()
+    a2 = np.linalg.norm(A, 2)
+    scale = max(np.max(np.abs(p.lam)), 1.0)
+    err = np.max(np.abs(lam - p.lam[:nev]) / np.maximum(np.abs(p.lam[:nev]), scale))
+    assert err <= tol, err
+    R = A @ X - (B @ X) * lam[None, :]
+    res = np.linalg.norm(R, axis=0) / (a2 * np.linalg.norm(X, axis=0))
+    assert res.max() <= tol, res.max()
+    assert np.max(np.abs(X.conj().T @ B @ X - np.eye(nev))) < 1e-10
+
+
+def test_solve_sequence_c1_matches_oracle_and_planted_spectrum(ctx):
+    seq = inputs.planted_sequence("c1")
+    As = [torch.tril(p.A).to(DEV) for p in seq.problems]
+    Bs = [torch.tril(p.B).to(DEV) for p in seq.problems]
+    cb.chfsi_reset_warm_state(ctx)
+    evals, evecs, stats = cb.chfsi_solve_sequence(ctx, As, Bs, seq.nev, seq.blk, seq.deg, 1e-10)
+    ref = O.chfsi_solve_sequence([np.tril(p.A.numpy()) for p in seq.problems],
+                                 [np.tril(p.B.numpy()) for p in seq.problems],
+                                 seq.nev, seq.blk, 1e-10, deg=seq.deg)
+    for ell, p in enumerate(seq.problems):
+        lam = evals[ell].numpy()
+        X = _np(evecs[ell])
+        _check_solution(p, lam, X, seq.nev)
+        w_def, _ = O.definition_eigenpairs(np.tril(p.A.numpy()), np.tril(p.B.numpy()), seq.nev)
+        assert np.max(np.abs(lam - w_def)) < 1e-10 * max(1, np.max(np.abs(w_def)))
+        lam_o, _, st_o = ref[ell]
+        assert np.max(np.abs(lam - lam_o)) < 1e-10 * max(1, np.max(np.abs(lam_o)))
+        assert abs(stats[ell]["loops"] - st_o.loops) <= 1
+        assert stats[ell]["converged"] == seq.nev
+
+
+def test_solve_adaptive_ill_conditioned_overlap(ctx):
+    seq = inputs.planted_sequence("c2", n=520, N=3, nev=20, blk=26)
+    cb.chfsi_reset_warm_state(ctx)
+    for p in seq.problems:
+        lam, X, st = cb.chfsi_solve_next(ctx, torch.tril(p.A).to(DEV), torch.tril(p.B).to(DEV),
+                                         20, 26, 0, 1e-10)
+        _check_solution(p, lam.cpu().numpy(), _np(X), 20)
+        assert st["max_resid"] <= 1e-10
+
+
+def test_host_pointers_give_the_device_result(ctx):
+    seq = inputs.planted_sequence("c1", n=256, N=1, nev=10, blk=16)
+    p = seq.problems[0]
+    cb.chfsi_reset_warm_state(ctx)
+    lam_d, X_d, _ = cb.chfsi_solve_next(ctx, p.A.to(DEV), p.B.to(DEV), 10, 16, 10)
+    cb.chfsi_reset_warm_state(ctx)
+    lam_h, X_h, _ = cb.chfsi_solve_next(ctx, p.A.clone(), p.B.clone(), 10, 16, 10, out_device="cpu")
+    assert torch.equal(lam_d.cpu(), lam_h)
+    assert torch.equal(X_d.cpu(), X_h)
+
+
+def test_cold_start_with_caller_block(ctx):
+    seq = inputs.planted_sequence("c1", n=300, N=1, nev=12, blk=20)
+    p = seq.problems[0]
+    V0 = inputs.gaussian_block(300, 20, 5)
+    cb.chfsi_reset_warm_state(ctx)
+    lam, X, st = cb.chfsi_solve_next(ctx, p.A.to(DEV), p.B.to(DEV), 12, 20, 10, V0=V0.to(DEV))
+    _check_solution(p, lam.cpu().numpy(), _np(X), 12)
+    lam_o, _, _, st_o = O.chfsi_solve(np.tril(p.A.numpy()), np.tril(p.B.numpy()), 12, 20, deg=10,
+                                      V0=V0.numpy())
+    assert np.max(np.abs(lam.cpu().numpy() - lam_o)) < 1e-10
+    assert abs(st["loops"] - st_o.loops) <= 1
+
+
+def test_invalid_arguments_are_reported(ctx):
+    seq = inputs.planted_sequence("c1", n=64, N=1, nev=4, blk=8)
+    p = seq.problems[0]
+    A, B = p.A.to(DEV), p.B.to(DEV)
+    with pytest.raises(cb.ChfsiError) as ei:
+        cb.chfsi_solve_next(ctx, A, B, 8, 4, 10)  # blk < nev
+    assert ei.value.code == cb.CHFSI_EINVAL
+    An = A.clone()
+    An[10, 3] = float("nan")
+    cb.chfsi_reset_warm_state(ctx)
+    with pytest.raises(cb.ChfsiError) as ei:
+        cb.chfsi_solve_next(ctx, An, B, 4, 8, 10)
+    assert ei.value.code == cb.CHFSI_EINVAL
+    Bn = -torch.eye(64, dtype=torch.complex128, device=DEV)
+    cb.chfsi_reset_warm_state(ctx)
+    with pytest.raises(cb.ChfsiError) as ei:
+        cb.chfsi_solve_next(ctx, A, Bn, 4, 8, 10)
+    assert ei.value.code == cb.CHFSI_ENOTPD
+    # still usable afterwards
+    cb.chfsi_reset_warm_state(ctx)
+    lam, X, st = cb.chfsi_solve_next(ctx, A, B, 4, 8, 10)
+    _check_solution(p, lam.cpu().numpy(), _np(X), 4)

@@ -65,6 +65,8 @@ typedef struct {
   int32_t converged;         /* locked pairs returned */
   int32_t accept_rounds;     /* times the locking threshold was tightened */
   int64_t matvecs;           /* column products Hs*y (filter + Rayleigh-Ritz + Lanczos) */
+  int64_t filter_matvecs;    /* column products Hs*y inside the Chebyshev filter only */
+  int64_t launches;          /* CUDA kernels launched by the library for this problem */
   double max_resid;          /* max_i ||A x_i - lambda_i B x_i|| / (||A||_est ||x_i||) */
   double lanczos_upper;      /* spectral upper bound b used by the filter */
   double t_reduce_ms, t_lanczos_ms, t_filter_ms, t_qr_ms, t_rr_ms, t_resid_ms, t_total_ms;

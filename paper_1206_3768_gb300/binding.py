@@ -37,7 +37,8 @@ class chfsi_opts(ctypes.Structure):
 
 class chfsi_stats(ctypes.Structure):
     _fields_ = [("loops", c_int32), ("filtered_vectors", c_int32), ("converged", c_int32),
-                ("accept_rounds", c_int32), ("matvecs", c_int64), ("max_resid", c_double),
+                ("accept_rounds", c_int32), ("matvecs", c_int64), ("filter_matvecs", c_int64),
+                ("launches", c_int64), ("max_resid", c_double),
                 ("lanczos_upper", c_double), ("t_reduce_ms", c_double), ("t_lanczos_ms", c_double),
                 ("t_filter_ms", c_double), ("t_qr_ms", c_double), ("t_rr_ms", c_double),
                 ("t_resid_ms", c_double), ("t_total_ms", c_double)]

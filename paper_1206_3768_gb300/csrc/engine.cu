@@ -17,6 +17,8 @@
 
 #include "internal.cuh"
 
+thread_local long long g_kernel_launches = 0;
+
 struct chfsi_ctx {
   Workspace ws;
   chfsi_opts opts;
@@ -409,6 +411,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
     return set_err(ctx, CHFSI_EINVAL, "bad adaptive degree range [%d, %d]", o.deg_min, o.deg_max);
   if (!(S.tol > 0.0)) return set_err(ctx, CHFSI_EINVAL, "tol must be positive");
   CKS(reset_status(ctx));
+  const long long launches0 = g_kernel_launches;
   cudaEvent_t t_start = next_event(ctx), t_end = next_event(ctx);
   CK(cudaEventRecord(t_start, ctx->stream));
 
@@ -531,7 +534,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       {
         PhaseScope ps(ctx, PH_FILTER);
         CKS(filter_block(ctx, ws.Hs, ld, n, m, &Ya, &Yb, &Yf, degs, perm_dev, a0, a, b_up,
-                         &st.matvecs));
+                         &st.filter_matvecs));
       }
       st.filtered_vectors += m;
       // ---- a5: deflation + Cholesky QR
@@ -662,6 +665,8 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   cudaEventElapsedTime(&tot, t_start, t_end);
   collect_times(ctx, tph);
   st.converged = conv;
+  st.matvecs += st.filter_matvecs;
+  st.launches = g_kernel_launches - launches0;
   st.max_resid = max_gres;
   st.t_reduce_ms = tph[PH_REDUCE];
   st.t_lanczos_ms = tph[PH_LANCZOS];

@@ -207,6 +207,7 @@ cudaError_t zgemm_run(const GemmDesc& g, Workspace& ws, cudaStream_t stream) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (g.K <= 0) {
     zgemm_k0<<<std::min<int64_t>(1024, ((int64_t)g.M * g.N + 255) / 256), 256, 0, stream>>>(g);
+    CHFSI_COUNT_LAUNCH();
     return cudaGetLastError();
   }
   Params p;
@@ -233,12 +234,14 @@ cudaError_t zgemm_run(const GemmDesc& g, Workspace& ws, cudaStream_t stream) {
   else if (g.opA == OPN && g.opB == OPC) zgemm3m_kernel<OPN, OPC><<<grid, NT, 0, stream>>>(p);
   else if (g.opA == OPC && g.opB == OPN) zgemm3m_kernel<OPC, OPN><<<grid, NT, 0, stream>>>(p);
   else zgemm3m_kernel<OPC, OPC><<<grid, NT, 0, stream>>>(p);
+  CHFSI_COUNT_LAUNCH();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (p.splits > 1) {
     const int64_t total = (int64_t)g.M * g.N;
     const int blocks = (int)std::min<int64_t>(4 * sm_count(), (total + 255) / 256);
     zgemm_splitk_epilogue<<<blocks, 256, 0, stream>>>(p);
+    CHFSI_COUNT_LAUNCH();
     e = cudaGetLastError();
   }
   return e;

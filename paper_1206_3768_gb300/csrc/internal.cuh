@@ -11,6 +11,10 @@
 
 typedef double2 zd;  // complex double: x = real part, y = imaginary part
 
+// Kernels launched by this library on the calling host thread (statistics only).
+extern thread_local long long g_kernel_launches;
+#define CHFSI_COUNT_LAUNCH() (++g_kernel_launches)
+
 #define CHFSI_HD __host__ __device__ __forceinline__
 
 CHFSI_HD zd zmk(double r, double i) { return make_double2(r, i); }

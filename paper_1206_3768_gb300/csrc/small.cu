@@ -382,6 +382,7 @@ cudaError_t small_cholesky(zd* G, int64_t ldg, int m, int scale, int shift_on_fa
   if (m <= 0) return cudaSuccess;
   cholesky_kernel<<<1, 1024, 0, s>>>(G, ldg, m, scale, shift_on_fail, shift_base, dscale, backup,
                                      status, info, info_base);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -391,6 +392,7 @@ cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m,
   const int warps = 8;
   const int blocks = (m + warps - 1) / warps;
   trinv_lower_kernel<<<blocks, 32 * warps, 0, s>>>(L, ldl, X, ldx, m);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -400,6 +402,7 @@ cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* 
   const int64_t tot = (int64_t)m * m;
   cholqr_T_kernel<<<(int)std::min<int64_t>(1024, (tot + 255) / 256), 256, 0, s>>>(X, ldx, m, dscale,
                                                                                    T, ldt);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
@@ -425,6 +428,7 @@ cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64
   }
   void* args[] = {(void*)&P};
   e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(half), dim3(128), args, smem, s);
+  CHFSI_COUNT_LAUNCH();
   if (e != cudaSuccess) return e;
   const size_t smem2 = (size_t)m * (sizeof(double) + sizeof(int));
   if (smem2 > 48 * 1024) {
@@ -433,5 +437,6 @@ cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64
     if (e != cudaSuccess) return e;
   }
   jacobi_finish_kernel<<<1, 1024, smem2, s>>>(P.Ga, P.Gb, P.Vw, barrier, m, mp, w, V, ldv);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -383,46 +383,54 @@ cudaError_t herm_from_lower(const zd* src, int64_t lds, zd* dst, int64_t ldd, in
   if (n <= 0) return cudaSuccess;
   const int nb = (n + TILE - 1) / TILE;
   herm_from_lower_kernel<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(src, lds, dst, ldd, n, status);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t mirror_lower(zd* H, int64_t ldh, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int nb = (n + TILE - 1) / TILE;
   mirror_lower_kernel<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(H, ldh, n);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t zero_upper(zd* L, int64_t ldl, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   zero_upper_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(L, ldl, n);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t copy_cols(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m, cudaStream_t s) {
   if (n <= 0 || m <= 0) return cudaSuccess;
   copy_cols_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(src, lds, dst, ldd, n, m, nullptr, nullptr);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t gather_cols(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m,
                         const int* perm, cudaStream_t s) {
   if (n <= 0 || m <= 0) return cudaSuccess;
   copy_cols_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(src, lds, dst, ldd, n, m, perm, nullptr);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t select_cols(const zd* src1, int64_t ld1, zd* dst, int64_t ldd, int n, int m,
                         const int* flag, cudaStream_t s) {
   if (n <= 0 || m <= 0) return cudaSuccess;
   copy_cols_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(src1, ld1, dst, ldd, n, m, nullptr, flag);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t compare_equal(const zd* a, int64_t lda, const zd* b, int64_t ldb, int n, int m,
                           int* diff_flag, cudaStream_t s) {
   if (n <= 0 || m <= 0) return cudaSuccess;
   compare_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(a, lda, b, ldb, n, m, diff_flag);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t column_residuals(const zd* HY, int64_t ldhy, const zd* Y, int64_t ldy,
                              const double* theta, int n, int m, double* r, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   column_residuals_kernel<<<m, 256, 0, s>>>(HY, ldhy, Y, ldy, theta, n, r);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t generalized_residuals(const zd* AX, int64_t ldax, const zd* BX, int64_t ldbx,
@@ -430,15 +438,18 @@ cudaError_t generalized_residuals(const zd* AX, int64_t ldax, const zd* BX, int6
                                   const double* a_norm, double* r, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   gen_residuals_kernel<<<m, 256, 0, s>>>(AX, ldax, BX, ldbx, X, ldx, lam, n, a_norm, r);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t splitmix_start_vector(zd* v, int n, uint64_t seed, cudaStream_t s) {
   start_vector_kernel<<<grid_for(n), 256, 0, s>>>(v, n, (unsigned long long)seed);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t splitmix_gaussian_block(zd* Y, int64_t ldy, int n, int m, uint64_t seed, cudaStream_t s) {
   gaussian_block_kernel<<<grid_for((int64_t)n * m), 256, 0, s>>>(Y, ldy, n, m,
                                                                  (unsigned long long)seed);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, double a, double b,
@@ -447,46 +458,56 @@ cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, doub
   if (m <= 0) return cudaSuccess;
   degrees_kernel<<<1, 1024, m * sizeof(int), s>>>(theta, r, m, a, b, tau, dmin, dmax, n_wanted,
                                                   deg, perm_desc, deg_sorted);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t lock_scan(const double* r, int m, double tau, int max_lock, int* nlock, cudaStream_t s) {
   lock_scan_kernel<<<1, 32, 0, s>>>(r, m, tau, max_lock, nlock);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t fill_nan(double* x, int m, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   fill_nan_kernel<<<grid_for(m), 256, 0, s>>>(x, m);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s) {
   const int warps_per_block = 8;
   const int blocks = std::max(1, std::min((n + warps_per_block - 1) / warps_per_block, 16 * sm_count()));
   hemv_rows_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(H, ldh, v, w, n);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t block_dots(const zd* V, int64_t ldv, int j, const zd* w, int n, zd* c, cudaStream_t s) {
   block_dots_kernel<<<j + 1, 256, 0, s>>>(V, ldv, w, n, c);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t block_update(const zd* V, int64_t ldv, int j, const zd* c, zd* w, int n, cudaStream_t s) {
   block_update_kernel<<<grid_for(n), 256, 0, s>>>(V, ldv, j + 1, c, w, n);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t vec_norm(const zd* w, int n, double* out, cudaStream_t s) {
   vec_norm_kernel<<<1, 1024, 0, s>>>(w, n, out);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t vec_scale_into(const zd* w, int n, const double* nrm, zd* dst, cudaStream_t s) {
   vec_scale_into_kernel<<<grid_for(n), 256, 0, s>>>(w, n, nrm, dst);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t lanczos_record(const zd* c, int j, const double* nrm, double* alpha, double* beta,
                            cudaStream_t s) {
   lanczos_record_kernel<<<1, 32, 0, s>>>(c, j, nrm, alpha, beta);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 cudaError_t tridiag_extremes(const double* alpha, const double* beta, int k, double* out3,
                              cudaStream_t s) {
   tridiag_extremes_kernel<<<1, 32, 0, s>>>(alpha, beta, k, out3);
+  CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

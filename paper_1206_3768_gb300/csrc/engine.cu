@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -108,6 +109,7 @@ void collect_times(chfsi_ctx* ctx, double* t) {
   for (auto& m : ctx->marks) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) t[m.phase] += ms;
+    else cudaGetLastError();
   }
   ctx->marks.clear();
   ctx->ev_used = 0;
@@ -143,6 +145,15 @@ int check_status(chfsi_ctx* ctx, const char* where) {
   if (st[0] & DEV_NOCONV)
     return set_err(ctx, CHFSI_ENOCONV, "%s: Jacobi eigensolver reached its sweep limit", where);
   return set_err(ctx, CHFSI_ECUDA, "%s: device status %d", where, st[0]);
+}
+
+// Every public entry point starts by clearing the runtime's last-error slot, so that a
+// non-sticky error left by an earlier, unrelated call is not reported as this call's
+// failure.  With CHFSI_DEBUG set, such stale errors are printed to stderr.
+void entry_guard(const char* fn) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess && std::getenv("CHFSI_DEBUG"))
+    std::fprintf(stderr, "[chfsi] stale CUDA error '%s' at entry of %s\n", cudaGetErrorString(e), fn);
 }
 
 int gemm(chfsi_ctx* ctx, const GemmDesc& g) {
@@ -755,6 +766,7 @@ int chfsi_create(chfsi_ctx** out, int64_t n_max, int32_t blk_max, const chfsi_op
   *out = nullptr;
   if (n_max <= 0 || blk_max <= 0 || blk_max > n_max || n_max > (int64_t)1 << 30)
     return CHFSI_EINVAL;
+  entry_guard("chfsi_create");
   chfsi_ctx* ctx = new chfsi_ctx;
   chfsi_default_opts(&ctx->opts);
   if (opts) ctx->opts = *opts;
@@ -785,6 +797,7 @@ int chfsi_create(chfsi_ctx** out, int64_t n_max, int32_t blk_max, const chfsi_op
 }
 
 void chfsi_destroy(chfsi_ctx* ctx) {
+  entry_guard("chfsi_destroy");
   if (!ctx) return;
   cudaSetDevice(ctx->ws.dev);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -807,6 +820,7 @@ int chfsi_reset_warm_state(chfsi_ctx* ctx) {
 int chfsi_solve_next(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const chfsi_z* B,
                      int64_t ldb, const chfsi_z* V0, int32_t nev, int32_t blk, int32_t deg,
                      double tol, double* evals, chfsi_z* evecs, chfsi_stats* st) {
+  entry_guard("chfsi_solve_next");
   CKS(validate_sizes(ctx, n, nev, blk));
   if (!A || !B || lda < n || ldb < n) return set_err(ctx, CHFSI_EINVAL, "bad A/B arguments");
   if (deg < 0) return set_err(ctx, CHFSI_EINVAL, "deg must be >= 0");
@@ -833,6 +847,7 @@ int chfsi_solve_sequence(chfsi_ctx* ctx, int32_t N, int64_t n, const chfsi_z* co
 // ---------------------------------------------------------------- step entry points
 int chfsi_cholesky(chfsi_ctx* ctx, int64_t n, const chfsi_z* B, int64_t ldb, chfsi_z* L,
                    int64_t ldl) {
+  entry_guard("chfsi_cholesky");
   if (!ctx || !B || !L || n <= 0 || ldb < n || ldl < n) return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (n > ctx->ws.n_max) return set_err(ctx, CHFSI_EINVAL, "n > n_max");
   cudaSetDevice(ctx->ws.dev);
@@ -846,6 +861,7 @@ int chfsi_cholesky(chfsi_ctx* ctx, int64_t n, const chfsi_z* B, int64_t ldb, chf
 
 int chfsi_reduce(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const chfsi_z* L,
                  int64_t ldl, chfsi_z* Hs, int64_t ldh) {
+  entry_guard("chfsi_reduce");
   if (!ctx || !A || !L || !Hs || n <= 0 || lda < n || ldl < n || ldh < n)
     return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (n > ctx->ws.n_max) return set_err(ctx, CHFSI_EINVAL, "n > n_max");
@@ -862,6 +878,7 @@ int chfsi_reduce(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const
 
 int chfsi_lanczos(chfsi_ctx* ctx, int64_t n, const chfsi_z* H, int64_t ldh, int32_t k,
                   const chfsi_z* v0, double* upper, double* theta_min, double* theta_max) {
+  entry_guard("chfsi_lanczos");
   if (!ctx || !H || n <= 0 || ldh < n || k <= 0) return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (n > ctx->ws.n_max) return set_err(ctx, CHFSI_EINVAL, "n > n_max");
   if (k > ctx->ws.lanczos_kmax)
@@ -879,6 +896,7 @@ int chfsi_lanczos(chfsi_ctx* ctx, int64_t n, const chfsi_z* H, int64_t ldh, int3
 
 int chfsi_filter(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh, chfsi_z* Y,
                  int64_t ldy, const int32_t* degrees, double a0, double a, double b) {
+  entry_guard("chfsi_filter");
   if (!ctx || !H || !Y || !degrees || n <= 0 || m <= 0 || ldh < n || ldy < n)
     return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (n > ctx->ws.n_max || m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "size > workspace");
@@ -909,6 +927,7 @@ int chfsi_filter(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t
 
 int chfsi_orthonormalize(chfsi_ctx* ctx, int64_t n, int32_t m, chfsi_z* Y, int64_t ldy, int32_t k,
                          const chfsi_z* YL, int64_t ldyl) {
+  entry_guard("chfsi_orthonormalize");
   if (!ctx || !Y || n <= 0 || m <= 0 || ldy < n || k < 0 || (k > 0 && (!YL || ldyl < n)))
     return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (n > ctx->ws.n_max || m > ctx->ws.blk_max || k > ctx->ws.blk_max || m + k > n)
@@ -929,6 +948,7 @@ int chfsi_orthonormalize(chfsi_ctx* ctx, int64_t n, int32_t m, chfsi_z* Y, int64
 
 int chfsi_rayleigh_ritz(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,
                         chfsi_z* Y, int64_t ldy, chfsi_z* HY, int64_t ldhy, double* theta) {
+  entry_guard("chfsi_rayleigh_ritz");
   if (!ctx || !H || !Y || !HY || !theta || n <= 0 || m <= 0 || ldh < n || ldy < n || ldhy < n)
     return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (n > ctx->ws.n_max || m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "size > workspace");
@@ -950,6 +970,7 @@ int chfsi_rayleigh_ritz(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, 
 
 int chfsi_residuals(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* HY, int64_t ldhy,
                     const chfsi_z* Y, int64_t ldy, const double* theta, double* r) {
+  entry_guard("chfsi_residuals");
   if (!ctx || !HY || !Y || !theta || !r || n <= 0 || m <= 0 || ldhy < n || ldy < n)
     return set_err(ctx, CHFSI_EINVAL, "bad args");
   cudaSetDevice(ctx->ws.dev);
@@ -961,6 +982,7 @@ int chfsi_residuals(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* HY, int
 int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* r, double a,
                   double b, double tau, int32_t dmin, int32_t dmax, int32_t n_wanted,
                   int32_t* degrees) {
+  entry_guard("chfsi_degrees");
   if (!ctx || !theta || !r || !degrees || m <= 0 || dmin < 0 || dmax < dmin || !(b > a) || n_wanted < 0)
     return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "m > blk_max");
@@ -973,6 +995,7 @@ int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* 
 
 int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double* w, chfsi_z* V,
                int64_t ldv) {
+  entry_guard("chfsi_heev");
   if (!ctx || !G || !w || !V || m <= 0 || ldg < m || ldv < m) return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "m > blk_max");
   cudaSetDevice(ctx->ws.dev);
@@ -986,6 +1009,7 @@ int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double*
 int chfsi_zgemm(chfsi_ctx* ctx, char opa, char opb, int32_t M, int32_t N, int32_t K, double alpha,
                 const chfsi_z* A, int64_t lda, const chfsi_z* B, int64_t ldb, double beta,
                 chfsi_z* C, int64_t ldc) {
+  entry_guard("chfsi_zgemm");
   if (!ctx || !C || M < 0 || N < 0 || K < 0 || (K > 0 && (!A || !B)))
     return set_err(ctx, CHFSI_EINVAL, "bad args");
   const int oA = (opa == 'C' || opa == 'c') ? OPC : OPN;

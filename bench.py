@@ -311,6 +311,32 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kernel_case(args):
+    """One Chebyshev filter call (deg launches of the filter GEMM) through the C ABI on a
+    seeded n x n Hermitian matrix and n x m block: the small case used for kernel profiles."""
+    from paper_1206_3768_gb300 import binding as cb
+
+    dev = torch.device("cuda:0")
+    g = torch.Generator(device="cpu").manual_seed(1206)
+    n, m = args.case_n, args.case_m
+    M = torch.randn(n, n, dtype=torch.complex128, generator=g)
+    H = (0.5 * (M + M.mH) / math.sqrt(n)).to(dev)
+    Y = torch.randn(n, m, dtype=torch.complex128, generator=g).to(dev)
+    with cb.Solver(n, m) as s:
+        for _ in range(args.case_reps):
+            out = cb.chfsi_filter(s.ctx, H, Y, [args.case_deg] * m, -2.0, -1.0, 2.5)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        out = cb.chfsi_filter(s.ctx, H, Y, [args.case_deg] * m, -2.0, -1.0, 2.5)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    flops = 8.0 * n * n * m * args.case_deg
+    print(json.dumps({"case": "filter", "n": n, "m": m, "deg": args.case_deg, "ms": ms,
+                      "tflops": flops / ms / 1e9, "finite": bool(torch.isfinite(out).all())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,8 +346,15 @@ def main():
     ap.add_argument("--cpu-problems", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kernel-case", choices=["filter"], default=None)
+    ap.add_argument("--case-n", type=int, default=4096)
+    ap.add_argument("--case-m", type=int, default=128)
+    ap.add_argument("--case-deg", type=int, default=3)
+    ap.add_argument("--case-reps", type=int, default=1)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.kernel_case:
+        run_kernel_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -690,8 +690,13 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   return status;
 }
 
+void debug_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess && std::getenv("CHFSI_DEBUG"))
+    std::fprintf(stderr, "[chfsi] %s: %s\n", what, cudaGetErrorString(e));
+}
+
 void release_stream(chfsi_ctx* ctx) {
-  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->own_stream && ctx->stream) debug_check(cudaStreamDestroy(ctx->stream), "cudaStreamDestroy");
   ctx->stream = nullptr;
 }
 
@@ -742,7 +747,7 @@ void workspace_free(Workspace& ws) {
                   ws.scal, ws.lal, ws.lbe, ws.deg, ws.perm, ws.degs, ws.flag, ws.ilist,
                   ws.status, ws.status + 1, ws.barrier, ws.splitk};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) debug_check(cudaFree(p), "cudaFree");
   ws = Workspace{};
 }
 
@@ -799,12 +804,13 @@ int chfsi_create(chfsi_ctx** out, int64_t n_max, int32_t blk_max, const chfsi_op
 void chfsi_destroy(chfsi_ctx* ctx) {
   entry_guard("chfsi_destroy");
   if (!ctx) return;
-  cudaSetDevice(ctx->ws.dev);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  debug_check(cudaSetDevice(ctx->ws.dev), "cudaSetDevice");
+  if (ctx->stream) debug_check(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  for (auto e : ctx->ev_pool) debug_check(cudaEventDestroy(e), "cudaEventDestroy");
   workspace_free(ctx->ws);
   release_stream(ctx);
   delete ctx;
+  cudaGetLastError();
 }
 
 const char* chfsi_last_error(const chfsi_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }

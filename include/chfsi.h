@@ -172,6 +172,27 @@ int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* 
 int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double* w,
                chfsi_z* V, int64_t ldv);
 
+/* ---------------------------------------------------------------- allocation-free variant
+ * The paper has no counterpart to this entry point; it serves callers that cannot call
+ * cudaMalloc (an application whose pool allocator owns all device memory, or a
+ * latency-critical path that must not trigger the implicit synchronisation of
+ * cudaMalloc/cudaFree) and therefore cannot create a context.
+ * Same computation as chfsi_heev (ascending eigenvalues w and orthonormal eigenvectors V of
+ * the m x m Hermitian G, device pointers) with no context and no allocation: the scratch is
+ * a fixed file-scope device array of 786,688 bytes that every GPU loading the library holds
+ * until the process exits, so m is limited to CHFSI_HEEV_NOALLOC_MAX.
+ *   cuda_stream  cudaStream_t to run on (NULL = the legacy default stream); the call
+ *                synchronises it before returning.
+ * All calls share the one array: calls that overlap on the GPU (several streams or host
+ * threads at once) race and must be serialised by the caller.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.
+ * Errors: EINVAL (m > CHFSI_HEEV_NOALLOC_MAX, m <= 0, NULL, ld < m), ECUDA, ETIMEOUT,
+ *         ENOCONV. */
+#define CHFSI_HEEV_NOALLOC_MAX 128
+int chfsi_heev_noalloc(int32_t m, const chfsi_z* G, int64_t ldg, double* w, chfsi_z* V,
+                       int64_t ldv, void* cuda_stream);
+
 /* Complex FP64 GEMM used by every dense step, exposed for testing:
  * C <- alpha op(A) op(B) + beta C, op = 'N' (as stored) or 'C' (conjugate transpose);
  * C is M x N, op(A) M x K, op(B) K x N.  alpha, beta real. */

@@ -71,6 +71,7 @@ _SIGS = {
     "chfsi_degrees": (c_int32, [_P, c_int32, _P, _P, c_double, c_double, c_double, c_int32,
                                 c_int32, c_int32, _P]),
     "chfsi_heev": (c_int32, [_P, c_int32, _P, c_int64, _P, _P, c_int64]),
+    "chfsi_heev_noalloc": (c_int32, [c_int32, _P, c_int64, _P, _P, c_int64, _P]),
     "chfsi_zgemm": (c_int32, [_P, c_char, c_char, c_int32, c_int32, c_int32, c_double, _P, c_int64,
                               _P, c_int64, c_double, _P, c_int64]),
 }
@@ -294,6 +295,23 @@ def chfsi_heev(ctx, G: torch.Tensor):
     w = torch.empty(m, dtype=torch.float64, device=G.device)
     V = fortran_empty(m, m, G.device)
     _check(ctx, load().chfsi_heev(ctx, m, _ptr(Gf), _ld(Gf), _ptr(w), _ptr(V), _ld(V)))
+    return w, V
+
+
+HEEV_NOALLOC_MAX = 128
+
+
+def chfsi_heev_noalloc(G: torch.Tensor, stream=None):
+    """Eigen-decomposition without a context or any device allocation by the library
+    (scratch in a fixed device array; m <= 128).  Output buffers come from the caller."""
+    m = G.shape[0]
+    Gf = fortran(G)
+    w = torch.empty(m, dtype=torch.float64, device=G.device)
+    V = fortran_empty(m, m, G.device)
+    s = None if stream is None else ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+    rc = load().chfsi_heev_noalloc(m, _ptr(Gf), _ld(Gf), _ptr(w), _ptr(V), _ld(V), s)
+    if rc != CHFSI_OK:
+        raise ChfsiError(rc, f"chfsi_heev_noalloc(m={m}) failed")
     return w, V
 
 

@@ -54,8 +54,12 @@ typedef struct {
   int32_t lanczos_k_warm;   /* Lanczos steps for the spectral upper bound, warm start */
   int32_t lanczos_k_cold;   /* ... cold start */
   int32_t reuse_factor;     /* 1: reuse L when B is bitwise equal to the previous B */
+  int32_t precision;        /* filter products: 0 = FP64, 1 = split-BF16 tensor-core digits
+                               (mixed precision; Rayleigh-Ritz and residuals stay FP64) */
+  int32_t slices_max;       /* most digit slices per operand in mixed mode (2..8, default 7) */
   uint64_t seed;            /* SplitMix64 seed of the Lanczos start vector / cold block */
-  void* cuda_stream;        /* cudaStream_t to run on; NULL = a stream owned by the context */
+  void* cuda_stream;        /* cudaStream_t to run on (cudaStreamLegacy for the legacy default
+                               stream); NULL = a stream created and owned by the context */
 } chfsi_opts;
 
 /* Per-problem statistics (Table 4 of the paper reports loops and filtered vectors). */
@@ -67,9 +71,12 @@ typedef struct {
   int64_t matvecs;           /* column products Hs*y (filter + Rayleigh-Ritz + Lanczos) */
   int64_t filter_matvecs;    /* column products Hs*y inside the Chebyshev filter only */
   int64_t launches;          /* CUDA kernels launched by the library for this problem */
+  int64_t filter_matvecs_fp64; /* filter column products done with FP64 arithmetic */
+  double tensor_flops;       /* tensor-core flops of the split-BF16 filter products (padded) */
   double max_resid;          /* max_i ||A x_i - lambda_i B x_i|| / (||A||_est ||x_i||) */
   double lanczos_upper;      /* spectral upper bound b used by the filter */
   double t_reduce_ms, t_lanczos_ms, t_filter_ms, t_qr_ms, t_rr_ms, t_resid_ms, t_total_ms;
+  double t_filter_gemm_ms;   /* device time of the filter's product kernels alone */
 } chfsi_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -140,6 +147,15 @@ int chfsi_lanczos(chfsi_ctx* ctx, int64_t n, const chfsi_z* H, int64_t ldh, int3
 int chfsi_filter(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,
                  chfsi_z* Y, int64_t ldy, const int32_t* degrees, double a0, double a,
                  double b);
+
+/* The same filter with split-BF16 tensor-core products (mixed-precision filter): every
+ * product Hs*Y is computed from `slices` 7-bit digit slices of each FP64 operand (power-of-
+ * two scales per row of H and per column of Y), exact in FP32 per 1024-term chunk, combined
+ * in double-float; relative error about 2^(-7 slices) of the operands' scales.
+ * slices in [1, 8].  H must be Hermitian (full storage). */
+int chfsi_filter_split(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,
+                       chfsi_z* Y, int64_t ldy, const int32_t* degrees, double a0, double a,
+                       double b, int32_t slices);
 
 /* Re-orthonormalisation (Algorithm 1): Y <- orthonormal basis of (I - YL YL^H) Y, by two
  * passes of classical Gram-Schmidt against the k locked columns YL (may be 0) and

@@ -8,6 +8,9 @@ points accept both; the step entry points need CUDA tensors).
 
 The library is the in-tree ``_lib/libchfsi.so`` built by ``build.py``; if it is missing
 or cannot be loaded, every call raises: there is no fallback implementation.
+
+Every context created here runs on torch's current CUDA stream (unless a stream is passed),
+so tensors produced by torch just before a call are complete when the library reads them.
 """
 from __future__ import annotations
 
@@ -32,16 +35,18 @@ class ChfsiError(RuntimeError):
 class chfsi_opts(ctypes.Structure):
     _fields_ = [("deg_min", c_int32), ("deg_max", c_int32), ("max_loops", c_int32),
                 ("lanczos_k_warm", c_int32), ("lanczos_k_cold", c_int32),
-                ("reuse_factor", c_int32), ("seed", c_uint64), ("cuda_stream", c_void_p)]
+                ("reuse_factor", c_int32), ("precision", c_int32), ("slices_max", c_int32),
+                ("seed", c_uint64), ("cuda_stream", c_void_p)]
 
 
 class chfsi_stats(ctypes.Structure):
     _fields_ = [("loops", c_int32), ("filtered_vectors", c_int32), ("converged", c_int32),
                 ("accept_rounds", c_int32), ("matvecs", c_int64), ("filter_matvecs", c_int64),
-                ("launches", c_int64), ("max_resid", c_double),
+                ("launches", c_int64), ("filter_matvecs_fp64", c_int64),
+                ("tensor_flops", c_double), ("max_resid", c_double),
                 ("lanczos_upper", c_double), ("t_reduce_ms", c_double), ("t_lanczos_ms", c_double),
                 ("t_filter_ms", c_double), ("t_qr_ms", c_double), ("t_rr_ms", c_double),
-                ("t_resid_ms", c_double), ("t_total_ms", c_double)]
+                ("t_resid_ms", c_double), ("t_total_ms", c_double), ("t_filter_gemm_ms", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -64,6 +69,8 @@ _SIGS = {
                                 POINTER(c_double), POINTER(c_double)]),
     "chfsi_filter": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64, POINTER(c_int32),
                                c_double, c_double, c_double]),
+    "chfsi_filter_split": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64,
+                                     POINTER(c_int32), c_double, c_double, c_double, c_int32]),
     "chfsi_orthonormalize": (c_int32, [_P, c_int64, c_int32, _P, c_int64, c_int32, _P, c_int64]),
     "chfsi_rayleigh_ritz": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64, _P, c_int64,
                                       _P]),
@@ -115,7 +122,9 @@ def fortran_empty(rows: int, cols: int, device, dtype=torch.complex128) -> torch
 
 
 def _ld(t: torch.Tensor) -> int:
-    return max(1, t.stride(1)) if t.dim() == 2 else max(1, t.shape[0])
+    if t.dim() == 2 and t.shape[1] > 1:
+        return max(1, t.stride(1))
+    return max(1, t.shape[0])  # one column (or a vector): its stride is irrelevant
 
 
 def _ptr(t):
@@ -137,11 +146,25 @@ def default_opts(**kw) -> chfsi_opts:
 
 
 # ---------------------------------------------------------------------- context
+_CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy: the context's legacy default stream
+
+
+def _stream_handle(stream) -> int:
+    """Raw cudaStream_t for the library: torch's current stream unless one is given, so the
+    library's work is ordered after torch's pending work on the same tensors (and torch's
+    later work after the library's).  torch's default stream is the legacy NULL stream,
+    passed as cudaStreamLegacy because a NULL handle asks the library for its own stream."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return h if h else _CUDA_STREAM_LEGACY
+
+
 def chfsi_create(n_max: int, blk_max: int, opts: chfsi_opts | None = None, stream=None, **kw):
     lib = load()
     o = opts if opts is not None else default_opts(**kw)
-    if stream is not None:
-        o.cuda_stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    if torch.cuda.is_available() or stream is not None:
+        o.cuda_stream = ctypes.c_void_p(_stream_handle(stream))
     ctx = ctypes.c_void_p()
     rc = lib.chfsi_create(ctypes.byref(ctx), int(n_max), int(blk_max), ctypes.byref(o))
     if rc != CHFSI_OK:
@@ -250,6 +273,17 @@ def chfsi_filter(ctx, H: torch.Tensor, Y: torch.Tensor, degrees, a0: float, a: f
     return Yf
 
 
+def chfsi_filter_split(ctx, H: torch.Tensor, Y: torch.Tensor, degrees, a0: float, a: float,
+                       b: float, slices: int = 7):
+    n, m = Y.shape
+    Hf = fortran(H)
+    Yf = fortran(Y).clone()
+    degs = (c_int32 * m)(*[int(d) for d in degrees])
+    _check(ctx, load().chfsi_filter_split(ctx, n, m, _ptr(Hf), _ld(Hf), _ptr(Yf), _ld(Yf), degs, a0,
+                                          a, b, slices))
+    return Yf
+
+
 def chfsi_orthonormalize(ctx, Y: torch.Tensor, YL: torch.Tensor | None = None):
     n, m = Y.shape
     Yf = fortran(Y.clone())
@@ -308,7 +342,7 @@ def chfsi_heev_noalloc(G: torch.Tensor, stream=None):
     Gf = fortran(G)
     w = torch.empty(m, dtype=torch.float64, device=G.device)
     V = fortran_empty(m, m, G.device)
-    s = None if stream is None else ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+    s = ctypes.c_void_p(_stream_handle(stream))
     rc = load().chfsi_heev_noalloc(m, _ptr(Gf), _ld(Gf), _ptr(w), _ptr(V), _ld(V), s)
     if rc != CHFSI_OK:
         raise ChfsiError(rc, f"chfsi_heev_noalloc(m={m}) failed")

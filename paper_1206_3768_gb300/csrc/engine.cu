@@ -43,7 +43,7 @@ struct chfsi_ctx {
 
 namespace {
 
-enum Phase { PH_REDUCE = 0, PH_LANCZOS, PH_FILTER, PH_QR, PH_RR, PH_RESID, PH_N };
+enum Phase { PH_REDUCE = 0, PH_LANCZOS, PH_FILTER, PH_QR, PH_RR, PH_RESID, PH_FGEMM, PH_N };
 
 int set_err(chfsi_ctx* c, int code, const char* fmt, ...) {
   char buf[512];
@@ -275,7 +275,7 @@ int lanczos_run(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int k, const zd
 // (in permuted order) is left in *Ya.
 int filter_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya, zd** Yb,
                  zd** Yf, const std::vector<int>& degs_sorted, const int* perm_dev, double a0,
-                 double a, double b, int64_t* matvecs) {
+                 double a, double b, int64_t* matvecs, int slices = 0, chfsi_stats* st = nullptr) {
   Workspace& ws = ctx->ws;
   const int64_t ld = ws.n_max;
   if (m <= 0 || degs_sorted.empty()) return CHFSI_OK;
@@ -303,10 +303,29 @@ int filter_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya
     }
     zd* cur = buf[(k - 1) & 1];
     zd* out = buf[k & 1];
-    GemmDesc g = gd(n, mk, n, H, ldh, OPN, cur, ld, OPN, out, ld, al);
-    g.beta = be; g.Cin = cur; g.ldcin = ld;
-    if (k >= 2) { g.gamma = ga; g.D = out; g.ldd = ld; }
-    CKS(gemm(ctx, g));
+    cudaEvent_t gb = nullptr, ge = nullptr;
+    if (st) {
+      gb = next_event(ctx);
+      ge = next_event(ctx);
+    }
+    if (slices > 0) {
+      // split-BF16 tensor-core product with the same fused recurrence epilogue
+      CK(oz_filter_product(cur, ld, n, mk, slices, al, be, cur, ld, k >= 2 ? ga : 0.0, out, ld, out,
+                           ld, ws.oz, ctx->stream, gb, ge));
+      if (st) {
+        st->tensor_flops += 2.0 * (double)oz_pair_count(slices) * ws.oz.Mp *
+                            (double)oz_padded_n(mk) * ws.oz.Kp;
+      }
+    } else {
+      GemmDesc g = gd(n, mk, n, H, ldh, OPN, cur, ld, OPN, out, ld, al);
+      g.beta = be; g.Cin = cur; g.ldcin = ld;
+      if (k >= 2) { g.gamma = ga; g.D = out; g.ldd = ld; }
+      if (gb) cudaEventRecord(gb, ctx->stream);
+      CKS(gemm(ctx, g));
+      if (ge) cudaEventRecord(ge, ctx->stream);
+      if (st) st->filter_matvecs_fp64 += mk;
+    }
+    if (st) ctx->marks.push_back({PH_FGEMM, gb, ge});
     if (matvecs) *matvecs += mk;
   }
   // columns with odd degree ended in buf[1]
@@ -321,6 +340,24 @@ int filter_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya
     CK(cudaStreamSynchronize(ctx->stream));  // odd[] lives on the host stack
   }
   return CHFSI_OK;
+}
+
+// Digit slices for the next filter loop of the mixed-precision mode: the products must be
+// accurate well below the residual the loop can reach, target = max(tau, r_min / (10 T)),
+// T = |T_dmax(t0)| the largest amplification of one loop; about 2^(-7 S) relative error
+// per product with S slices.
+int slices_for_loop(double hs_norm, double tau, double r_min, double a0, double a, double b,
+                    int dmax, int s_max) {
+  if (!(r_min > 0.0) || !std::isfinite(r_min)) return s_max;
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double t0 = std::fabs((a0 - c) / e);
+  double T = 1.0;
+  if (t0 > 1.0) T = std::cosh(dmax * std::acosh(t0));
+  if (!std::isfinite(T)) T = 1e300;
+  const double target = std::max(tau, r_min / (10.0 * T));
+  const double bits = std::log2(hs_norm / target) + 6.0;
+  const int S = (int)std::ceil(bits / 7.0);
+  return std::min(s_max, std::max(2, S));
 }
 
 // CGS2 against YL (k columns) then Cholesky QR three times (shifted on breakdown).
@@ -454,6 +491,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
     CKS(stage_in(ctx, S.A, S.lda, n, n, ws.Hs, ld, &Asrc));
     CK(herm_from_lower(Asrc, Asrc == ws.Hs ? ld : S.lda, ws.Af, ld, n, ws.status, ctx->stream));
     CKS(reduce_to_standard(ctx, ws.Af, ld, ws.Linv, ld, ws.Hs, ld, n));
+    if (o.precision == 1) CK(oz_slice_hermitian(ws.Hs, ld, n, o.slices_max, ws.oz, ctx->stream));
   }
   CKS(check_status(ctx, "input"));
 
@@ -528,6 +566,9 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   int status = CHFSI_OK;
   std::vector<int> degs;
   double max_gres = NAN;
+  const double hs_norm = std::max(std::fabs(a0), std::fabs(b_up));
+  bool mixed = o.precision == 1;
+  double prev_rmin = INFINITY;
   for (int accept = 0; accept < 4; ++accept) {
     while (conv < nev && st.loops < o.max_loops) {
       const int m = blk - conv;
@@ -541,11 +582,20 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
         CKS(read_back(ctx, degs.data(), ws.degs, m));
         perm_dev = ws.perm;
       }
-      // ---- a4: filter
+      // ---- a4: filter (split-BF16 tensor-core products in mixed mode)
+      int slices = 0;
+      double rmin = INFINITY;
+      if (have_r)
+        for (int i = 0; i < std::min(nev - conv, (int)rr.size()); ++i) rmin = std::min(rmin, rr[i]);
+      if (mixed) {
+        const int dmax_loop = degs.empty() ? 0 : *std::max_element(degs.begin(), degs.end());
+        slices = slices_for_loop(hs_norm, tau, have_r ? rmin : NAN, a0, a, b_up, dmax_loop,
+                                 o.slices_max);
+      }
       {
         PhaseScope ps(ctx, PH_FILTER);
         CKS(filter_block(ctx, ws.Hs, ld, n, m, &Ya, &Yb, &Yf, degs, perm_dev, a0, a, b_up,
-                         &st.filter_matvecs));
+                         &st.filter_matvecs, slices, &st));
       }
       st.filtered_vectors += m;
       // ---- a5: deflation + Cholesky QR
@@ -597,6 +647,16 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       rr.resize(blk - conv);
       a0 = th[0];
       a = th[blk - conv - 1];
+      // A mixed-precision loop that neither locked a pair nor reduced the smallest wanted
+      // residual has met the precision floor of its products: finish with FP64 filters.
+      if (mixed && nlock == 0) {
+        double rmin_new = INFINITY;
+        for (int i = 0; i < std::min(nev - conv, (int)rr.size()); ++i) rmin_new = std::min(rmin_new, rr[i]);
+        if (rmin_new > 0.9 * std::min(prev_rmin, rmin)) mixed = false;
+        prev_rmin = rmin_new;
+      } else {
+        prev_rmin = INFINITY;
+      }
     }
     if (conv < nev) {
       status = set_err(ctx, CHFSI_ENOCONV, "%d of %d pairs converged after %d loops", conv, nev,
@@ -685,6 +745,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   st.t_qr_ms = tph[PH_QR];
   st.t_rr_ms = tph[PH_RR];
   st.t_resid_ms = tph[PH_RESID];
+  st.t_filter_gemm_ms = tph[PH_FGEMM];
   st.t_total_ms = tot;
   if (S.st) *S.st = st;
   return status;
@@ -732,6 +793,8 @@ cudaError_t workspace_alloc(Workspace& ws, int64_t n_max, int blk_max, int lancz
   ws.splitk_elems = (size_t)std::max<int64_t>(8 * nb, 48 * mm);
   AL(ws.splitk, ws.splitk_elems);
 #undef AL
+  e = oz_alloc(ws.oz, (int)n_max, ws.blk_max, 8);
+  if (e != cudaSuccess) return e;
   e = cudaMemset(ws.status, 0, 2 * sizeof(int));
   if (e != cudaSuccess) return e;
   const int big = 0x7fffffff;
@@ -748,6 +811,7 @@ void workspace_free(Workspace& ws) {
                   ws.status, ws.status + 1, ws.barrier, ws.splitk};
   for (void* p : ptrs)
     if (p) debug_check(cudaFree(p), "cudaFree");
+  oz_free(ws.oz);
   ws = Workspace{};
 }
 
@@ -762,6 +826,8 @@ void chfsi_default_opts(chfsi_opts* o) {
   o->lanczos_k_warm = 10;
   o->lanczos_k_cold = 40;
   o->reuse_factor = 1;
+  o->precision = 1;
+  o->slices_max = 7;
   o->seed = 12063768ull;
   o->cuda_stream = nullptr;
 }
@@ -772,6 +838,9 @@ int chfsi_create(chfsi_ctx** out, int64_t n_max, int32_t blk_max, const chfsi_op
   if (n_max <= 0 || blk_max <= 0 || blk_max > n_max || n_max > (int64_t)1 << 30)
     return CHFSI_EINVAL;
   entry_guard("chfsi_create");
+  if (opts && (opts->precision < 0 || opts->precision > 1 || opts->slices_max < 1 ||
+               opts->slices_max > 8))
+    return CHFSI_EINVAL;
   chfsi_ctx* ctx = new chfsi_ctx;
   chfsi_default_opts(&ctx->opts);
   if (opts) ctx->opts = *opts;
@@ -923,6 +992,39 @@ int chfsi_filter(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t
   zd *Ya = ws.Y0, *Yb = ws.Y1, *Yf = ws.F;
   CKS(filter_block(ctx, Z(H), ldh, (int)n, m, &Ya, &Yb, &Yf, ds, ws.perm, a0, a, b, nullptr));
   // undo the permutation: Y[:, j] = Ya[:, inv[j]]
+  CK(cudaMemcpyAsync(ws.deg, inv.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(gather_cols(Ya, ld, Yb, ld, (int)n, m, ws.deg, ctx->stream));
+  CK(cudaMemcpy2DAsync(Y, ldy * sizeof(zd), Yb, ld * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHFSI_OK;
+}
+
+int chfsi_filter_split(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,
+                       chfsi_z* Y, int64_t ldy, const int32_t* degrees, double a0, double a,
+                       double b, int32_t slices) {
+  entry_guard("chfsi_filter_split");
+  if (!ctx || !H || !Y || !degrees || n <= 0 || m <= 0 || ldh < n || ldy < n || slices < 1 ||
+      slices > 8)
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (n > ctx->ws.n_max || m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "size > workspace");
+  if (!(b > a)) return set_err(ctx, CHFSI_EINVAL, "need b > a");
+  cudaSetDevice(ctx->ws.dev);
+  Workspace& ws = ctx->ws;
+  const int64_t ld = ws.n_max;
+  std::vector<int> idx(m);
+  std::iota(idx.begin(), idx.end(), 0);
+  for (int j = 0; j < m; ++j)
+    if (degrees[j] < 0) return set_err(ctx, CHFSI_EINVAL, "negative degree");
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return degrees[x] > degrees[y]; });
+  std::vector<int> ds(m), inv(m);
+  for (int r = 0; r < m; ++r) { ds[r] = degrees[idx[r]]; inv[idx[r]] = r; }
+  CK(oz_slice_hermitian(Z(H), ldh, (int)n, slices, ws.oz, ctx->stream));
+  CK(cudaMemcpy2DAsync(ws.Y0, ld * sizeof(zd), Y, ldy * sizeof(zd), n * sizeof(zd), m,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ws.perm, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  zd *Ya = ws.Y0, *Yb = ws.Y1, *Yf = ws.F;
+  CKS(filter_block(ctx, Z(H), ldh, (int)n, m, &Ya, &Yb, &Yf, ds, ws.perm, a0, a, b, nullptr, slices));
   CK(cudaMemcpyAsync(ws.deg, inv.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
   CK(gather_cols(Ya, ld, Yb, ld, (int)n, m, ws.deg, ctx->stream));
   CK(cudaMemcpy2DAsync(Y, ldy * sizeof(zd), Yb, ld * sizeof(zd), n * sizeof(zd), m,

@@ -125,6 +125,33 @@ cudaError_t lanczos_record(const zd* c, int j, const double* nrm, double* alpha,
 cudaError_t tridiag_extremes(const double* alpha, const double* beta, int k, double* out3,
                              cudaStream_t s);
 
+// ------------------------------------------------------------------ split-BF16 products
+struct OzWorkspace {
+  int S_max = 0, Kp_max = 0, Mp_max = 0, Np_max = 0;
+  int S_A = 0, Kp = 0, Mp = 0;      // current slicing of the A operand
+  int64_t sliceA = 0;
+  struct __nv_bfloat16* A = nullptr;
+  struct __nv_bfloat16* B = nullptr;
+  int* eA = nullptr;
+  int* eB = nullptr;
+  double* part = nullptr;
+  size_t part_elems = 0;
+};
+int oz_padded_k(int n);
+int oz_padded_m(int n);
+int oz_padded_n(int m);
+int64_t oz_pair_count(int S);
+cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max);
+void oz_free(OzWorkspace& oz);
+// Digit slices of the real embedding of the Hermitian Hs (once per problem).
+cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
+                               cudaStream_t s);
+// out = alpha Hs Y + beta Cin + gamma D with S-slice split-BF16 products.
+cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, double alpha,
+                              double beta, const zd* Cin, int64_t ldcin, double gamma, const zd* D,
+                              int64_t ldd, zd* out, int64_t ldo, OzWorkspace& oz, cudaStream_t s,
+                              cudaEvent_t ev_gemm_begin = nullptr, cudaEvent_t ev_gemm_end = nullptr);
+
 // ------------------------------------------------------------------ workspace
 struct Workspace {
   int dev = 0;
@@ -149,6 +176,7 @@ struct Workspace {
   // split-K partials
   zd* splitk = nullptr;
   size_t splitk_elems = 0;
+  OzWorkspace oz;
   // pinned host mirror for small read-backs
   void* host_pinned = nullptr;
   size_t host_pinned_bytes = 0;

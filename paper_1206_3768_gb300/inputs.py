@@ -47,6 +47,21 @@ CONFIGS = {
 }
 
 
+def _preload_cuda_linalg():
+    """Load torch's CUDA linear-algebra library by absolute path once, so that the lazy
+    load inside torch.linalg also works under tools that change the library search path
+    (a profiler launching the benchmark)."""
+    import ctypes
+    import os
+
+    lib = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(lib):
+        try:
+            ctypes.CDLL(lib, mode=ctypes.RTLD_GLOBAL)
+        except OSError:
+            pass
+
+
 def _rng(config_id: int, stream: int = 0) -> np.random.Generator:
     ss = np.random.SeedSequence([SEED_BASE + config_id, stream])
     return np.random.Generator(np.random.PCG64(ss))
@@ -156,6 +171,8 @@ def planted_sequence(name: str = "c1", *, n: int | None = None, N: int | None = 
     cid = cfg["config_id"] + 1000 * seed_offset
     rng = _rng(cid)
     dev = torch.device(device)
+    if dev.type == "cuda":
+        _preload_cuda_linalg()
 
     B = _overlap(rng, n, cfg["overlap"], cfg.get("kappa", 1e4), dev)
     Lg = torch.linalg.cholesky(B)

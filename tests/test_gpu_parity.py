@@ -349,3 +349,59 @@ def test_invalid_arguments_are_reported(ctx):
     cb.chfsi_reset_warm_state(ctx)
     lam, X, st = cb.chfsi_solve_next(ctx, A, B, 4, 8, 10)
     _check_solution(p, lam.cpu().numpy(), _np(X), 4)
+
+
+# ---------------------------------------------------------------------------- split-BF16 filter
+@pytest.mark.parametrize("n,m,slices,tol", [(300, 30, 7, 1e-12), (513, 17, 7, 1e-12),
+                                            (640, 130, 7, 1e-12), (513, 40, 4, 1e-7),
+                                            (300, 9, 3, 1e-5), (64, 1, 8, 1e-13)])
+def test_filter_split_matches_oracle(ctx, n, m, slices, tol):
+    """Split-BF16 digit products reproduce the FP64 filter to about 2^(-7 slices)."""
+    rng = _rng(n + m + slices)
+    lam = np.sort(rng.uniform(-2, 2, n))
+    Q, _ = np.linalg.qr(_cgauss(rng, n, n))
+    H = (Q * lam) @ Q.conj().T
+    H = 0.5 * (H + H.conj().T)
+    Y = _cgauss(rng, n, m)
+    degs = rng.integers(0, 16, m)
+    degs[0] = 15
+    a0, a, b = lam[0], lam[min(n - 2, m + 5)], lam[-1] + 0.01
+    got = _np(cb.chfsi_filter_split(ctx, _t(H), _t(Y), degs, a0, a, b, slices))
+    ref = O.chebyshev_filter(H, Y, degs, a0, a, b)
+    for j in range(m):
+        scale = np.max(np.abs(ref[:, j]))
+        assert np.max(np.abs(got[:, j] - ref[:, j])) <= tol * max(scale, 1e-300), (j, degs[j])
+
+
+def test_filter_split_single_product_is_exact_to_fp64_level():
+    """One degree-1 step with 8 slices against the FP64 product on random (not Hermitian-
+    structured beyond symmetry) data: error at the level of FP64 rounding of the result."""
+    n, m = 1100, 64   # K = 2n = 2200 spans three exact 1024-term chunks
+    rng = _rng(99)
+    H = _herm(rng, n, 1.0) * np.exp(rng.uniform(-3, 3, (n, 1)))  # rows on different scales
+    H = 0.5 * (H + H.conj().T)
+    Y = _cgauss(rng, n, m) * np.exp(rng.uniform(-5, 5, (1, m)))
+    a0, a, b = -5.0, -1.0, 3.0   # degree 1: Y1 = (sigma1/e) (H - c) Y
+    with cb.Solver(n, m) as s:
+        got = _np(cb.chfsi_filter_split(s.ctx, _t(H), _t(Y), [1] * m, a0, a, b, 8))
+    ref = O.chebyshev_filter(H, Y, [1] * m, a0, a, b)
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    s1 = e / (a0 - c)
+    bound = abs(s1 / e) * (np.abs(H) @ np.abs(Y) + abs(c) * np.abs(Y))
+    assert np.max(np.abs(got - ref) / bound) < 2 * n * 1.1e-16  # the FP64 GEMM error bound
+
+
+def test_solve_plain_fp64_mode_matches_mixed_mode():
+    seq = inputs.planted_sequence("c1", n=400, N=2, nev=12, blk=20)
+    res = {}
+    for prec in (0, 1):
+        with cb.Solver(400, 20, precision=prec) as s:
+            As = [torch.tril(p.A).to(DEV) for p in seq.problems]
+            Bs = [torch.tril(p.B).to(DEV) for p in seq.problems]
+            ev, X, st = cb.chfsi_solve_sequence(s.ctx, As, Bs, 12, 20, 10, 1e-10)
+            res[prec] = (ev.numpy(), st)
+            for ell, p in enumerate(seq.problems):
+                _check_solution(p, ev[ell].numpy(), _np(X[ell]), 12)
+    assert np.max(np.abs(res[0][0] - res[1][0])) < 1e-10
+    assert all(s["filter_matvecs_fp64"] == s["filter_matvecs"] for s in res[0][1])
+    assert all(s["tensor_flops"] > 0 for s in res[1][1])

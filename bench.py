@@ -237,8 +237,10 @@ def run_ours(args):
     if t_flops > 0:
         achieved = t_flops / (g_ms / 1e3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
-        roofline = {"bound": "tensor", "kernel": "oz_gemm_kernel (split-BF16 digit products, "
-                    "mma.sync bf16 -> fp32)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        kname = ("oz_gemm_tc_kernel (split-BF16 digit products, TMA + tcgen05.mma, FP32 "
+                 "accumulators in tensor memory)" if os.environ.get("CHFSI_OZ_KERNEL", "tc") != "mma"
+                 else "oz_gemm_kernel (split-BF16 digit products, mma.sync bf16 -> fp32)")
+        roofline = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": traffic,
                     "fp64_equivalent_tflops": fp64_equiv / (g_ms / 1e3) / 1e12,
                     "peak_note": f"bf16 dense sustained ({peak_kind}); achieved counts the "

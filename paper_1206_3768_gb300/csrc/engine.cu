@@ -174,6 +174,7 @@ GemmDesc gd(int M, int N, int K, const zd* A, int64_t lda, int opA, const zd* B,
 }
 
 constexpr int NB = 128;  // panel width of the blocked factorisations
+constexpr int kRRSlices = 8;  // digit slices of the Rayleigh-Ritz product Hs Y in mixed mode
 
 // In-place blocked right-looking Cholesky on the lower triangle of L (n x n).
 int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n) {
@@ -377,12 +378,20 @@ int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const z
   }
   const double u = 1.1102230246251565e-16;
   const double shift_base = 11.0 * ((double)n * m + (double)m * (m + 1)) * u;
+  // Cholesky QR twice; a third pass only when the first one needed the shifted retry
+  // (shifted Cholesky QR3), which the device reports in ws.shiftflag.
+  CK(cudaMemsetAsync(ws.shiftflag, 0, sizeof(int), ctx->stream));
   for (int pass = 0; pass < 3; ++pass) {
+    if (pass == 2) {
+      int shifted = 1;
+      CKS(read_back(ctx, &shifted, ws.shiftflag, 1));
+      if (!shifted) break;
+    }
     GemmDesc g = gd(m, m, n, *Ya, ld, OPC, *Ya, ld, OPN, ws.G, ldm);
     g.lowerC = 1;
     CKS(gemm(ctx, g));
     CK(small_cholesky(ws.G, ldm, m, 1, 1, shift_base, ws.dscale, ws.jac, ws.status, ws.status + 1, 0,
-                      ctx->stream));
+                      ctx->stream, pass == 0 ? ws.shiftflag : nullptr));
     CK(trinv_lower(ws.G, ldm, ws.Rt, ldm, m, ctx->stream));
     CK(cholqr_T(ws.Rt, ldm, m, ws.dscale, ws.V, ldm, ctx->stream));
     GemmDesc h = gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld);
@@ -395,11 +404,17 @@ int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const z
 
 // Rayleigh-Ritz on the m columns of *Ya: theta (device), *Ya <- Ritz vectors, *W <- H *Ya.
 int rayleigh_ritz_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya, zd** Yb,
-                        zd** W, zd** Zb, double* theta) {
+                        zd** W, zd** Zb, double* theta, int rr_slices = 0) {
   Workspace& ws = ctx->ws;
   const int64_t ld = ws.n_max;
   const int64_t ldm = ws.blk_max;
-  CKS(gemm(ctx, gd(n, m, n, H, ldh, OPN, *Ya, ld, OPN, *W, ld)));
+  if (rr_slices > 0) {
+    // FP64-level product from 8 digit slices per operand (error below the FP64 GEMM bound)
+    CK(oz_filter_product(*Ya, ld, n, m, rr_slices, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, *W, ld,
+                         ws.oz, ctx->stream));
+  } else {
+    CKS(gemm(ctx, gd(n, m, n, H, ldh, OPN, *Ya, ld, OPN, *W, ld)));
+  }
   GemmDesc g = gd(m, m, n, *Ya, ld, OPC, *W, ld, OPN, ws.G, ldm);
   g.lowerC = 1;
   CKS(gemm(ctx, g));
@@ -491,9 +506,11 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
     CKS(stage_in(ctx, S.A, S.lda, n, n, ws.Hs, ld, &Asrc));
     CK(herm_from_lower(Asrc, Asrc == ws.Hs ? ld : S.lda, ws.Af, ld, n, ws.status, ctx->stream));
     CKS(reduce_to_standard(ctx, ws.Af, ld, ws.Linv, ld, ws.Hs, ld, n));
-    if (o.precision == 1) CK(oz_slice_hermitian(ws.Hs, ld, n, o.slices_max, ws.oz, ctx->stream));
+    if (o.precision == 1) CK(oz_slice_hermitian(ws.Hs, ld, n, kRRSlices, ws.oz, ctx->stream));
   }
   CKS(check_status(ctx, "input"));
+
+  const int rr_slices = o.precision == 1 ? kRRSlices : 0;
 
   // ---------------------------------------------------------------- a3: Lanczos bounds
   const bool warm = ctx->has_warm && ctx->warm_n == n && ctx->warm_blk == blk;
@@ -542,7 +559,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
     }
     {
       PhaseScope ps(ctx, PH_RR);
-      CKS(rayleigh_ritz_block(ctx, ws.Hs, ld, n, blk, &Ya, &Yb, &W, &Zb, theta));
+      CKS(rayleigh_ritz_block(ctx, ws.Hs, ld, n, blk, &Ya, &Yb, &W, &Zb, theta, rr_slices));
     }
     {
       PhaseScope ps(ctx, PH_RESID);
@@ -568,7 +585,8 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   double max_gres = NAN;
   const double hs_norm = std::max(std::fabs(a0), std::fabs(b_up));
   bool mixed = o.precision == 1;
-  double prev_rmin = INFINITY;
+  int slice_boost = 0;        // extra slices after a loop that stalled on product precision
+  double front_before = NAN;  // residual of the first active (next to lock) column
   for (int accept = 0; accept < 4; ++accept) {
     while (conv < nev && st.loops < o.max_loops) {
       const int m = blk - conv;
@@ -584,13 +602,17 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       }
       // ---- a4: filter (split-BF16 tensor-core products in mixed mode)
       int slices = 0;
-      double rmin = INFINITY;
+      // smallest residual among the wanted active columns that still need filtering
+      double rneed = INFINITY;
       if (have_r)
-        for (int i = 0; i < std::min(nev - conv, (int)rr.size()); ++i) rmin = std::min(rmin, rr[i]);
+        for (int i = 0; i < std::min(nev - conv, (int)rr.size()); ++i)
+          if (rr[i] >= tau) rneed = std::min(rneed, rr[i]);
+      front_before = (have_r && !rr.empty()) ? rr[0] : NAN;
       if (mixed) {
         const int dmax_loop = degs.empty() ? 0 : *std::max_element(degs.begin(), degs.end());
-        slices = slices_for_loop(hs_norm, tau, have_r ? rmin : NAN, a0, a, b_up, dmax_loop,
+        slices = slices_for_loop(hs_norm, tau, have_r ? rneed : NAN, a0, a, b_up, dmax_loop,
                                  o.slices_max);
+        slices = std::min(o.slices_max, slices + slice_boost);
       }
       {
         PhaseScope ps(ctx, PH_FILTER);
@@ -606,7 +628,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       // ---- a6: Rayleigh-Ritz
       {
         PhaseScope ps(ctx, PH_RR);
-        CKS(rayleigh_ritz_block(ctx, ws.Hs, ld, n, m, &Ya, &Yb, &W, &Zb, theta));
+        CKS(rayleigh_ritz_block(ctx, ws.Hs, ld, n, m, &Ya, &Yb, &W, &Zb, theta, rr_slices));
       }
       st.matvecs += m;
       // ---- a7: residuals and locking
@@ -647,15 +669,13 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       rr.resize(blk - conv);
       a0 = th[0];
       a = th[blk - conv - 1];
-      // A mixed-precision loop that neither locked a pair nor reduced the smallest wanted
-      // residual has met the precision floor of its products: finish with FP64 filters.
-      if (mixed && nlock == 0) {
-        double rmin_new = INFINITY;
-        for (int i = 0; i < std::min(nev - conv, (int)rr.size()); ++i) rmin_new = std::min(rmin_new, rr[i]);
-        if (rmin_new > 0.9 * std::min(prev_rmin, rmin)) mixed = false;
-        prev_rmin = rmin_new;
-      } else {
-        prev_rmin = INFINITY;
+      // A mixed-precision loop that locked nothing and did not halve the residual of the
+      // column blocking the locked prefix has met the precision floor of its products:
+      // add two slices, and once the maximum is in use finish with FP64 filters.
+      if (mixed && nlock == 0 && !rr.empty() && std::isfinite(front_before) &&
+          rr[0] > 0.5 * front_before) {
+        if (slices >= o.slices_max) mixed = false;
+        else slice_boost += 2;
       }
     }
     if (conv < nev) {
@@ -789,12 +809,13 @@ cudaError_t workspace_alloc(Workspace& ws, int64_t n_max, int blk_max, int lancz
   AL(ws.lal, lanczos_kmax + 1); AL(ws.lbe, lanczos_kmax + 1);
   AL(ws.deg, ws.blk_max); AL(ws.perm, ws.blk_max); AL(ws.degs, ws.blk_max);
   AL(ws.flag, ws.blk_max + 64); AL(ws.ilist, 64);
-  AL(ws.status, 2); AL(ws.barrier, 4);
+  AL(ws.status, 2); AL(ws.barrier, 4); AL(ws.shiftflag, 4);
   ws.splitk_elems = (size_t)std::max<int64_t>(8 * nb, 48 * mm);
   AL(ws.splitk, ws.splitk_elems);
 #undef AL
   e = oz_alloc(ws.oz, (int)n_max, ws.blk_max, 8);
   if (e != cudaSuccess) return e;
+  ws.oz.status = ws.status;
   e = cudaMemset(ws.status, 0, 2 * sizeof(int));
   if (e != cudaSuccess) return e;
   const int big = 0x7fffffff;

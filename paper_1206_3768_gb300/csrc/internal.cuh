@@ -74,7 +74,7 @@ int sm_count();
 // status and atomically lowers *info to info_base + the failing pivot.  One CTA.
 cudaError_t small_cholesky(zd* G, int64_t ldg, int m, int scale, int shift_on_fail,
                            double shift_base, double* dscale, zd* backup, int* status, int* info,
-                           int info_base, cudaStream_t s);
+                           int info_base, cudaStream_t s, int* shift_flag = nullptr);
 // X = L^{-1} for an m x m lower-triangular L (strict upper of X zeroed).  X != L.
 cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m, cudaStream_t s);
 // T = D X^H (upper triangular, zero below): the right factor of Cholesky QR, Q = Y T.
@@ -136,7 +136,9 @@ struct OzWorkspace {
   int* eB = nullptr;
   double* part = nullptr;
   size_t part_elems = 0;
+  int* status = nullptr;            // device status word for bounded-wait timeouts
 };
+bool oz_use_tcgen05();
 int oz_padded_k(int n);
 int oz_padded_m(int n);
 int oz_padded_n(int m);
@@ -172,6 +174,7 @@ struct Workspace {
   double *dscale = nullptr, *scal = nullptr, *lal = nullptr, *lbe = nullptr;
   int *deg = nullptr, *perm = nullptr, *degs = nullptr, *flag = nullptr, *ilist = nullptr;
   int* status = nullptr;  // [0]: DEV_* flags, [1]: first failing pivot
+  int* shiftflag = nullptr;  // set when a Cholesky QR pass needed the shifted retry
   unsigned* barrier = nullptr;
   // split-K partials
   zd* splitk = nullptr;

@@ -19,7 +19,13 @@
 // run 570x slower than bf16 mma.sync on this part).
 #include <algorithm>
 #include <cmath>
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -228,6 +234,313 @@ __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int N
   }
 }
 
+
+// ============================================================================ tcgen05 path
+// The same digit products on the 5th-generation tensor cores: TMA (128-byte swizzle) stages
+// 128 x 64 bf16 tiles of A and B in shared memory, one elected thread issues
+// tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor memory), and four drain
+// warps fold each exact 1024-term chunk into double-float sums that also live in tensor
+// memory.  Tensor memory (512 columns): two 128-column accumulators used alternately
+// (one fills while the other drains), the high words of the sums (256..383) and the low
+// words (384..511).  Warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..5 drain.
+// Every wait on an mbarrier is bounded; a wait that runs out sets DEV_TIMEOUT and the CTA
+// unwinds (waiting, again bounded, for its own copies and MMAs) before freeing tensor memory.
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 5, TC_THREADS = 192;
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB (A) and 16 KB (B) per stage
+constexpr long kMbarSpinLimit = 1L << 26;
+
+struct TcParams {
+  int nkb, tiles_m, splits, Mp, Np, n_real;  // n_real: columns of B^ that hold data
+  OzPairs pairs;
+  double* part;
+  int* status;
+};
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar));
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity));
+  return ok != 0;
+}
+// Bounded wait: false (with DEV_TIMEOUT set and the CTA's abort flag raised) if it ran out
+// or another role of this CTA already gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* status) {
+  long it = 0;
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if (++it > kMbarSpinLimit) {
+      *abort_flag = 1;
+      atomicOr(status, DEV_TIMEOUT);
+      return false;
+    }
+    if (it > 64) __nanosleep(32);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, both K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+               ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+
+#define TC_R32(v) \
+  "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), \
+  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),      \
+  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),    \
+  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),    \
+  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+#define TC_W32(v) \
+  "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), \
+  "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),   \
+  "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),  \
+  "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : TC_R32(v)
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n"
+      ::"r"(taddr), TC_W32(v));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// chunk boundaries of the flattened (pair, k-block) sequence q0..q1 of one CTA
+__device__ __forceinline__ bool tc_chunk_start(int q, int q0, int nkb) {
+  const int kb = q % nkb;
+  return q == q0 || (kb % OZ_CHUNK_KB) == 0;
+}
+__device__ __forceinline__ bool tc_chunk_end(int q, int q1, int nkb) {
+  const int kb = q % nkb;
+  return q == q1 - 1 || (kb % OZ_CHUNK_KB) == OZ_CHUNK_KB - 1 || kb == nkb - 1;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    oz_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const TcParams p) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  const uintptr_t base = (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023;
+  unsigned char* sA = reinterpret_cast<unsigned char*>(base);
+  unsigned char* sB = sA + TC_STAGES * TC_TILE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_TILE_BYTES);
+  // bars: full[STAGES], empty[STAGES], accf[2], acce[2], done[1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tm = blockIdx.x % p.tiles_m, tn = blockIdx.x / p.tiles_m;
+  const int m0 = tm * TC_BM, n0 = tn * TC_BN;
+  const int ncols = min(TC_BN, ((p.n_real - n0 + 15) / 16) * 16);  // MMA N for this tile
+  const int total = p.pairs.n * p.nkb;
+  const int per = (total + p.splits - 1) / p.splits;
+  const int q0 = min(total, (int)blockIdx.y * per), q1 = min(total, q0 + per);
+
+  const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * TC_STAGES;
+  const uint32_t accf0 = empty0 + 8 * TC_STAGES, acce0 = accf0 + 16, done_bar = acce0 + 16;
+
+  if (tid == 0) {
+    for (int i = 0; i < TC_STAGES; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 128);
+    }
+    mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(
+        smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = q0; q < q1; ++q, ++issued) {
+        const int i = q - q0, stage = i % TC_STAGES;
+        if (i >= TC_STAGES && !mbar_wait(empty0 + 8 * stage, ((i / TC_STAGES) & 1) ^ 1, abort_flag, p.status))
+          break;
+        const int pr = q / p.nkb, kb = q - pr * p.nkb;
+        mbar_expect_tx(full0 + 8 * stage, 2 * TC_TILE_BYTES);
+        tma_load_2d(sA_u + stage * TC_TILE_BYTES, &tmA, kb * TC_BK, p.pairs.s[pr] * p.Mp + m0,
+                    full0 + 8 * stage);
+        tma_load_2d(sB_u + stage * TC_TILE_BYTES, &tmB, kb * TC_BK, p.pairs.t[pr] * p.Np + n0,
+                    full0 + 8 * stage);
+      }
+      // on abort: let the copies already issued land before the CTA can exit
+      if (*abort_flag) {
+        for (int j = max(0, issued - TC_STAGES); j < issued; ++j) {
+          long it = 0;
+          while (!mbar_try(full0 + 8 * (j % TC_STAGES), (j / TC_STAGES) & 1) && ++it < kMbarSpinLimit) {}
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(TC_BM, ncols);
+      int chunk = -1;
+      for (int q = q0; q < q1; ++q) {
+        const int i = q - q0, stage = i % TC_STAGES;
+        if (!mbar_wait(full0 + 8 * stage, (i / TC_STAGES) & 1, abort_flag, p.status)) break;
+        tc_fence_after();
+        const bool start = tc_chunk_start(q, q0, p.nkb);
+        if (start) {
+          ++chunk;
+          if (chunk >= 2 && !mbar_wait(acce0 + 8 * (chunk & 1), ((chunk >> 1) - 1) & 1, abort_flag, p.status))
+            break;
+          tc_fence_after();
+        }
+        const uint32_t d = tmem + (uint32_t)((chunk & 1) * TC_BN);
+        const uint32_t a_s = sA_u + stage * TC_TILE_BYTES, b_s = sB_u + stage * TC_TILE_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk)
+          tc_mma(d, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc,
+                 (start && kk == 0) ? 0u : 1u);
+        tc_commit(empty0 + 8 * stage);
+        if (tc_chunk_end(q, q1, p.nkb)) tc_commit(accf0 + 8 * (chunk & 1));
+      }
+      // all MMAs issued by this thread are complete once done_bar fires
+      tc_commit(done_bar);
+      long it = 0;
+      while (!mbar_try(done_bar, 0) && ++it < kMbarSpinLimit) {}
+    }
+  } else {
+    // ------------------------------------------------------------ drain warps (2..5)
+    const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    uint32_t zero[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) zero[j] = 0u;
+#pragma unroll
+    for (int cb = 0; cb < TC_BN / 32; ++cb) {
+      tmem_st32(lane_base + 256 + cb * 32, zero);
+      tmem_st32(lane_base + 384 + cb * 32, zero);
+    }
+    tmem_wait_st();
+    int chunk = -1;
+    bool ok = true;
+    for (int q = q0; q < q1 && ok; ++q) {
+      if (tc_chunk_start(q, q0, p.nkb)) ++chunk;
+      if (!tc_chunk_end(q, q1, p.nkb)) continue;
+      const int b = chunk & 1;
+      if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status)) { ok = false; break; }
+      tc_fence_after();
+      const int pr = q / p.nkb;
+      const float sc = ldexpf(1.0f, -OZ_BETA * (p.pairs.s[pr] + p.pairs.t[pr] + 2));
+#pragma unroll 1
+      for (int cb = 0; cb < TC_BN / 32; ++cb) {
+        if (cb * 32 >= ncols) break;
+        uint32_t acc[32], hi[32], lo[32];
+        tmem_ld32(lane_base + b * TC_BN + cb * 32, acc);
+        tmem_ld32(lane_base + 256 + cb * 32, hi);
+        tmem_ld32(lane_base + 384 + cb * 32, lo);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float h = __uint_as_float(hi[j]), l = __uint_as_float(lo[j]);
+          two_sum_acc(h, l, __uint_as_float(acc[j]) * sc);
+          hi[j] = __float_as_uint(h);
+          lo[j] = __float_as_uint(l);
+        }
+        tmem_st32(lane_base + 256 + cb * 32, hi);
+        tmem_st32(lane_base + 384 + cb * 32, lo);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(acce0 + 8 * b);
+    }
+    if (ok && !*abort_flag) {
+      // partial sums of this split: P[split][col * Mp + row]
+      double* P = p.part + (int64_t)blockIdx.y * p.Mp * p.Np;
+      const int row = m0 + quarter * 32 + lane;
+#pragma unroll 1
+      for (int cb = 0; cb < TC_BN / 32; ++cb) {
+        if (cb * 32 >= ncols) break;
+        uint32_t hi[32], lo[32];
+        tmem_ld32(lane_base + 256 + cb * 32, hi);
+        tmem_ld32(lane_base + 384 + cb * 32, lo);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + cb * 32 + j;
+          if (col < p.Np)
+            P[(int64_t)col * p.Mp + row] = (double)__uint_as_float(hi[j]) + (double)__uint_as_float(lo[j]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+}
+
 __device__ __forceinline__ int exponent_bound(double mx) {
   // smallest e with mx < 2^e (0 for mx == 0)
   if (!(mx > 0.0)) return 0;
@@ -336,9 +649,44 @@ int choose_oz_splits(int tiles, int total_kb, size_t cap_elems, int64_t tile_ele
 }  // namespace
 
 // ---------------------------------------------------------------------------- host side
+// Product kernel: tcgen05 (default) or the mma.sync kernel, chosen once per process by the
+// environment variable CHFSI_OZ_KERNEL ("tc" or "mma").
+bool oz_use_tcgen05() {
+  static int choice = -1;
+  if (choice < 0) {
+    const char* v = std::getenv("CHFSI_OZ_KERNEL");
+    choice = (v && std::strcmp(v, "mma") == 0) ? 0 : 1;
+  }
+  return choice == 1;
+}
+
+// 2-D bf16 tensor map over `rows` rows of `inner` elements (row pitch inner * 2 bytes),
+// 64 x 128 boxes, 128-byte swizzle (the layout the tcgen05 descriptors expect).
+static bool encode_bf16_map(CUtensorMap* map, const void* ptr, int inner, uint64_t rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
 int oz_padded_k(int n) { return ((2 * n + OZ_BK - 1) / OZ_BK) * OZ_BK; }
 int oz_padded_m(int n) { return ((2 * n + OZ_BM - 1) / OZ_BM) * OZ_BM; }
-int oz_padded_n(int m) { return ((m + OZ_BN - 1) / OZ_BN) * OZ_BN; }
+int oz_padded_n(int m) {
+  return oz_use_tcgen05() ? ((m + 15) / 16) * 16 : ((m + OZ_BN - 1) / OZ_BN) * OZ_BN;
+}
 
 cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
                                cudaStream_t s) {
@@ -373,44 +721,78 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
   if (e != cudaSuccess) return e;
   oz_slice_cols_kernel<<<Np, 256, 0, s>>>(Y, ldy, n, m, S, oz.B, sliceB, Kp, oz.eB);
   CHFSI_COUNT_LAUNCH();
-  OzParams p;
-  p.A = oz.A;
-  p.B = oz.B;
-  p.sliceA = oz.sliceA;
-  p.sliceB = sliceB;
-  p.Kp = Kp;
-  p.nkb = Kp / OZ_BK;
-  p.tiles_m = Mp / OZ_BM;
-  p.Mp = Mp;
-  p.Np = Np;
-  p.pairs.n = 0;
-  for (int lvl = 2; lvl <= S + 1; ++lvl)
-    for (int si = 1; si <= S; ++si) {
-      const int ti = lvl - si;
-      if (ti < 1 || ti > S) continue;
-      p.pairs.s[p.pairs.n] = (unsigned char)(si - 1);
-      p.pairs.t[p.pairs.n] = (unsigned char)(ti - 1);
-      ++p.pairs.n;
+  // Pairs (s, t) with s + t <= S + 1, grouped by the A slice s so that consecutive pairs
+  // stream the same slice of the large operand (it stays in L2 between them).
+  OzPairs pairs;
+  pairs.n = 0;
+  for (int si = 1; si <= S; ++si)
+    for (int ti = 1; si + ti <= S + 1; ++ti) {
+      pairs.s[pairs.n] = (unsigned char)(si - 1);
+      pairs.t[pairs.n] = (unsigned char)(ti - 1);
+      ++pairs.n;
     }
-  const int tiles = p.tiles_m * (Np / OZ_BN);
-  p.splits = choose_oz_splits(tiles, p.pairs.n * p.nkb, oz.part_elems, (int64_t)Mp * Np);
-  p.part = oz.part;
-  const size_t smem = (size_t)OZ_STAGES * (OZ_BM + OZ_BN) * OZ_BK * 2;
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int splits = 1;
+  if (oz_use_tcgen05()) {
+    TcParams tp;
+    tp.nkb = Kp / OZ_BK;
+    tp.tiles_m = Mp / TC_BM;
+    tp.Mp = Mp;
+    tp.Np = Np;
+    tp.n_real = m;
+    tp.pairs = pairs;
+    tp.part = oz.part;
+    tp.status = oz.status;
+    const int tiles = tp.tiles_m * ((Np + TC_BN - 1) / TC_BN);
+    tp.splits = splits = choose_oz_splits(tiles, pairs.n * tp.nkb, oz.part_elems, (int64_t)Mp * Np);
+    CUtensorMap mapA, mapB;
+    if (!encode_bf16_map(&mapA, oz.A, Kp, (uint64_t)oz.S_A * Mp) ||
+        !encode_bf16_map(&mapB, oz.B, Kp, (uint64_t)S * Np))
+      return cudaErrorInvalidValue;
+    const size_t smem = 1024 + (size_t)TC_STAGES * 2 * TC_TILE_BYTES + 256;
+    static bool tc_attr = false;
+    if (!tc_attr) {
+      e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      tc_attr = true;
+    }
+    if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
+    oz_gemm_tc_kernel<<<dim3(tiles, splits), TC_THREADS, smem, s>>>(mapA, mapB, tp);
+    CHFSI_COUNT_LAUNCH();
+    if (ev_gemm_end) cudaEventRecord(ev_gemm_end, s);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    attr_set = true;
+  } else {
+    OzParams p;
+    p.A = oz.A;
+    p.B = oz.B;
+    p.sliceA = oz.sliceA;
+    p.sliceB = sliceB;
+    p.Kp = Kp;
+    p.nkb = Kp / OZ_BK;
+    p.tiles_m = Mp / OZ_BM;
+    p.Mp = Mp;
+    p.Np = Np;
+    p.pairs = pairs;
+    const int tiles = p.tiles_m * (Np / OZ_BN);
+    p.splits = splits = choose_oz_splits(tiles, p.pairs.n * p.nkb, oz.part_elems, (int64_t)Mp * Np);
+    p.part = oz.part;
+    const size_t smem = (size_t)OZ_STAGES * (OZ_BM + OZ_BN) * OZ_BK * 2;
+    static bool attr_set = false;
+    if (!attr_set) {
+      e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
+    oz_gemm_kernel<<<dim3(tiles, p.splits), OZ_THREADS, smem, s>>>(p);
+    CHFSI_COUNT_LAUNCH();
+    if (ev_gemm_end) cudaEventRecord(ev_gemm_end, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
-  oz_gemm_kernel<<<dim3(tiles, p.splits), OZ_THREADS, smem, s>>>(p);
-  CHFSI_COUNT_LAUNCH();
-  if (ev_gemm_end) cudaEventRecord(ev_gemm_end, s);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   const int64_t tot = (int64_t)n * m;
   const int blocks = (int)std::min<int64_t>(4 * sm_count(), (tot + 255) / 256);
-  oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, p.splits, Mp, Np, oz.eA, oz.eB, n, m, alpha,
+  oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, oz.eA, oz.eB, n, m, alpha,
                                             beta, Cin, ldcin, gamma, D, ldd, out, ldo);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
@@ -422,7 +804,7 @@ cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max) {
   oz.S_max = S_max;
   oz.Kp_max = oz_padded_k(n_max);
   oz.Mp_max = oz_padded_m(n_max);
-  oz.Np_max = oz_padded_n(blk_max);
+  oz.Np_max = ((blk_max + OZ_BN - 1) / OZ_BN) * OZ_BN;  // covers both kernels' paddings
   cudaError_t e;
   e = cudaMalloc((void**)&oz.A, sizeof(__nv_bfloat16) * (size_t)S_max * oz.Mp_max * oz.Kp_max);
   if (e != cudaSuccess) return e;

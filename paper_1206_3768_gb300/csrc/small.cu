@@ -18,7 +18,7 @@ namespace {
 // pivot is not positive.  backup: m x m scratch used for the retry.
 __global__ void cholesky_kernel(zd* G, int64_t ldg, int m, int scale, int shift_on_fail,
                                 double shift_base, double* dscale, zd* backup, int* status,
-                                int* info, int info_base) {
+                                int* info, int info_base, int* shift_flag) {
   __shared__ int fail;
   __shared__ double pivot;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -88,6 +88,7 @@ __global__ void cholesky_kernel(zd* G, int64_t ldg, int m, int scale, int shift_
     }
     // shifted retry: G <- backup + s I with s = shift_base * trace(backup)
     __shared__ double tr;
+    if (tid == 0 && shift_flag) *shift_flag = 1;
     if (tid == 0) {
       double t = 0.0;
       for (int i = 0; i < m; ++i) t += backup[i + (int64_t)i * m].x;
@@ -378,10 +379,10 @@ __global__ void jacobi_finish_kernel(const zd* Ga, const zd* Gb, const zd* Vw, c
 
 cudaError_t small_cholesky(zd* G, int64_t ldg, int m, int scale, int shift_on_fail,
                            double shift_base, double* dscale, zd* backup, int* status, int* info,
-                           int info_base, cudaStream_t s) {
+                           int info_base, cudaStream_t s, int* shift_flag) {
   if (m <= 0) return cudaSuccess;
   cholesky_kernel<<<1, 1024, 0, s>>>(G, ldg, m, scale, shift_on_fail, shift_base, dscale, backup,
-                                     status, info, info_base);
+                                     status, info, info_base, shift_flag);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

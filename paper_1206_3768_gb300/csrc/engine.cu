@@ -225,10 +225,23 @@ int blocked_trinv(chfsi_ctx* ctx, const zd* L, int64_t ld, zd* X, int64_t ldx, i
   return CHFSI_OK;
 }
 
-// Hs = Linv Af Linv^H (lower computed, mirrored)
+// Hs = Linv Af Linv^H (lower computed, mirrored).  split: the two products use 8-slice
+// split-BF16 tensor-core products (FP64-level accuracy), skipping the zero k-blocks of the
+// triangular Linv and the upper tiles of Hs: T = Linv Af, Hs = Linv T^H.
 int reduce_to_standard(chfsi_ctx* ctx, const zd* Af, int64_t lda, const zd* Linv, int64_t ldl,
-                       zd* Hs, int64_t ldh, int n) {
+                       zd* Hs, int64_t ldh, int n, bool split = false) {
   Workspace& ws = ctx->ws;
+  if (split) {
+    const int S = kRRSlices;
+    CK(oz_slice_a_rows(Linv, ldl, n, S, ws.oz, ctx->stream));
+    CK(oz_slice_b_cols(Af, lda, n, n, S, ws.oz, ctx->stream));
+    CK(oz_run_product(n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, ws.T, ws.n_max, 1, 0, ws.oz,
+                      ctx->stream));
+    CK(oz_slice_b_conj_rows(ws.T, ws.n_max, n, n, S, ws.oz, ctx->stream));
+    CK(oz_run_product(n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, Hs, ldh, 1, 1, ws.oz, ctx->stream));
+    CK(mirror_lower(Hs, ldh, n, ctx->stream));
+    return CHFSI_OK;
+  }
   GemmDesc g = gd(n, n, n, Linv, ldl, OPN, Af, lda, OPN, ws.T, ws.n_max);
   g.triA = 1;
   CKS(gemm(ctx, g));
@@ -505,7 +518,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
     const zd* Asrc = nullptr;
     CKS(stage_in(ctx, S.A, S.lda, n, n, ws.Hs, ld, &Asrc));
     CK(herm_from_lower(Asrc, Asrc == ws.Hs ? ld : S.lda, ws.Af, ld, n, ws.status, ctx->stream));
-    CKS(reduce_to_standard(ctx, ws.Af, ld, ws.Linv, ld, ws.Hs, ld, n));
+    CKS(reduce_to_standard(ctx, ws.Af, ld, ws.Linv, ld, ws.Hs, ld, n, o.precision == 1));
     if (o.precision == 1) CK(oz_slice_hermitian(ws.Hs, ld, n, kRRSlices, ws.oz, ctx->stream));
   }
   CKS(check_status(ctx, "input"));
@@ -966,7 +979,8 @@ int chfsi_reduce(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const
   Workspace& ws = ctx->ws;
   CKS(blocked_trinv(ctx, Z(L), ldl, ws.Linv, ws.n_max, (int)n));
   CK(herm_from_lower(Z(A), lda, ws.Af, ws.n_max, (int)n, ws.status, ctx->stream));
-  CKS(reduce_to_standard(ctx, ws.Af, ws.n_max, ws.Linv, ws.n_max, Z(Hs), ldh, (int)n));
+  CKS(reduce_to_standard(ctx, ws.Af, ws.n_max, ws.Linv, ws.n_max, Z(Hs), ldh, (int)n,
+                         ctx->opts.precision == 1));
   ctx->has_factor = false;  // ws.Linv no longer matches ws.Bf
   CK(cudaStreamSynchronize(ctx->stream));
   return check_status(ctx, "chfsi_reduce");
@@ -1088,7 +1102,12 @@ int chfsi_rayleigh_ritz(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, 
   CK(cudaMemcpy2DAsync(ws.Y0, ld * sizeof(zd), Y, ldy * sizeof(zd), n * sizeof(zd), m,
                        cudaMemcpyDeviceToDevice, ctx->stream));
   zd *Ya = ws.Y0, *Yb = ws.Y1, *W = ws.W, *Zb = ws.Z;
-  CKS(rayleigh_ritz_block(ctx, Z(H), ldh, (int)n, m, &Ya, &Yb, &W, &Zb, theta));
+  int rr_slices = 0;
+  if (ctx->opts.precision == 1) {
+    rr_slices = kRRSlices;
+    CK(oz_slice_hermitian(Z(H), ldh, (int)n, rr_slices, ws.oz, ctx->stream));
+  }
+  CKS(rayleigh_ritz_block(ctx, Z(H), ldh, (int)n, m, &Ya, &Yb, &W, &Zb, theta, rr_slices));
   CK(cudaMemcpy2DAsync(Y, ldy * sizeof(zd), Ya, ld * sizeof(zd), n * sizeof(zd), m,
                        cudaMemcpyDeviceToDevice, ctx->stream));
   CK(cudaMemcpy2DAsync(HY, ldhy * sizeof(zd), W, ld * sizeof(zd), n * sizeof(zd), m,

@@ -130,6 +130,8 @@ struct OzWorkspace {
   int S_max = 0, Kp_max = 0, Mp_max = 0, Np_max = 0;
   int S_A = 0, Kp = 0, Mp = 0;      // current slicing of the A operand
   int64_t sliceA = 0;
+  int S_B = 0, Np = 0, m = 0;       // current slicing of the B operand (m columns)
+  int64_t sliceB = 0;
   struct __nv_bfloat16* A = nullptr;
   struct __nv_bfloat16* B = nullptr;
   int* eA = nullptr;
@@ -148,6 +150,19 @@ void oz_free(OzWorkspace& oz);
 // Digit slices of the real embedding of the Hermitian Hs (once per problem).
 cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
                                cudaStream_t s);
+// Digit slices of the rows of a general square X as the A operand.
+cudaError_t oz_slice_a_rows(const zd* X, int64_t ldx, int n, int S, OzWorkspace& oz, cudaStream_t s);
+// Digit slices of the columns of Y (n x m) as the B operand.
+cudaError_t oz_slice_b_cols(const zd* Y, int64_t ldy, int n, int m, int S, OzWorkspace& oz,
+                            cudaStream_t s);
+// Digit slices of X^H (X: m x n) as the B operand: column r = conj(row r of X).
+cudaError_t oz_slice_b_conj_rows(const zd* X, int64_t ldx, int m, int n, int S, OzWorkspace& oz,
+                                 cudaStream_t s);
+// out = alpha A B + beta Cin + gamma D from the current slices.
+cudaError_t oz_run_product(int n, int S, double alpha, double beta, const zd* Cin, int64_t ldcin,
+                           double gamma, const zd* D, int64_t ldd, zd* out, int64_t ldo, int a_lower,
+                           int c_lower, OzWorkspace& oz, cudaStream_t s,
+                           cudaEvent_t ev_gemm_begin = nullptr, cudaEvent_t ev_gemm_end = nullptr);
 // out = alpha Hs Y + beta Cin + gamma D with S-slice split-BF16 products.
 cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, double alpha,
                               double beta, const zd* Cin, int64_t ldcin, double gamma, const zd* D,

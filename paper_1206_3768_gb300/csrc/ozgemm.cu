@@ -42,6 +42,8 @@ struct OzPairs {
 };
 
 struct OzParams {
+  int a_lower;             // A^ is the embedding of a lower-triangular matrix: skip zero k-blocks
+  int c_lower;             // only the lower triangle of the complex result is needed
   const __nv_bfloat16* A;  // S_A slices, each Mp x Kp row-major
   const __nv_bfloat16* B;  // S_B slices, each Np x Kp (column j of B^ contiguous)
   int64_t sliceA, sliceB;  // elements per slice
@@ -104,8 +106,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzParams p
   const int wm = warp & 3, wn = warp >> 2;
   const int tm = blockIdx.x % p.tiles_m, tn = blockIdx.x / p.tiles_m;
   const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
+  if (p.c_lower && n0 > (m0 + OZ_BM - 1) / 2) return;
+  const int nkb = p.a_lower ? min(p.nkb, m0 / OZ_BK + OZ_BM / OZ_BK) : p.nkb;
 
-  const int total = p.pairs.n * p.nkb;
+  const int total = p.pairs.n * nkb;
   const int per = (total + p.splits - 1) / p.splits;
   const int q0 = min(total, (int)blockIdx.y * per), q1 = min(total, q0 + per);
 
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzParams p
       for (int c = 0; c < 4; ++c) acc[a][b][c] = hi[a][b][c] = lo[a][b][c] = 0.f;
 
   auto load_stage = [&](int q, int stage) {
-    const int pr = q / p.nkb, kb = q - pr * p.nkb;
+    const int pr = q / nkb, kb = q - pr * nkb;
     const __nv_bfloat16* Ag = p.A + (int64_t)p.pairs.s[pr] * p.sliceA + (int64_t)m0 * p.Kp + kb * OZ_BK;
     const __nv_bfloat16* Bg = p.B + (int64_t)p.pairs.t[pr] * p.sliceB + (int64_t)n0 * p.Kp + kb * OZ_BK;
     const uint32_t sa = smem_u32(sA + stage * OZ_BM * OZ_BK * 2);
@@ -177,8 +181,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzParams p
         for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bf[nt][0], bf[nt][1]);
     }
     // drain the exact FP32 chunk at chunk ends, pair ends and the end of this CTA's range
-    const int pr = q / p.nkb, kb = q - pr * p.nkb;
-    if (((kb + 1) % OZ_CHUNK_KB) == 0 || kb == p.nkb - 1 || q == q1 - 1) {
+    const int pr = q / nkb, kb = q - pr * nkb;
+    if (((kb + 1) % OZ_CHUNK_KB) == 0 || kb == nkb - 1 || q == q1 - 1) {
       const float sc = ldexpf(1.0f, -OZ_BETA * (p.pairs.s[pr] + p.pairs.t[pr] + 2));
 #pragma unroll
       for (int a = 0; a < 2; ++a)
@@ -213,11 +217,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzParams p
 __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int Np, const int* eA,
                                    const int* eB, int n, int m, double alpha, double beta,
                                    const zd* Cin, int64_t ldcin, double gamma, const zd* D,
-                                   int64_t ldd, zd* out, int64_t ldo) {
+                                   int64_t ldd, zd* out, int64_t ldo, int lower) {
   const int64_t total = (int64_t)n * m;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % n), j = (int)(e / n);
+    if (lower && j > i) continue;
     double re = 0.0, im = 0.0;
     for (int s = 0; s < splits; ++s) {
       const double2 v = *reinterpret_cast<const double2*>(part + (int64_t)s * Mp * Np +
@@ -250,6 +255,7 @@ constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB (A) and 16 KB (B) per
 constexpr long kMbarSpinLimit = 1L << 26;
 
 struct TcParams {
+  int a_lower, c_lower;                      // as in OzParams
   int nkb, tiles_m, splits, Mp, Np, n_real;  // n_real: columns of B^ that hold data
   OzPairs pairs;
   double* part;
@@ -386,8 +392,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tm = blockIdx.x % p.tiles_m, tn = blockIdx.x / p.tiles_m;
   const int m0 = tm * TC_BM, n0 = tn * TC_BN;
+  if (p.c_lower && n0 > (m0 + TC_BM - 1) / 2) return;  // tile above the diagonal: not needed
+  const int nkb = p.a_lower ? min(p.nkb, m0 / TC_BK + TC_BM / TC_BK) : p.nkb;
   const int ncols = min(TC_BN, ((p.n_real - n0 + 15) / 16) * 16);  // MMA N for this tile
-  const int total = p.pairs.n * p.nkb;
+  const int total = p.pairs.n * nkb;
   const int per = (total + p.splits - 1) / p.splits;
   const int q0 = min(total, (int)blockIdx.y * per), q1 = min(total, q0 + per);
 
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int i = q - q0, stage = i % TC_STAGES;
         if (i >= TC_STAGES && !mbar_wait(empty0 + 8 * stage, ((i / TC_STAGES) & 1) ^ 1, abort_flag, p.status))
           break;
-        const int pr = q / p.nkb, kb = q - pr * p.nkb;
+        const int pr = q / nkb, kb = q - pr * nkb;
         mbar_expect_tx(full0 + 8 * stage, 2 * TC_TILE_BYTES);
         tma_load_2d(sA_u + stage * TC_TILE_BYTES, &tmA, kb * TC_BK, p.pairs.s[pr] * p.Mp + m0,
                     full0 + 8 * stage);
@@ -449,7 +457,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int i = q - q0, stage = i % TC_STAGES;
         if (!mbar_wait(full0 + 8 * stage, (i / TC_STAGES) & 1, abort_flag, p.status)) break;
         tc_fence_after();
-        const bool start = tc_chunk_start(q, q0, p.nkb);
+        const bool start = tc_chunk_start(q, q0, nkb);
         if (start) {
           ++chunk;
           if (chunk >= 2 && !mbar_wait(acce0 + 8 * (chunk & 1), ((chunk >> 1) - 1) & 1, abort_flag, p.status))
@@ -463,7 +471,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_mma(d, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc,
                  (start && kk == 0) ? 0u : 1u);
         tc_commit(empty0 + 8 * stage);
-        if (tc_chunk_end(q, q1, p.nkb)) tc_commit(accf0 + 8 * (chunk & 1));
+        if (tc_chunk_end(q, q1, nkb)) tc_commit(accf0 + 8 * (chunk & 1));
       }
       // all MMAs issued by this thread are complete once done_bar fires
       tc_commit(done_bar);
@@ -486,12 +494,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int chunk = -1;
     bool ok = true;
     for (int q = q0; q < q1 && ok; ++q) {
-      if (tc_chunk_start(q, q0, p.nkb)) ++chunk;
-      if (!tc_chunk_end(q, q1, p.nkb)) continue;
+      if (tc_chunk_start(q, q0, nkb)) ++chunk;
+      if (!tc_chunk_end(q, q1, nkb)) continue;
       const int b = chunk & 1;
       if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status)) { ok = false; break; }
       tc_fence_after();
-      const int pr = q / p.nkb;
+      const int pr = q / nkb;
       const float sc = ldexpf(1.0f, -OZ_BETA * (p.pairs.s[pr] + p.pairs.t[pr] + 2));
 #pragma unroll 1
       for (int cb = 0; cb < TC_BN / 32; ++cb) {
@@ -607,6 +615,64 @@ __global__ void oz_slice_hermitian_kernel(const zd* Hs, int64_t ldh, int n, int 
   }
 }
 
+
+// Slices from the ROWS of a general complex matrix X (rows x cols, column-major): the row
+// scale needs a full pass over the row, and the row is strided in memory, so 32-row blocks
+// are read column by column (coalesced) and transposed through shared memory.
+//   mode 0 (A operand, real embedding): rows 2r, 2r+1 of A^ = [Re x, -Im x], [Im x, Re x]
+//   mode 1 (B operand of X^H): column r of B^ = conj(row r of X) = [Re x, -Im x]
+__global__ void oz_slice_rows_kernel(const zd* X, int64_t ldx, int rows, int cols, int S, int mode,
+                                     __nv_bfloat16* out, int64_t slice_stride, int Kp, int* e_out) {
+  __shared__ double red[8][32];
+  __shared__ int ex[32];
+  __shared__ zd tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int r0 = blockIdx.x * 32;
+  const int r = r0 + tx;
+  double mx = 0.0;
+  if (r < rows)
+    for (int k = ty; k < cols; k += 8) {
+      const zd v = X[r + (int64_t)k * ldx];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  red[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0) {
+    double m2 = red[0][tx];
+    for (int j = 1; j < 8; ++j) m2 = fmax(m2, red[j][tx]);
+    ex[tx] = exponent_bound(m2);
+    if (r < rows) e_out[r] = ex[tx];
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < cols; k0 += 32) {
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int gr = r0 + tx, gk = k0 + rr;  // read column gk, rows r0..r0+31 (coalesced)
+      tile[rr][tx] = (gr < rows && gk < cols) ? X[gr + (int64_t)gk * ldx] : zmk(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int rr = ty; rr < 32; rr += 8) {  // write row r0 + rr, columns k0 + tx (coalesced)
+      const int gr = r0 + rr, gk = k0 + tx;
+      if (gr < rows && gk < cols) {
+        const zd v = tile[tx][rr];
+        const int e = ex[rr];
+        if (mode == 0) {
+          __nv_bfloat16* o0 = out + (int64_t)(2 * gr) * Kp + 2 * gk;
+          __nv_bfloat16* o1 = o0 + Kp;
+          digits(v.x, e, S, o0, slice_stride);
+          digits(-v.y, e, S, o0 + 1, slice_stride);
+          digits(v.y, e, S, o1, slice_stride);
+          digits(v.x, e, S, o1 + 1, slice_stride);
+        } else {
+          __nv_bfloat16* o0 = out + (int64_t)gr * Kp + 2 * gk;
+          digits(v.x, e, S, o0, slice_stride);
+          digits(-v.y, e, S, o0 + 1, slice_stride);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // B-side slices of Y^ (the n x m complex block read as a 2n x m real array): one CTA per
 // column j; columns j >= m of the padded block are zero.
 __global__ void oz_slice_cols_kernel(const zd* Y, int64_t ldy, int n, int m, int S,
@@ -688,39 +754,81 @@ int oz_padded_n(int m) {
   return oz_use_tcgen05() ? ((m + 15) / 16) * 16 : ((m + OZ_BN - 1) / OZ_BN) * OZ_BN;
 }
 
-cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
-                               cudaStream_t s) {
+static cudaError_t set_a_shape(OzWorkspace& oz, int n, int S) {
   const int Kp = oz_padded_k(n), Mp = oz_padded_m(n);
-  if (S > oz.S_max || Kp > oz.Kp_max || Mp > oz.Mp_max) return cudaErrorInvalidValue;
+  if (S > oz.S_max || S < 1 || Kp > oz.Kp_max || Mp > oz.Mp_max) return cudaErrorInvalidValue;
   oz.Kp = Kp;
   oz.Mp = Mp;
   oz.S_A = S;
   oz.sliceA = (int64_t)Mp * Kp;
-  // zero the padding (rows >= 2n and columns >= 2n) once per slicing
-  cudaError_t e = cudaMemsetAsync(oz.A, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceA, s);
+  return cudaSuccess;
+}
+
+cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
+                               cudaStream_t s) {
+  cudaError_t e = set_a_shape(oz, n, S);
   if (e != cudaSuccess) return e;
-  oz_slice_hermitian_kernel<<<n, 256, 0, s>>>(Hs, ldh, n, S, oz.A, oz.sliceA, Kp, oz.eA);
+  // zero the padding (rows >= 2n and columns >= 2n) once per slicing
+  e = cudaMemsetAsync(oz.A, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceA, s);
+  if (e != cudaSuccess) return e;
+  oz_slice_hermitian_kernel<<<n, 256, 0, s>>>(Hs, ldh, n, S, oz.A, oz.sliceA, oz.Kp, oz.eA);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
-// out(n x m) = alpha Hs Y + beta Cin + gamma D with Hs given by its slices in oz (S_A of
-// them) and Y sliced here into S slices; pairs (s, t) with s + t <= S + 1.
-cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, double alpha,
-                              double beta, const zd* Cin, int64_t ldcin, double gamma, const zd* D,
-                              int64_t ldd, zd* out, int64_t ldo, OzWorkspace& oz, cudaStream_t s,
-                              cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end) {
-  if (m <= 0) return cudaSuccess;
-  if (S > oz.S_A || S < 1) return cudaErrorInvalidValue;
-  const int Np = oz_padded_n(m);
-  if (Np > oz.Np_max) return cudaErrorInvalidValue;
-  const int Kp = oz.Kp, Mp = oz.Mp;
-  const int64_t sliceB = (int64_t)Np * Kp;
-  // B-side slices (padding rows k >= 2n of each column are zeroed by the memset)
-  cudaError_t e = cudaMemsetAsync(oz.B, 0, sizeof(__nv_bfloat16) * (size_t)S * sliceB, s);
+cudaError_t oz_slice_a_rows(const zd* X, int64_t ldx, int n, int S, OzWorkspace& oz, cudaStream_t s) {
+  cudaError_t e = set_a_shape(oz, n, S);
   if (e != cudaSuccess) return e;
-  oz_slice_cols_kernel<<<Np, 256, 0, s>>>(Y, ldy, n, m, S, oz.B, sliceB, Kp, oz.eB);
+  e = cudaMemsetAsync(oz.A, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceA, s);
+  if (e != cudaSuccess) return e;
+  oz_slice_rows_kernel<<<(n + 31) / 32, 256, 0, s>>>(X, ldx, n, n, S, 0, oz.A, oz.sliceA, oz.Kp, oz.eA);
   CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+static cudaError_t set_b_shape(OzWorkspace& oz, int m, int S) {
+  const int Np = oz_padded_n(m);
+  if (Np > oz.Np_max || S > oz.S_A || S < 1) return cudaErrorInvalidValue;
+  oz.Np = Np;
+  oz.m = m;
+  oz.S_B = S;
+  oz.sliceB = (int64_t)Np * oz.Kp;
+  return cudaSuccess;
+}
+
+cudaError_t oz_slice_b_cols(const zd* Y, int64_t ldy, int n, int m, int S, OzWorkspace& oz,
+                            cudaStream_t s) {
+  cudaError_t e = set_b_shape(oz, m, S);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(oz.B, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceB, s);
+  if (e != cudaSuccess) return e;
+  oz_slice_cols_kernel<<<oz.Np, 256, 0, s>>>(Y, ldy, n, m, S, oz.B, oz.sliceB, oz.Kp, oz.eB);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t oz_slice_b_conj_rows(const zd* X, int64_t ldx, int m, int n, int S, OzWorkspace& oz,
+                                 cudaStream_t s) {
+  cudaError_t e = set_b_shape(oz, m, S);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(oz.B, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceB, s);
+  if (e != cudaSuccess) return e;
+  oz_slice_rows_kernel<<<(m + 31) / 32, 256, 0, s>>>(X, ldx, m, n, S, 1, oz.B, oz.sliceB, oz.Kp, oz.eB);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// out(n x m) = alpha A B + beta Cin + gamma D from the current A and B slices (S pairs
+// levels); a_lower: A is lower triangular; c_lower: only the lower triangle of out is
+// written (out must be square).
+cudaError_t oz_run_product(int n, int S, double alpha, double beta, const zd* Cin, int64_t ldcin,
+                           double gamma, const zd* D, int64_t ldd, zd* out, int64_t ldo, int a_lower,
+                           int c_lower, OzWorkspace& oz, cudaStream_t s, cudaEvent_t ev_gemm_begin,
+                           cudaEvent_t ev_gemm_end) {
+  const int m = oz.m, Kp = oz.Kp, Mp = oz.Mp, Np = oz.Np;
+  if (m <= 0) return cudaSuccess;
+  if (S > oz.S_B || S > oz.S_A || S < 1) return cudaErrorInvalidValue;
+  cudaError_t e;
   // Pairs (s, t) with s + t <= S + 1, grouped by the A slice s so that consecutive pairs
   // stream the same slice of the large operand (it stays in L2 between them).
   OzPairs pairs;
@@ -734,6 +842,8 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
   int splits = 1;
   if (oz_use_tcgen05()) {
     TcParams tp;
+    tp.a_lower = a_lower;
+    tp.c_lower = c_lower;
     tp.nkb = Kp / OZ_BK;
     tp.tiles_m = Mp / TC_BM;
     tp.Mp = Mp;
@@ -746,7 +856,7 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
     tp.splits = splits = choose_oz_splits(tiles, pairs.n * tp.nkb, oz.part_elems, (int64_t)Mp * Np);
     CUtensorMap mapA, mapB;
     if (!encode_bf16_map(&mapA, oz.A, Kp, (uint64_t)oz.S_A * Mp) ||
-        !encode_bf16_map(&mapB, oz.B, Kp, (uint64_t)S * Np))
+        !encode_bf16_map(&mapB, oz.B, Kp, (uint64_t)oz.S_B * Np))
       return cudaErrorInvalidValue;
     const size_t smem = 1024 + (size_t)TC_STAGES * 2 * TC_TILE_BYTES + 256;
     static bool tc_attr = false;
@@ -763,10 +873,12 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
     if (e != cudaSuccess) return e;
   } else {
     OzParams p;
+    p.a_lower = a_lower;
+    p.c_lower = c_lower;
     p.A = oz.A;
     p.B = oz.B;
     p.sliceA = oz.sliceA;
-    p.sliceB = sliceB;
+    p.sliceB = oz.sliceB;
     p.Kp = Kp;
     p.nkb = Kp / OZ_BK;
     p.tiles_m = Mp / OZ_BM;
@@ -792,10 +904,24 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
   }
   const int64_t tot = (int64_t)n * m;
   const int blocks = (int)std::min<int64_t>(4 * sm_count(), (tot + 255) / 256);
-  oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, oz.eA, oz.eB, n, m, alpha,
-                                            beta, Cin, ldcin, gamma, D, ldd, out, ldo);
+  oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, oz.eA, oz.eB, n, m, alpha, beta,
+                                            Cin, ldcin, gamma, D, ldd, out, ldo, c_lower);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
+}
+
+// out(n x m) = alpha Hs Y + beta Cin + gamma D with Hs given by its slices in oz (S_A of
+// them) and Y sliced here into S slices; pairs (s, t) with s + t <= S + 1.
+cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, double alpha,
+                              double beta, const zd* Cin, int64_t ldcin, double gamma, const zd* D,
+                              int64_t ldd, zd* out, int64_t ldo, OzWorkspace& oz, cudaStream_t s,
+                              cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end) {
+  if (m <= 0) return cudaSuccess;
+  if (S > oz.S_A || S < 1) return cudaErrorInvalidValue;
+  cudaError_t e = oz_slice_b_cols(Y, ldy, n, m, S, oz, s);
+  if (e != cudaSuccess) return e;
+  return oz_run_product(n, S, alpha, beta, Cin, ldcin, gamma, D, ldd, out, ldo, 0, 0, oz, s,
+                        ev_gemm_begin, ev_gemm_end);
 }
 
 int64_t oz_pair_count(int S) { return (int64_t)S * (S + 1) / 2; }
@@ -804,7 +930,9 @@ cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max) {
   oz.S_max = S_max;
   oz.Kp_max = oz_padded_k(n_max);
   oz.Mp_max = oz_padded_m(n_max);
-  oz.Np_max = ((blk_max + OZ_BN - 1) / OZ_BN) * OZ_BN;  // covers both kernels' paddings
+  // B operands: blocks of up to blk_max columns, and n_max columns for the reduction
+  const int cols = std::max(n_max, blk_max);
+  oz.Np_max = ((cols + OZ_BN - 1) / OZ_BN) * OZ_BN;  // covers both kernels' paddings
   cudaError_t e;
   e = cudaMalloc((void**)&oz.A, sizeof(__nv_bfloat16) * (size_t)S_max * oz.Mp_max * oz.Kp_max);
   if (e != cudaSuccess) return e;
@@ -814,7 +942,8 @@ cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max) {
   if (e != cudaSuccess) return e;
   e = cudaMalloc((void**)&oz.eB, sizeof(int) * (size_t)oz.Np_max);
   if (e != cudaSuccess) return e;
-  oz.part_elems = (size_t)16 * oz.Mp_max * oz.Np_max;
+  const int np_blk = ((blk_max + OZ_BN - 1) / OZ_BN) * OZ_BN;
+  oz.part_elems = std::max((size_t)16 * oz.Mp_max * np_blk, (size_t)oz.Mp_max * oz.Np_max);
   e = cudaMalloc((void**)&oz.part, sizeof(double) * oz.part_elems);
   return e;
 }

@@ -100,13 +100,22 @@ def test_cholesky_reports_not_positive_definite(ctx):
     assert np.all(np.isfinite(L))
 
 
+@pytest.fixture(scope="module")
+def ctx64():
+    s = cb.Solver(700, 160, precision=0)
+    yield s.ctx
+    s.close()
+
+
 @pytest.mark.parametrize("n", [64, 257, 640])
-def test_reduce_matches_oracle(ctx, n):
+@pytest.mark.parametrize("mode", ["split", "fp64"])
+def test_reduce_matches_oracle(ctx, ctx64, n, mode):
     rng = _rng(n + 1)
     A = _herm(rng, n, 3.0)
     B = _hpd(rng, n)
     Lo = O.cholesky_lower(np.tril(B))
-    H = _np(cb.chfsi_reduce(ctx, _t(np.tril(A)), _t(Lo)))
+    c = ctx if mode == "split" else ctx64
+    H = _np(cb.chfsi_reduce(c, _t(np.tril(A)), _t(Lo)))
     Ho = O.reduce_standard(np.tril(A), Lo)
     assert np.allclose(H, H.conj().T, atol=0)
     assert _rel(H, Ho) < 1e-12
@@ -197,14 +206,15 @@ def test_orthonormalize_survives_near_rank_deficiency(ctx):
 
 
 @pytest.mark.parametrize("n,m", [(300, 25), (640, 130), (513, 131)])
-def test_rayleigh_ritz_matches_oracle(ctx, n, m):
+@pytest.mark.parametrize("mode", ["split", "fp64"])
+def test_rayleigh_ritz_matches_oracle(ctx, ctx64, n, m, mode):
     rng = _rng(n * m)
     lam = np.sort(rng.uniform(-1, 4, n))
     Q, _ = np.linalg.qr(_cgauss(rng, n, n))
     H = (Q * lam) @ Q.conj().T
     H = 0.5 * (H + H.conj().T)
     S = np.linalg.qr(Q[:, :m] + 1e-3 * _cgauss(rng, n, m))[0]
-    theta, Y, HY = cb.chfsi_rayleigh_ritz(ctx, _t(H), _t(S))
+    theta, Y, HY = cb.chfsi_rayleigh_ritz(ctx if mode == "split" else ctx64, _t(H), _t(S))
     th_o, Y_o, W_o = O.rayleigh_ritz(H, S)
     theta, Y, HY = _np(theta), _np(Y), _np(HY)
     assert np.max(np.abs(theta - th_o)) < 1e-12 * np.max(np.abs(lam))

@@ -254,8 +254,8 @@ def run_ours(args):
                     "peak_note": f"FP64 = {peak_kind} bf16 sustained x 1.25/2250 (nominal FP64/bf16 "
                                  "ratio); achieved counts 8 flops per complex FMA"}
     phase = {k: sum(s[k] for s in all_stats) / args.steps for k in
-             ("t_reduce_ms", "t_lanczos_ms", "t_filter_ms", "t_filter_gemm_ms", "t_qr_ms", "t_rr_ms",
-              "t_resid_ms", "t_total_ms")}
+             ("t_reduce_ms", "t_lanczos_ms", "t_filter_ms", "t_filter_gemm_ms", "t_qr_ms", "t_small_ms",
+              "t_rr_ms", "t_eig_ms", "t_resid_ms", "t_total_ms")}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
     e2e = None

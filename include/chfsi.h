@@ -77,6 +77,8 @@ typedef struct {
   double lanczos_upper;      /* spectral upper bound b used by the filter */
   double t_reduce_ms, t_lanczos_ms, t_filter_ms, t_qr_ms, t_rr_ms, t_resid_ms, t_total_ms;
   double t_filter_gemm_ms;   /* device time of the filter's product kernels alone */
+  double t_small_ms;         /* Cholesky QR factorisations of the Gram matrices (within t_qr) */
+  double t_eig_ms;           /* Rayleigh-Ritz eigensolver (within t_rr) */
 } chfsi_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -46,7 +46,8 @@ class chfsi_stats(ctypes.Structure):
                 ("tensor_flops", c_double), ("max_resid", c_double),
                 ("lanczos_upper", c_double), ("t_reduce_ms", c_double), ("t_lanczos_ms", c_double),
                 ("t_filter_ms", c_double), ("t_qr_ms", c_double), ("t_rr_ms", c_double),
-                ("t_resid_ms", c_double), ("t_total_ms", c_double), ("t_filter_gemm_ms", c_double)]
+                ("t_resid_ms", c_double), ("t_total_ms", c_double), ("t_filter_gemm_ms", c_double),
+                ("t_small_ms", c_double), ("t_eig_ms", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -43,7 +43,7 @@ struct chfsi_ctx {
 
 namespace {
 
-enum Phase { PH_REDUCE = 0, PH_LANCZOS, PH_FILTER, PH_QR, PH_RR, PH_RESID, PH_FGEMM, PH_N };
+enum Phase { PH_REDUCE = 0, PH_LANCZOS, PH_FILTER, PH_QR, PH_RR, PH_RESID, PH_FGEMM, PH_SMALL, PH_EIG, PH_N };
 
 int set_err(chfsi_ctx* c, int code, const char* fmt, ...) {
   char buf[512];
@@ -161,6 +161,21 @@ int gemm(chfsi_ctx* ctx, const GemmDesc& g) {
   return CHFSI_OK;
 }
 
+// A dense product in the context's precision: in mixed mode, products large enough to
+// amortise the slicing run as 8-slice split-BF16 tensor-core products (FP64-level accuracy;
+// triangular operands are used with their exact zeros), the rest as FP64 GEMMs.
+int gemm_auto(chfsi_ctx* ctx, const GemmDesc& g) {
+  const double work = (double)g.M * g.N * g.K;
+  const bool square_c = !g.lowerC || g.M == g.N;
+  if (ctx->opts.precision == 1 && work >= 16777216.0 && square_c) {
+    CK(oz_gemm(g.opA, g.A, g.lda, g.opB, g.B, g.ldb, g.M, g.N, g.K, 8, g.alpha, g.beta, g.Cin,
+               g.ldcin, g.gamma, g.D, g.ldd, g.C, g.ldc, g.triA == 1, g.lowerC, ctx->ws.oz,
+               ctx->stream));
+    return CHFSI_OK;
+  }
+  return gemm(ctx, g);
+}
+
 // C(MxN) = alpha op(A) op(B) [+ beta Cin]
 GemmDesc gd(int M, int N, int K, const zd* A, int64_t lda, int opA, const zd* B, int64_t ldb,
             int opB, zd* C, int64_t ldc, double alpha = 1.0) {
@@ -177,10 +192,10 @@ constexpr int NB = 128;  // panel width of the blocked factorisations
 constexpr int kRRSlices = 8;  // digit slices of the Rayleigh-Ritz product Hs Y in mixed mode
 
 // In-place blocked right-looking Cholesky on the lower triangle of L (n x n).
-int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n) {
+int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n, int nb = NB) {
   Workspace& ws = ctx->ws;
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = std::min(NB, n - k0);
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int kb = std::min(nb, n - k0);
     zd* L11 = L + k0 + (int64_t)k0 * ld;
     CK(small_cholesky(L11, ld, kb, 0, 0, 0.0, nullptr, nullptr, ws.status, ws.status + 1, k0,
                       ctx->stream));
@@ -206,11 +221,11 @@ int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n) {
 
 // X = L^{-1} (n x n, lower) by block rows: X_II = inv(L_II),
 // X[I, 0:I] = -X_II (L[I, 0:I] X[0:I, 0:I]).
-int blocked_trinv(chfsi_ctx* ctx, const zd* L, int64_t ld, zd* X, int64_t ldx, int n) {
+int blocked_trinv(chfsi_ctx* ctx, const zd* L, int64_t ld, zd* X, int64_t ldx, int n, int nb = NB) {
   Workspace& ws = ctx->ws;
   CK(cudaMemset2DAsync(X, ldx * sizeof(zd), 0, n * sizeof(zd), n, ctx->stream));
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = std::min(NB, n - k0);
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int kb = std::min(nb, n - k0);
     CK(trinv_lower(L + k0 + (int64_t)k0 * ld, ld, X + k0 + (int64_t)k0 * ldx, ldx, kb, ctx->stream));
     if (k0 == 0) continue;
     // Zt = L[I, 0:k0] X[0:k0, 0:k0]  (kb x k0), X lower => op(B)(k, j) = 0 for k < j
@@ -233,12 +248,10 @@ int reduce_to_standard(chfsi_ctx* ctx, const zd* Af, int64_t lda, const zd* Linv
   Workspace& ws = ctx->ws;
   if (split) {
     const int S = kRRSlices;
-    CK(oz_slice_a_rows(Linv, ldl, n, S, ws.oz, ctx->stream));
-    CK(oz_slice_b_cols(Af, lda, n, n, S, ws.oz, ctx->stream));
-    CK(oz_run_product(n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, ws.T, ws.n_max, 1, 0, ws.oz,
-                      ctx->stream));
-    CK(oz_slice_b_conj_rows(ws.T, ws.n_max, n, n, S, ws.oz, ctx->stream));
-    CK(oz_run_product(n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, Hs, ldh, 1, 1, ws.oz, ctx->stream));
+    CK(oz_gemm(OPN, Linv, ldl, OPN, Af, lda, n, n, n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, ws.T,
+               ws.n_max, 1, 0, ws.oz, ctx->stream));
+    CK(oz_gemm(OPN, Linv, ldl, OPC, ws.T, ws.n_max, n, n, n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
+               Hs, ldh, 1, 1, ws.oz, ctx->stream));
     CK(mirror_lower(Hs, ldh, n, ctx->stream));
     return CHFSI_OK;
   }
@@ -327,8 +340,8 @@ int filter_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya
       CK(oz_filter_product(cur, ld, n, mk, slices, al, be, cur, ld, k >= 2 ? ga : 0.0, out, ld, out,
                            ld, ws.oz, ctx->stream, gb, ge));
       if (st) {
-        st->tensor_flops += 2.0 * (double)oz_pair_count(slices) * ws.oz.Mp *
-                            (double)oz_padded_n(mk) * ws.oz.Kp;
+        st->tensor_flops += 2.0 * (double)oz_pair_count(slices) * ws.oz.H.Mp *
+                            (double)oz_padded_n(mk) * ws.oz.H.Kp;
       }
     } else {
       GemmDesc g = gd(n, mk, n, H, ldh, OPN, cur, ld, OPN, out, ld, al);
@@ -369,7 +382,12 @@ int slices_for_loop(double hs_norm, double tau, double r_min, double a0, double 
   if (t0 > 1.0) T = std::cosh(dmax * std::acosh(t0));
   if (!std::isfinite(T)) T = 1e300;
   const double target = std::max(tau, r_min / (10.0 * T));
-  const double bits = std::log2(hs_norm / target) + 6.0;
+  static double margin = -1.0;
+  if (margin < 0.0) {
+    const char* v = std::getenv("CHFSI_SLICE_MARGIN_BITS");
+    margin = v ? std::atof(v) : 6.0;
+  }
+  const double bits = std::log2(hs_norm / target) + margin;
   const int S = (int)std::ceil(bits / 7.0);
   return std::min(s_max, std::max(2, S));
 }
@@ -383,10 +401,10 @@ int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const z
   if (m <= 0) return CHFSI_OK;
   if (k > 0) {
     for (int pass = 0; pass < 2; ++pass) {
-      CKS(gemm(ctx, gd(k, m, n, YL, ldyl, OPC, *Ya, ld, OPN, ws.G, ldm)));
+      CKS(gemm_auto(ctx, gd(k, m, n, YL, ldyl, OPC, *Ya, ld, OPN, ws.G, ldm)));
       GemmDesc g = gd(n, m, k, YL, ldyl, OPN, ws.G, ldm, OPN, *Ya, ld, -1.0);
       g.beta = 1.0; g.Cin = *Ya; g.ldcin = ld;
-      CKS(gemm(ctx, g));
+      CKS(gemm_auto(ctx, g));
     }
   }
   const double u = 1.1102230246251565e-16;
@@ -402,14 +420,17 @@ int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const z
     }
     GemmDesc g = gd(m, m, n, *Ya, ld, OPC, *Ya, ld, OPN, ws.G, ldm);
     g.lowerC = 1;
-    CKS(gemm(ctx, g));
-    CK(small_cholesky(ws.G, ldm, m, 1, 1, shift_base, ws.dscale, ws.jac, ws.status, ws.status + 1, 0,
-                      ctx->stream, pass == 0 ? ws.shiftflag : nullptr));
-    CK(trinv_lower(ws.G, ldm, ws.Rt, ldm, m, ctx->stream));
-    CK(cholqr_T(ws.Rt, ldm, m, ws.dscale, ws.V, ldm, ctx->stream));
+    CKS(gemm_auto(ctx, g));
+    {
+      PhaseScope ps(ctx, PH_SMALL);
+      CK(small_cholesky(ws.G, ldm, m, 1, 1, shift_base, ws.dscale, ws.jac, ws.status, ws.status + 1, 0,
+                        ctx->stream, pass == 0 ? ws.shiftflag : nullptr));
+      CK(trinv_lower(ws.G, ldm, ws.Rt, ldm, m, ctx->stream));
+      CK(cholqr_T(ws.Rt, ldm, m, ws.dscale, ws.V, ldm, ctx->stream));
+    }
     GemmDesc h = gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld);
     h.triB = 1;
-    CKS(gemm(ctx, h));
+    CKS(gemm_auto(ctx, h));
     std::swap(*Ya, *Yb);
   }
   return CHFSI_OK;
@@ -430,11 +451,14 @@ int rayleigh_ritz_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, 
   }
   GemmDesc g = gd(m, m, n, *Ya, ld, OPC, *W, ld, OPN, ws.G, ldm);
   g.lowerC = 1;
-  CKS(gemm(ctx, g));
+  CKS(gemm_auto(ctx, g));
   CK(mirror_lower(ws.G, ldm, m, ctx->stream));
-  CK(jacobi_heev(ws.G, ldm, m, theta, ws.V, ldm, ws.jac, ws.barrier, ws.status, ctx->stream));
-  CKS(gemm(ctx, gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld)));
-  CKS(gemm(ctx, gd(n, m, m, *W, ld, OPN, ws.V, ldm, OPN, *Zb, ld)));
+  {
+    PhaseScope ps(ctx, PH_EIG);
+    CK(jacobi_heev(ws.G, ldm, m, theta, ws.V, ldm, ws.jac, ws.barrier, ws.status, ctx->stream));
+  }
+  CKS(gemm_auto(ctx, gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld)));
+  CKS(gemm_auto(ctx, gd(n, m, m, *W, ld, OPN, ws.V, ldm, OPN, *Zb, ld)));
   std::swap(*Ya, *Yb);
   std::swap(*W, *Zb);
   return CHFSI_OK;
@@ -547,7 +571,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   if (warm) {
     GemmDesc g = gd(n, blk, n, ws.Lf, ld, OPC, ws.Xw, ld, OPN, Ya, ld);
     g.triA = 2;
-    CKS(gemm(ctx, g));
+    CKS(gemm_auto(ctx, g));
   } else if (S.V0) {
     const zd* v0 = nullptr;
     CKS(stage_in(ctx, S.V0, n, n, blk, Yb, ld, &v0));
@@ -701,9 +725,9 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       PhaseScope ps(ctx, PH_RESID);
       GemmDesc g1 = gd(n, conv, n, ws.Linv, ld, OPC, ws.YL, ld, OPN, ws.Xw, ld);
       g1.triA = 2;
-      CKS(gemm(ctx, g1));
-      CKS(gemm(ctx, gd(n, nev, n, ws.Af, ld, OPN, ws.Xw, ld, OPN, W, ld)));
-      CKS(gemm(ctx, gd(n, nev, n, ws.Bf, ld, OPN, ws.Xw, ld, OPN, Zb, ld)));
+      CKS(gemm_auto(ctx, g1));
+      CKS(gemm_auto(ctx, gd(n, nev, n, ws.Af, ld, OPN, ws.Xw, ld, OPN, W, ld)));
+      CKS(gemm_auto(ctx, gd(n, nev, n, ws.Bf, ld, OPN, ws.Xw, ld, OPN, Zb, ld)));
       CK(generalized_residuals(W, ld, Zb, ld, ws.Xw, ld, ws.lamL, n, nev, ws.scal + 6, ws.gres,
                                ctx->stream));
     }
@@ -737,10 +761,10 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   {
     GemmDesc g1 = gd(n, conv, n, ws.Linv, ld, OPC, ws.YL, ld, OPN, ws.Xw, ld);
     g1.triA = 2;
-    CKS(gemm(ctx, g1));
+    CKS(gemm_auto(ctx, g1));
     GemmDesc g2 = gd(n, blk - conv, n, ws.Linv, ld, OPC, Ya, ld, OPN, ws.Xw + (int64_t)conv * ld, ld);
     g2.triA = 2;
-    CKS(gemm(ctx, g2));
+    CKS(gemm_auto(ctx, g2));
   }
   std::vector<double> lam_out(nev, NAN);
   for (int i = 0; i < std::min(conv, nev); ++i) lam_out[i] = lamL[i];
@@ -779,6 +803,8 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   st.t_rr_ms = tph[PH_RR];
   st.t_resid_ms = tph[PH_RESID];
   st.t_filter_gemm_ms = tph[PH_FGEMM];
+  st.t_small_ms = tph[PH_SMALL];
+  st.t_eig_ms = tph[PH_EIG];
   st.t_total_ms = tot;
   if (S.st) *S.st = st;
   return status;

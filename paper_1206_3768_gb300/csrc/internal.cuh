@@ -77,6 +77,9 @@ cudaError_t small_cholesky(zd* G, int64_t ldg, int m, int scale, int shift_on_fa
                            int info_base, cudaStream_t s, int* shift_flag = nullptr);
 // X = L^{-1} for an m x m lower-triangular L (strict upper of X zeroed).  X != L.
 cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m, cudaStream_t s);
+// Unit-diagonal scaling of a Gram matrix (lower) with a backup copy, and the shifted restore.
+cudaError_t gram_scale(zd* G, int64_t ldg, int m, double* dscale, zd* backup, cudaStream_t s);
+cudaError_t gram_shift(const zd* backup, int m, double shift_base, zd* G, int64_t ldg, cudaStream_t s);
 // T = D X^H (upper triangular, zero below): the right factor of Cholesky QR, Q = Y T.
 cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* T, int64_t ldt,
                      cudaStream_t s);
@@ -126,17 +129,25 @@ cudaError_t tridiag_extremes(const double* alpha, const double* beta, int k, dou
                              cudaStream_t s);
 
 // ------------------------------------------------------------------ split-BF16 products
+struct OzA {                        // A operand: S digit slices of op(A) (M x K complex)
+  struct __nv_bfloat16* ptr = nullptr;
+  int* e = nullptr;                 // power-of-two scale per complex row
+  int S = 0, M = 0, K = 0, Mp = 0, Kp = 0;
+  int64_t slice = 0;
+  int S_max = 0, Mp_max = 0, Kp_max = 0;
+};
+struct OzB {                        // B operand: S digit slices of op(B) (K x N complex)
+  struct __nv_bfloat16* ptr = nullptr;
+  int* e = nullptr;                 // power-of-two scale per column
+  int S = 0, N = 0, Np = 0, Kp = 0;
+  int64_t slice = 0;
+  int S_max = 0, Np_max = 0, Kp_max = 0;
+};
 struct OzWorkspace {
-  int S_max = 0, Kp_max = 0, Mp_max = 0, Np_max = 0;
-  int S_A = 0, Kp = 0, Mp = 0;      // current slicing of the A operand
-  int64_t sliceA = 0;
-  int S_B = 0, Np = 0, m = 0;       // current slicing of the B operand (m columns)
-  int64_t sliceB = 0;
-  struct __nv_bfloat16* A = nullptr;
-  struct __nv_bfloat16* B = nullptr;
-  int* eA = nullptr;
-  int* eB = nullptr;
-  double* part = nullptr;
+  OzA H;                            // slices of the problem's Hs (kept for the whole solve)
+  OzA X;                            // scratch A operand of general products
+  OzB B;                            // scratch B operand
+  double* part = nullptr;           // split-K partial sums
   size_t part_elems = 0;
   int* status = nullptr;            // device status word for bounded-wait timeouts
 };
@@ -147,27 +158,28 @@ int oz_padded_n(int m);
 int64_t oz_pair_count(int S);
 cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max);
 void oz_free(OzWorkspace& oz);
-// Digit slices of the real embedding of the Hermitian Hs (once per problem).
+// Digit slices of op(A) = X (op N: rows of X, M x K) or X^H (op C: conj columns of X, K x M).
+cudaError_t oz_slice_a(OzA& a, int op, const zd* X, int64_t ldx, int M, int K, int S, cudaStream_t s);
+// Digit slices of op(B) = X (op N: columns, K x N) or X^H (op C: conj rows of X, N x K).
+cudaError_t oz_slice_b(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, int S, int Kp,
+                       cudaStream_t s);
+cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double beta, const zd* Cin,
+                       int64_t ldcin, double gamma, const zd* D, int64_t ldd, zd* out, int64_t ldo,
+                       int a_lower, int c_lower, OzWorkspace& oz, cudaStream_t s,
+                       cudaEvent_t ev_gemm_begin = nullptr, cudaEvent_t ev_gemm_end = nullptr);
+// Slices of the Hermitian Hs into oz.H (once per problem).
 cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
                                cudaStream_t s);
-// Digit slices of the rows of a general square X as the A operand.
-cudaError_t oz_slice_a_rows(const zd* X, int64_t ldx, int n, int S, OzWorkspace& oz, cudaStream_t s);
-// Digit slices of the columns of Y (n x m) as the B operand.
-cudaError_t oz_slice_b_cols(const zd* Y, int64_t ldy, int n, int m, int S, OzWorkspace& oz,
-                            cudaStream_t s);
-// Digit slices of X^H (X: m x n) as the B operand: column r = conj(row r of X).
-cudaError_t oz_slice_b_conj_rows(const zd* X, int64_t ldx, int m, int n, int S, OzWorkspace& oz,
-                                 cudaStream_t s);
-// out = alpha A B + beta Cin + gamma D from the current slices.
-cudaError_t oz_run_product(int n, int S, double alpha, double beta, const zd* Cin, int64_t ldcin,
-                           double gamma, const zd* D, int64_t ldd, zd* out, int64_t ldo, int a_lower,
-                           int c_lower, OzWorkspace& oz, cudaStream_t s,
-                           cudaEvent_t ev_gemm_begin = nullptr, cudaEvent_t ev_gemm_end = nullptr);
-// out = alpha Hs Y + beta Cin + gamma D with S-slice split-BF16 products.
+// out = alpha Hs Y + beta Cin + gamma D with S-slice split-BF16 products (Hs from oz.H).
 cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, double alpha,
                               double beta, const zd* Cin, int64_t ldcin, double gamma, const zd* D,
                               int64_t ldd, zd* out, int64_t ldo, OzWorkspace& oz, cudaStream_t s,
                               cudaEvent_t ev_gemm_begin = nullptr, cudaEvent_t ev_gemm_end = nullptr);
+// General split product on the scratch operands.
+cudaError_t oz_gemm(int opA, const zd* A, int64_t lda, int opB, const zd* B, int64_t ldb, int M, int N,
+                    int K, int S, double alpha, double beta, const zd* Cin, int64_t ldcin, double gamma,
+                    const zd* D, int64_t ldd, zd* C, int64_t ldc, int a_lower, int c_lower,
+                    OzWorkspace& oz, cudaStream_t s);
 
 // ------------------------------------------------------------------ workspace
 struct Workspace {

@@ -5,12 +5,12 @@
 // (re, im), so that Y^ and C^ are the complex column-major arrays read as real arrays)
 // with the 2n x m real Y^.  Each operand is split into S "digit slices":
 //
-//     H^(r, k) = 2^{eA(r)} sum_s a_s(r, k) 2^{-7 s},   a_1 in [-128, 128], a_{s>1} in [-64, 64]
+//     H^(r, k) = 2^{eA(r)} sum_s a_s(r, k) 2^{-7 s},   |a_1| <= 129, |a_{s>1}| <= 64
 //     Y^(k, j) = 2^{eB(j)} sum_t b_t(k, j) 2^{-7 t}
 //
 // with power-of-two scales per (complex) row of Hs and per column of Y.  Every digit is an
 // integer that bf16 holds exactly, every digit product is exact in FP32, and a sum of at
-// most 1024 such products stays below 2^24, so each K-chunk of 1024 accumulates EXACTLY in
+// most 960 such products stays below 2^24, so each K-chunk of 960 accumulates EXACTLY in
 // the FP32 accumulators of mma.sync.m16n8k16 (bf16 inputs, FP32 accumulation).  Chunks
 // are scaled by 2^{-7(s+t)} (exact) and summed in double-float (FP32 pairs), and slice
 // pairs with s + t <= S + 1 are kept.  The truncation error of the kept pairs is about
@@ -33,7 +33,7 @@ namespace {
 
 constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64, OZ_THREADS = 256, OZ_STAGES = 3;
 constexpr int OZ_BETA = 7;         // bits per digit slice
-constexpr int OZ_CHUNK_KB = 16;    // k-blocks of 64 per exact FP32 chunk (1024)
+constexpr int OZ_CHUNK_KB = 15;    // k-blocks of 64 per exact FP32 chunk (960 terms: 960 * 129^2 < 2^24)
 constexpr int OZ_MAX_PAIRS = 64;
 
 struct OzPairs {
@@ -549,40 +549,81 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
 }
 
-__device__ __forceinline__ int exponent_bound(double mx) {
-  // smallest e with mx < 2^e (0 for mx == 0)
-  if (!(mx > 0.0)) return 0;
-  int e;
-  frexp(mx, &e);
-  return e;
+// Digit extraction with integer operations only (the FP64 pipe of this part is 1/64 of the
+// FP32 rate, so shifting the 53-bit significand is much cheaper than FP64 arithmetic).
+// |x| is a non-negative double: its bit pattern orders like its value.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
-
-// Digits of x (|x| < 2^e) for S slices: x 2^{7-e} = d_1 + 2^{-7} d_2 + ...
+// smallest e with max < 2^e, from the bit pattern of max (0 for max == 0)
+__device__ __forceinline__ int exponent_from_bits(unsigned long long mb) {
+  if (mb == 0) return 0;
+  const int E = (int)(mb >> 52);
+  return (E ? E : 1) - 1022;
+}
+// Balanced digits of x (|x| < 2^e), computed with integer operations: y = |x| 2^{-e} is
+// rounded to 7S fractional bits, split into base-128 digits, and re-centred from the least
+// significant end (a digit >= 64 becomes digit - 128 with a carry into the next one), so
+// that digits 2..S lie in [-64, 63] and digit 1 in [0, 129]; the sign of x is applied to all.
+// Then |x - 2^e sum_k d_k 2^{-7k}| <= 2^{e-7S-1}, and the dropped slice pairs of a product
+// carry digits of both signs (they largely cancel).  Every digit is exact in bf16.
 __device__ __forceinline__ void digits(double x, int e, int S, __nv_bfloat16* out, int64_t stride) {
-  double r = ldexp(x, OZ_BETA - e);
-  for (int s = 0; s < S; ++s) {
-    const double d = rint(r);
-    out[s * stride] = __float2bfloat16_rn((float)d);
-    r = ldexp(r - d, OZ_BETA);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  const bool neg = (bits >> 63) != 0;
+  unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+  const int Eu = (E ? E : 1) - 1075;  // x = mant * 2^Eu
+  const int sh_last = e - Eu - OZ_BETA * S;
+  if (sh_last >= 1 && sh_last <= 63) mant += 1ull << (sh_last - 1);  // round half up (magnitude)
+  int d[8];
+#pragma unroll
+  for (int k = 1; k <= 8; ++k) {
+    if (k > S) break;
+    const int sh = e - Eu - OZ_BETA * k;  // right shift that leaves digit k in the low bits
+    unsigned long long w;
+    if (sh >= 64) w = 0ull;
+    else if (sh >= 0) w = mant >> sh;
+    else w = mant << (-sh);
+    d[k - 1] = (k == 1) ? (int)w : (int)(w & 127ull);
+  }
+#pragma unroll
+  for (int k = 8; k >= 2; --k) {
+    if (k > S) continue;
+    if (d[k - 1] >= 64) {
+      d[k - 1] -= 128;
+      d[k - 2] += 1;
+    }
+  }
+#pragma unroll
+  for (int k = 1; k <= 8; ++k) {
+    if (k > S) break;
+    const float v = (float)(neg ? -d[k - 1] : d[k - 1]);
+    out[(int64_t)(k - 1) * stride] = __float2bfloat16_rn(v);
   }
 }
 
-__device__ double block_max(double v) {
-  __shared__ double sh[32];
-  __shared__ double res;
+__device__ unsigned long long block_max_bits(unsigned long long v) {
+  __shared__ unsigned long long sh[32];
+  __shared__ unsigned long long res;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
   if (lane == 0) sh[w] = v;
   __syncthreads();
   if (w == 0) {
-    double t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    unsigned long long t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0ull;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, t, o);
+      t = u > t ? u : t;
+    }
     if (lane == 0) res = t;
   }
   __syncthreads();
-  const double r = res;
+  const unsigned long long r = res;
   __syncthreads();
   return r;
 }
@@ -593,15 +634,18 @@ __device__ double block_max(double v) {
 //   [ Im h   Re h ]
 __global__ void oz_slice_hermitian_kernel(const zd* Hs, int64_t ldh, int n, int S,
                                           __nv_bfloat16* A, int64_t sliceA, int Kp, int* eA) {
+  // (n = K: the length of column i of X, i.e. of row i of op(A) = X^H)
   const int i = blockIdx.x;
   const zd* col = Hs + (int64_t)i * ldh;
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const zd h = col[k];
-    mx = fmax(mx, fmax(fabs(h.x), fabs(h.y)));
+    const unsigned long long a = abs_bits(h.x), b = abs_bits(h.y);
+    mx = a > mx ? a : mx;
+    mx = b > mx ? b : mx;
   }
-  mx = block_max(mx);
-  const int e = exponent_bound(mx);
+  mx = block_max_bits(mx);
+  const int e = exponent_from_bits(mx);
   if (threadIdx.x == 0) eA[i] = e;
   __nv_bfloat16* r0 = A + (int64_t)(2 * i) * Kp;
   __nv_bfloat16* r1 = r0 + Kp;
@@ -623,24 +667,26 @@ __global__ void oz_slice_hermitian_kernel(const zd* Hs, int64_t ldh, int n, int 
 //   mode 1 (B operand of X^H): column r of B^ = conj(row r of X) = [Re x, -Im x]
 __global__ void oz_slice_rows_kernel(const zd* X, int64_t ldx, int rows, int cols, int S, int mode,
                                      __nv_bfloat16* out, int64_t slice_stride, int Kp, int* e_out) {
-  __shared__ double red[8][32];
+  __shared__ unsigned long long red[8][32];
   __shared__ int ex[32];
   __shared__ zd tile[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int r0 = blockIdx.x * 32;
   const int r = r0 + tx;
-  double mx = 0.0;
+  unsigned long long mx = 0ull;
   if (r < rows)
     for (int k = ty; k < cols; k += 8) {
       const zd v = X[r + (int64_t)k * ldx];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+      const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
+      mx = a > mx ? a : mx;
+      mx = b > mx ? b : mx;
     }
   red[ty][tx] = mx;
   __syncthreads();
   if (ty == 0) {
-    double m2 = red[0][tx];
-    for (int j = 1; j < 8; ++j) m2 = fmax(m2, red[j][tx]);
-    ex[tx] = exponent_bound(m2);
+    unsigned long long m2 = red[0][tx];
+    for (int j = 1; j < 8; ++j) m2 = red[j][tx] > m2 ? red[j][tx] : m2;
+    ex[tx] = exponent_from_bits(m2);
     if (r < rows) e_out[r] = ex[tx];
   }
   __syncthreads();
@@ -686,10 +732,14 @@ __global__ void oz_slice_cols_kernel(const zd* Y, int64_t ldy, int n, int m, int
     return;
   }
   const zd* y = Y + (int64_t)j * ldy;
-  double mx = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) mx = fmax(mx, fmax(fabs(y[k].x), fabs(y[k].y)));
-  mx = block_max(mx);
-  const int e = exponent_bound(mx);
+  unsigned long long mx = 0ull;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const unsigned long long a = abs_bits(y[k].x), b = abs_bits(y[k].y);
+    mx = a > mx ? a : mx;
+    mx = b > mx ? b : mx;
+  }
+  mx = block_max_bits(mx);
+  const int e = exponent_from_bits(mx);
   if (threadIdx.x == 0) eB[j] = e;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const zd v = y[k];
@@ -754,80 +804,54 @@ int oz_padded_n(int m) {
   return oz_use_tcgen05() ? ((m + 15) / 16) * 16 : ((m + OZ_BN - 1) / OZ_BN) * OZ_BN;
 }
 
-static cudaError_t set_a_shape(OzWorkspace& oz, int n, int S) {
-  const int Kp = oz_padded_k(n), Mp = oz_padded_m(n);
-  if (S > oz.S_max || S < 1 || Kp > oz.Kp_max || Mp > oz.Mp_max) return cudaErrorInvalidValue;
-  oz.Kp = Kp;
-  oz.Mp = Mp;
-  oz.S_A = S;
-  oz.sliceA = (int64_t)Mp * Kp;
-  return cudaSuccess;
-}
-
-cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
-                               cudaStream_t s) {
-  cudaError_t e = set_a_shape(oz, n, S);
+// ---- operands
+cudaError_t oz_slice_a(OzA& a, int op, const zd* X, int64_t ldx, int M, int K, int S, cudaStream_t s) {
+  const int Kp = oz_padded_k(K), Mp = oz_padded_m(M);
+  if (S > a.S_max || S < 1 || Kp > a.Kp_max || Mp > a.Mp_max || M <= 0 || K <= 0)
+    return cudaErrorInvalidValue;
+  a.S = S; a.M = M; a.K = K; a.Mp = Mp; a.Kp = Kp;
+  a.slice = (int64_t)Mp * Kp;
+  // zero the padding (rows >= 2M, columns >= 2K)
+  cudaError_t e = cudaMemsetAsync(a.ptr, 0, sizeof(__nv_bfloat16) * (size_t)S * a.slice, s);
   if (e != cudaSuccess) return e;
-  // zero the padding (rows >= 2n and columns >= 2n) once per slicing
-  e = cudaMemsetAsync(oz.A, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceA, s);
-  if (e != cudaSuccess) return e;
-  oz_slice_hermitian_kernel<<<n, 256, 0, s>>>(Hs, ldh, n, S, oz.A, oz.sliceA, oz.Kp, oz.eA);
+  if (op == OPC) {
+    // op(A) = X^H: row i of op(A) is conj(column i of X), contiguous (X is K x M)
+    oz_slice_hermitian_kernel<<<M, 256, 0, s>>>(X, ldx, K, S, a.ptr, a.slice, Kp, a.e);
+  } else {
+    oz_slice_rows_kernel<<<(M + 31) / 32, 256, 0, s>>>(X, ldx, M, K, S, 0, a.ptr, a.slice, Kp, a.e);
+  }
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
-cudaError_t oz_slice_a_rows(const zd* X, int64_t ldx, int n, int S, OzWorkspace& oz, cudaStream_t s) {
-  cudaError_t e = set_a_shape(oz, n, S);
+cudaError_t oz_slice_b(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, int S, int Kp,
+                       cudaStream_t s) {
+  const int Np = oz_padded_n(N);
+  if (Np > b.Np_max || Kp > b.Kp_max || S > b.S_max || S < 1 || N <= 0) return cudaErrorInvalidValue;
+  b.S = S; b.N = N; b.Np = Np; b.Kp = Kp;
+  b.slice = (int64_t)Np * Kp;
+  cudaError_t e = cudaMemsetAsync(b.ptr, 0, sizeof(__nv_bfloat16) * (size_t)S * b.slice, s);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(oz.A, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceA, s);
-  if (e != cudaSuccess) return e;
-  oz_slice_rows_kernel<<<(n + 31) / 32, 256, 0, s>>>(X, ldx, n, n, S, 0, oz.A, oz.sliceA, oz.Kp, oz.eA);
+  if (op == OPC) {
+    // op(B) = X^H (X is N x K): column j = conj(row j of X)
+    oz_slice_rows_kernel<<<(N + 31) / 32, 256, 0, s>>>(X, ldx, N, K, S, 1, b.ptr, b.slice, Kp, b.e);
+  } else {
+    oz_slice_cols_kernel<<<Np, 256, 0, s>>>(X, ldx, K, N, S, b.ptr, b.slice, Kp, b.e);
+  }
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
-static cudaError_t set_b_shape(OzWorkspace& oz, int m, int S) {
-  const int Np = oz_padded_n(m);
-  if (Np > oz.Np_max || S > oz.S_A || S < 1) return cudaErrorInvalidValue;
-  oz.Np = Np;
-  oz.m = m;
-  oz.S_B = S;
-  oz.sliceB = (int64_t)Np * oz.Kp;
-  return cudaSuccess;
-}
-
-cudaError_t oz_slice_b_cols(const zd* Y, int64_t ldy, int n, int m, int S, OzWorkspace& oz,
-                            cudaStream_t s) {
-  cudaError_t e = set_b_shape(oz, m, S);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(oz.B, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceB, s);
-  if (e != cudaSuccess) return e;
-  oz_slice_cols_kernel<<<oz.Np, 256, 0, s>>>(Y, ldy, n, m, S, oz.B, oz.sliceB, oz.Kp, oz.eB);
-  CHFSI_COUNT_LAUNCH();
-  return cudaGetLastError();
-}
-
-cudaError_t oz_slice_b_conj_rows(const zd* X, int64_t ldx, int m, int n, int S, OzWorkspace& oz,
-                                 cudaStream_t s) {
-  cudaError_t e = set_b_shape(oz, m, S);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(oz.B, 0, sizeof(__nv_bfloat16) * (size_t)S * oz.sliceB, s);
-  if (e != cudaSuccess) return e;
-  oz_slice_rows_kernel<<<(m + 31) / 32, 256, 0, s>>>(X, ldx, m, n, S, 1, oz.B, oz.sliceB, oz.Kp, oz.eB);
-  CHFSI_COUNT_LAUNCH();
-  return cudaGetLastError();
-}
-
-// out(n x m) = alpha A B + beta Cin + gamma D from the current A and B slices (S pairs
-// levels); a_lower: A is lower triangular; c_lower: only the lower triangle of out is
-// written (out must be square).
-cudaError_t oz_run_product(int n, int S, double alpha, double beta, const zd* Cin, int64_t ldcin,
-                           double gamma, const zd* D, int64_t ldd, zd* out, int64_t ldo, int a_lower,
-                           int c_lower, OzWorkspace& oz, cudaStream_t s, cudaEvent_t ev_gemm_begin,
-                           cudaEvent_t ev_gemm_end) {
-  const int m = oz.m, Kp = oz.Kp, Mp = oz.Mp, Np = oz.Np;
-  if (m <= 0) return cudaSuccess;
-  if (S > oz.S_B || S > oz.S_A || S < 1) return cudaErrorInvalidValue;
+// out (M x N complex, M = a.M, N = b.N) = alpha op(A) op(B) + beta Cin + gamma D from the
+// operands' slices, with the slice pairs (s, t), s + t <= S + 1.  a_lower: op(A) is lower
+// triangular (zero k-blocks skipped); c_lower: only the lower triangle of out is written.
+cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double beta, const zd* Cin,
+                       int64_t ldcin, double gamma, const zd* D, int64_t ldd, zd* out, int64_t ldo,
+                       int a_lower, int c_lower, OzWorkspace& oz, cudaStream_t s,
+                       cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end) {
+  const int n = a.M, m = b.N, Kp = a.Kp, Mp = a.Mp, Np = b.Np;
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (S > b.S || S > a.S || S < 1 || a.Kp != b.Kp) return cudaErrorInvalidValue;
   cudaError_t e;
   // Pairs (s, t) with s + t <= S + 1, grouped by the A slice s so that consecutive pairs
   // stream the same slice of the large operand (it stays in L2 between them).
@@ -855,8 +879,8 @@ cudaError_t oz_run_product(int n, int S, double alpha, double beta, const zd* Ci
     const int tiles = tp.tiles_m * ((Np + TC_BN - 1) / TC_BN);
     tp.splits = splits = choose_oz_splits(tiles, pairs.n * tp.nkb, oz.part_elems, (int64_t)Mp * Np);
     CUtensorMap mapA, mapB;
-    if (!encode_bf16_map(&mapA, oz.A, Kp, (uint64_t)oz.S_A * Mp) ||
-        !encode_bf16_map(&mapB, oz.B, Kp, (uint64_t)oz.S_B * Np))
+    if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)a.S * Mp) ||
+        !encode_bf16_map(&mapB, b.ptr, Kp, (uint64_t)b.S * Np))
       return cudaErrorInvalidValue;
     const size_t smem = 1024 + (size_t)TC_STAGES * 2 * TC_TILE_BYTES + 256;
     static bool tc_attr = false;
@@ -875,10 +899,10 @@ cudaError_t oz_run_product(int n, int S, double alpha, double beta, const zd* Ci
     OzParams p;
     p.a_lower = a_lower;
     p.c_lower = c_lower;
-    p.A = oz.A;
-    p.B = oz.B;
-    p.sliceA = oz.sliceA;
-    p.sliceB = oz.sliceB;
+    p.A = a.ptr;
+    p.B = b.ptr;
+    p.sliceA = a.slice;
+    p.sliceB = b.slice;
     p.Kp = Kp;
     p.nkb = Kp / OZ_BK;
     p.tiles_m = Mp / OZ_BM;
@@ -904,55 +928,80 @@ cudaError_t oz_run_product(int n, int S, double alpha, double beta, const zd* Ci
   }
   const int64_t tot = (int64_t)n * m;
   const int blocks = (int)std::min<int64_t>(4 * sm_count(), (tot + 255) / 256);
-  oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, oz.eA, oz.eB, n, m, alpha, beta,
-                                            Cin, ldcin, gamma, D, ldd, out, ldo, c_lower);
+  oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, a.e, b.e, n, m, alpha, beta, Cin,
+                                            ldcin, gamma, D, ldd, out, ldo, c_lower);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
-// out(n x m) = alpha Hs Y + beta Cin + gamma D with Hs given by its slices in oz (S_A of
-// them) and Y sliced here into S slices; pairs (s, t) with s + t <= S + 1.
+// ---- the Hermitian matrix of the filter (its slices stay in oz.H for the whole problem)
+cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
+                               cudaStream_t s) {
+  return oz_slice_a(oz.H, OPC, Hs, ldh, n, n, S, s);
+}
+
+// out(n x m) = alpha Hs Y + beta Cin + gamma D with Hs given by its slices in oz.H and Y
+// sliced here into S slices.
 cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, double alpha,
                               double beta, const zd* Cin, int64_t ldcin, double gamma, const zd* D,
                               int64_t ldd, zd* out, int64_t ldo, OzWorkspace& oz, cudaStream_t s,
                               cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end) {
   if (m <= 0) return cudaSuccess;
-  if (S > oz.S_A || S < 1) return cudaErrorInvalidValue;
-  cudaError_t e = oz_slice_b_cols(Y, ldy, n, m, S, oz, s);
+  if (S > oz.H.S || S < 1 || oz.H.M != n) return cudaErrorInvalidValue;
+  cudaError_t e = oz_slice_b(oz.B, OPN, Y, ldy, n, m, S, oz.H.Kp, s);
   if (e != cudaSuccess) return e;
-  return oz_run_product(n, S, alpha, beta, Cin, ldcin, gamma, D, ldd, out, ldo, 0, 0, oz, s,
-                        ev_gemm_begin, ev_gemm_end);
+  return oz_product(oz.H, oz.B, S, alpha, beta, Cin, ldcin, gamma, D, ldd, out, ldo, 0, 0, oz, s,
+                    ev_gemm_begin, ev_gemm_end);
+}
+
+// General product with split operands: C = alpha op(A) op(B) + beta Cin + gamma D,
+// op(A) M x K, op(B) K x N.  Uses the scratch operand buffers (not oz.H).
+cudaError_t oz_gemm(int opA, const zd* A, int64_t lda, int opB, const zd* B, int64_t ldb, int M, int N,
+                    int K, int S, double alpha, double beta, const zd* Cin, int64_t ldcin, double gamma,
+                    const zd* D, int64_t ldd, zd* C, int64_t ldc, int a_lower, int c_lower,
+                    OzWorkspace& oz, cudaStream_t s) {
+  cudaError_t e = oz_slice_a(oz.X, opA, A, lda, M, K, S, s);
+  if (e != cudaSuccess) return e;
+  e = oz_slice_b(oz.B, opB, B, ldb, K, N, S, oz.X.Kp, s);
+  if (e != cudaSuccess) return e;
+  return oz_product(oz.X, oz.B, S, alpha, beta, Cin, ldcin, gamma, D, ldd, C, ldc, a_lower, c_lower, oz,
+                    s, nullptr, nullptr);
 }
 
 int64_t oz_pair_count(int S) { return (int64_t)S * (S + 1) / 2; }
 
+static cudaError_t alloc_a(OzA& a, int n_max, int S_max) {
+  a.S_max = S_max;
+  a.Kp_max = oz_padded_k(n_max);
+  a.Mp_max = oz_padded_m(n_max);
+  cudaError_t e = cudaMalloc((void**)&a.ptr, sizeof(__nv_bfloat16) * (size_t)S_max * a.Mp_max * a.Kp_max);
+  if (e != cudaSuccess) return e;
+  return cudaMalloc((void**)&a.e, sizeof(int) * (size_t)a.Mp_max);
+}
+
 cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max) {
-  oz.S_max = S_max;
-  oz.Kp_max = oz_padded_k(n_max);
-  oz.Mp_max = oz_padded_m(n_max);
+  cudaError_t e = alloc_a(oz.H, n_max, S_max);
+  if (e != cudaSuccess) return e;
+  e = alloc_a(oz.X, n_max, S_max);
+  if (e != cudaSuccess) return e;
   // B operands: blocks of up to blk_max columns, and n_max columns for the reduction
   const int cols = std::max(n_max, blk_max);
-  oz.Np_max = ((cols + OZ_BN - 1) / OZ_BN) * OZ_BN;  // covers both kernels' paddings
-  cudaError_t e;
-  e = cudaMalloc((void**)&oz.A, sizeof(__nv_bfloat16) * (size_t)S_max * oz.Mp_max * oz.Kp_max);
+  oz.B.S_max = S_max;
+  oz.B.Kp_max = oz_padded_k(n_max);
+  oz.B.Np_max = ((cols + OZ_BN - 1) / OZ_BN) * OZ_BN;  // covers both kernels' paddings
+  e = cudaMalloc((void**)&oz.B.ptr, sizeof(__nv_bfloat16) * (size_t)S_max * oz.B.Np_max * oz.B.Kp_max);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc((void**)&oz.B, sizeof(__nv_bfloat16) * (size_t)S_max * oz.Np_max * oz.Kp_max);
-  if (e != cudaSuccess) return e;
-  e = cudaMalloc((void**)&oz.eA, sizeof(int) * (size_t)oz.Mp_max);
-  if (e != cudaSuccess) return e;
-  e = cudaMalloc((void**)&oz.eB, sizeof(int) * (size_t)oz.Np_max);
+  e = cudaMalloc((void**)&oz.B.e, sizeof(int) * (size_t)oz.B.Np_max);
   if (e != cudaSuccess) return e;
   const int np_blk = ((blk_max + OZ_BN - 1) / OZ_BN) * OZ_BN;
-  oz.part_elems = std::max((size_t)16 * oz.Mp_max * np_blk, (size_t)oz.Mp_max * oz.Np_max);
-  e = cudaMalloc((void**)&oz.part, sizeof(double) * oz.part_elems);
-  return e;
+  const size_t mp = (size_t)oz_padded_m(n_max);
+  oz.part_elems = std::max((size_t)32 * mp * np_blk, mp * oz.B.Np_max);
+  return cudaMalloc((void**)&oz.part, sizeof(double) * oz.part_elems);
 }
 
 void oz_free(OzWorkspace& oz) {
-  if (oz.A) cudaFree(oz.A);
-  if (oz.B) cudaFree(oz.B);
-  if (oz.eA) cudaFree(oz.eA);
-  if (oz.eB) cudaFree(oz.eB);
-  if (oz.part) cudaFree(oz.part);
+  void* ptrs[] = {oz.H.ptr, oz.H.e, oz.X.ptr, oz.X.e, oz.B.ptr, oz.B.e, oz.part};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
   oz = OzWorkspace{};
 }

@@ -156,6 +156,43 @@ __global__ void cholqr_T_kernel(const zd* X, int64_t ldx, int m, const double* d
   }
 }
 
+// ------------------------------------------------------------------ Gram scaling for Cholesky QR
+// dscale_i = 1/sqrt(G_ii); G <- D G D on the lower triangle; backup (ld m) <- the scaled lower
+// triangle, kept for a shifted retry.  One CTA.
+__global__ void gram_scale_kernel(zd* G, int64_t ldg, int m, double* dscale, zd* backup) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double d = G[i + (int64_t)i * ldg].x;
+    dscale[i] = (d > 0.0 && isfinite(d)) ? rsqrt(d) : 1.0;
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    if (i < j) continue;
+    const zd v = zscale(G[i + (int64_t)j * ldg], dscale[i] * dscale[j]);
+    G[i + (int64_t)j * ldg] = v;
+    backup[i + (int64_t)j * m] = v;
+  }
+}
+
+// G <- backup + s I (lower), s = shift_base * trace(backup).  One CTA.
+__global__ void gram_shift_kernel(const zd* backup, int m, double shift_base, zd* G, int64_t ldg) {
+  __shared__ double tr;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < m; ++i) t += backup[i + (int64_t)i * m].x;
+    tr = t;
+  }
+  __syncthreads();
+  const double sft = shift_base * tr;
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    if (i < j) continue;
+    zd v = backup[i + (int64_t)j * m];
+    if (i == j) v.x += sft;
+    G[i + (int64_t)j * ldg] = v;
+  }
+}
+
 // ------------------------------------------------------------------ Jacobi eigensolver
 struct JacParams {
   const zd* G;
@@ -393,6 +430,20 @@ cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m,
   const int warps = 8;
   const int blocks = (m + warps - 1) / warps;
   trinv_lower_kernel<<<blocks, 32 * warps, 0, s>>>(L, ldl, X, ldx, m);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t gram_scale(zd* G, int64_t ldg, int m, double* dscale, zd* backup, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  gram_scale_kernel<<<1, 1024, 0, s>>>(G, ldg, m, dscale, backup);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t gram_shift(const zd* backup, int m, double shift_base, zd* G, int64_t ldg, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  gram_shift_kernel<<<1, 1024, 0, s>>>(backup, m, shift_base, G, ldg);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -104,6 +104,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def combine_ranks(ms: float, units: float, device="cpu"):
+    """Whole-job figures over all ranks: the slowest rank's time and the units of all
+    ranks (independent sequences per rank: weak scaling, no data-path collective)."""
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    c = torch.tensor([units], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def load_workload(device, rank: int, name: str = WORKLOAD, N=None):
     from paper_1206_3768_gb300 import inputs
 
@@ -167,7 +180,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    seq = load_workload(dev, rank)
+    seq = load_workload(dev, rank, N=args.problems)
     n, nev, blk, N = seq.n, seq.nev, seq.blk, len(seq.problems)
     As = [cb.fortran(torch.tril(p.A)) for p in seq.problems]
     Bs = [cb.fortran(torch.tril(p.B)) for p in seq.problems]
@@ -209,15 +222,8 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    t_dev = torch.tensor([ms], dtype=torch.float64, device=dev)
-    c_dev = torch.tensor([converged], dtype=torch.float64, device=dev)
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
-        dist.all_reduce(c_dev, op=dist.ReduceOp.SUM)
-    ms_max = float(t_dev.item())
-    value = float(c_dev.item()) / (ms_max / 1e3)
+    ms_max, units = combine_ranks(ms, converged, dev)
+    value = units / (ms_max / 1e3)
     max_resid = max(s["max_resid"] for s in all_stats)
     launches = sum(s["launches"] for s in all_stats)
 
@@ -276,14 +282,8 @@ def run_ours(args):
             conv_e2e += int(torch.isfinite(ev).sum())
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        t_e = torch.tensor([dt], dtype=torch.float64, device=dev)
-        c_e = torch.tensor([conv_e2e], dtype=torch.float64, device=dev)
-        if ws > 1:
-            import torch.distributed as dist
-
-            dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-            dist.all_reduce(c_e, op=dist.ReduceOp.SUM)
-        e2e = {"value": float(c_e.item()) / float(t_e.item()), "unit": UNIT,
+        t_e, c_e = combine_ranks(dt, conv_e2e, dev)
+        e2e = {"value": c_e / t_e, "unit": UNIT,
                "h2d_bytes_per_step": N * 2 * n * n * 16,
                "d2h_bytes_per_step": N * (nev * 8 + n * nev * 16), "steps": steps_e2e}
 
@@ -345,6 +345,30 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_heev_case(args):
+    """One dense Hermitian eigensolve (the Rayleigh-Ritz Jacobi kernel) of a seeded random
+    m x m Hermitian matrix through the C ABI: the small case used for the Jacobi profile."""
+    from paper_1206_3768_gb300 import binding as cb
+
+    dev = torch.device("cuda:0")
+    g = torch.Generator(device="cpu").manual_seed(5)
+    m = args.case_m
+    M = torch.randn(m, m, dtype=torch.complex128, generator=g)
+    G = (0.5 * (M + M.mH)).to(dev)
+    with cb.Solver(max(args.case_n, m), m) as s:
+        for _ in range(args.case_reps):
+            cb.chfsi_heev(s.ctx, G)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        w, V = cb.chfsi_heev(s.ctx, G)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    resid = float(((G @ V - V * w.to(V.dtype).unsqueeze(0)).abs().max() / G.abs().max()).item())
+    print(json.dumps({"case": "heev", "m": m, "ms": ms, "rel_resid": resid}))
+
+
 def run_kernel_case(args):
     """One Chebyshev filter call (deg launches of the filter GEMM) through the C ABI on a
     seeded n x n Hermitian matrix and n x m block: the small case used for kernel profiles."""
@@ -391,14 +415,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--kernel-case", choices=["filter"], default=None)
+    ap.add_argument("--problems", type=int, default=None,
+                    help="solve only the first N problems of the sequence (profiling runs)")
+    ap.add_argument("--kernel-case", choices=["filter", "heev"], default=None)
     ap.add_argument("--case-n", type=int, default=4096)
     ap.add_argument("--case-m", type=int, default=128)
     ap.add_argument("--case-deg", type=int, default=3)
     ap.add_argument("--case-reps", type=int, default=1)
     ap.add_argument("--case-slices", type=int, default=0)
     args = ap.parse_args()
-    if args.kernel_case:
+    if args.kernel_case == "heev":
+        run_heev_case(args)
+    elif args.kernel_case:
         run_kernel_case(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -250,7 +250,7 @@ __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int N
 // words (384..511).  Warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..5 drain.
 // Every wait on an mbarrier is bounded; a wait that runs out sets DEV_TIMEOUT and the CTA
 // unwinds (waiting, again bounded, for its own copies and MMAs) before freeing tensor memory.
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 5, TC_THREADS = 192;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 6, TC_THREADS = 192;
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB (A) and 16 KB (B) per stage
 constexpr long kMbarSpinLimit = 1L << 26;
 
@@ -282,17 +282,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 // Bounded wait: false (with DEV_TIMEOUT set and the CTA's abort flag raised) if it ran out
 // or another role of this CTA already gave up.
+// The single-thread producer and MMA roles spin without back-off (their waits sit on the
+// critical path); the drain warps back off after a while.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status) {
+                                          int* status, bool backoff = false) {
   long it = 0;
   while (!mbar_try(bar, parity)) {
-    if (*abort_flag) return false;
     if (++it > kMbarSpinLimit) {
       *abort_flag = 1;
       atomicOr(status, DEV_TIMEOUT);
       return false;
     }
-    if (it > 64) __nanosleep(32);
+    if ((it & 255) == 0 && *abort_flag) return false;
+    if (backoff && it > 1024) __nanosleep(64);
   }
   return true;
 }
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (tc_chunk_start(q, q0, nkb)) ++chunk;
       if (!tc_chunk_end(q, q1, nkb)) continue;
       const int b = chunk & 1;
-      if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status)) { ok = false; break; }
+      if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status, true)) { ok = false; break; }
       tc_fence_after();
       const int pr = q / nkb;
       const float sc = ldexpf(1.0f, -OZ_BETA * (p.pairs.s[pr] + p.pairs.t[pr] + 2));

@@ -407,6 +407,30 @@ int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const z
       CKS(gemm_auto(ctx, g));
     }
   }
+  if (ctx->opts.precision == 1) {
+    // Mixed precision: FP32 Cholesky QR steps until the Gram matrix is within 1e-3 of the
+    // identity, then FP64 first-order Loewdin steps (T = I - (G - I)/2) until it is within
+    // 1e-8, which leaves an orthonormality error of about 1e-16.  The device chooses the
+    // step from G; the host reads the "finished" flag from the third pass on.
+    CK(cudaMemsetAsync(ws.shiftflag, 0, 4 * sizeof(int), ctx->stream));
+    for (int pass = 0; pass < 12; ++pass) {
+      GemmDesc g = gd(m, m, n, *Ya, ld, OPC, *Ya, ld, OPN, ws.G, ldm);
+      g.lowerC = 1;
+      CKS(gemm_auto(ctx, g));
+      {
+        PhaseScope ps(ctx, PH_SMALL);
+        CK(qr_pass(ws.G, ldm, m, ws.V, ldm, ws.dscale, ws.jac, ws.shiftflag, ws.status, ctx->stream));
+      }
+      CKS(gemm_auto(ctx, gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld)));
+      std::swap(*Ya, *Yb);
+      if (pass >= 2) {
+        int done = 0;
+        CKS(read_back(ctx, &done, ws.shiftflag, 1));
+        if (done) return CHFSI_OK;
+      }
+    }
+    // not finished (a numerically rank-deficient block): finish with FP64 shifted Cholesky QR
+  }
   const double u = 1.1102230246251565e-16;
   const double shift_base = 11.0 * ((double)n * m + (double)m * (m + 1)) * u;
   // Cholesky QR twice; a third pass only when the first one needed the shifted retry

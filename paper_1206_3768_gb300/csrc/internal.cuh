@@ -77,9 +77,12 @@ cudaError_t small_cholesky(zd* G, int64_t ldg, int m, int scale, int shift_on_fa
                            int info_base, cudaStream_t s, int* shift_flag = nullptr);
 // X = L^{-1} for an m x m lower-triangular L (strict upper of X zeroed).  X != L.
 cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m, cudaStream_t s);
-// Unit-diagonal scaling of a Gram matrix (lower) with a backup copy, and the shifted restore.
-cudaError_t gram_scale(zd* G, int64_t ldg, int m, double* dscale, zd* backup, cudaStream_t s);
-cudaError_t gram_shift(const zd* backup, int m, double shift_base, zd* G, int64_t ldg, cudaStream_t s);
+// One pass of the mixed-precision re-orthonormalisation (Y <- Y T) from G = Y^H Y (lower):
+// a first-order Loewdin step in FP64 when ||G - I||_F <= 1e-3 (flags[0] = 1 once that norm
+// is <= 1e-8), else an FP32 Cholesky QR step on the scaled Gram (shift on breakdown).
+// T is m x m (full).  scratch: m*m + 32*m float2 (used when m > 144).  flags: 4 ints.
+cudaError_t qr_pass(const zd* G, int64_t ldg, int m, zd* T, int64_t ldt, double* dscale, void* scratch,
+                    int* flags, int* status, cudaStream_t s);
 // T = D X^H (upper triangular, zero below): the right factor of Cholesky QR, Q = Y T.
 cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* T, int64_t ldt,
                      cudaStream_t s);

@@ -213,22 +213,38 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_gemm_kernel(const OzParams p
 }
 
 // Complex epilogue: C(i, j) = 2^{eA(i)+eB(j)} (sum_s P[s](2i, j), sum_s P[s](2i+1, j)),
-// out = alpha C + beta Cin + gamma D (out may alias Cin or D element-wise).
+// out = alpha C + beta Cin + gamma D (out may alias Cin or D element-wise).  The partial
+// sums are FP64 (pairs == 0) or double-float (hi, lo) pairs of FP32 (pairs != 0), which are
+// summed over the splits in double-float arithmetic and converted to FP64 once.
 __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int Np, const int* eA,
                                    const int* eB, int n, int m, double alpha, double beta,
                                    const zd* Cin, int64_t ldcin, double gamma, const zd* D,
-                                   int64_t ldd, zd* out, int64_t ldo, int lower) {
+                                   int64_t ldd, zd* out, int64_t ldo, int lower, int pairs) {
   const int64_t total = (int64_t)n * m;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % n), j = (int)(e / n);
     if (lower && j > i) continue;
     double re = 0.0, im = 0.0;
-    for (int s = 0; s < splits; ++s) {
-      const double2 v = *reinterpret_cast<const double2*>(part + (int64_t)s * Mp * Np +
+    if (pairs) {
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      for (int s = 0; s < splits; ++s) {
+        const float4 v = *reinterpret_cast<const float4*>(part + (int64_t)s * Mp * Np +
                                                           (int64_t)j * Mp + 2 * i);
-      re += v.x;
-      im += v.y;
+        two_sum_acc(rh, rl, v.x);
+        rl += v.y;
+        two_sum_acc(ih, il, v.z);
+        il += v.w;
+      }
+      re = (double)rh + (double)rl;
+      im = (double)ih + (double)il;
+    } else {
+      for (int s = 0; s < splits; ++s) {
+        const double2 v = *reinterpret_cast<const double2*>(part + (int64_t)s * Mp * Np +
+                                                            (int64_t)j * Mp + 2 * i);
+        re += v.x;
+        im += v.y;
+      }
     }
     // the kernel applied the slice-level scales 2^{-7(s+t)}; the row and column scales remain
     const int ex = eA[i] + eB[j];
@@ -242,21 +258,32 @@ __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int N
 
 // ============================================================================ tcgen05 path
 // The same digit products on the 5th-generation tensor cores: TMA (128-byte swizzle) stages
-// 128 x 64 bf16 tiles of A and B in shared memory, one elected thread issues
-// tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor memory), and four drain
-// warps fold each exact 1024-term chunk into double-float sums that also live in tensor
-// memory.  Tensor memory (512 columns): two 128-column accumulators used alternately
-// (one fills while the other drains), the high words of the sums (256..383) and the low
-// words (384..511).  Warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..5 drain.
-// Every wait on an mbarrier is bounded; a wait that runs out sets DEV_TIMEOUT and the CTA
-// unwinds (waiting, again bounded, for its own copies and MMAs) before freeing tensor memory.
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 6, TC_THREADS = 192;
-constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 2;  // 16 KB (A) and 16 KB (B) per stage
+// a 128 x 64 bf16 tile of A and a 144 x 64 tile of B in shared memory, one elected thread
+// issues tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor memory, N up to
+// 144 so that a 130-column block is one tile and the large operand is streamed once), and
+// twelve drain warps fold each exact 960-term chunk into double-float sums.  Tensor memory
+// (512 columns): two 144-column accumulators at columns 0 and 160 used alternately (one
+// fills while the other drains) and the high words of the sums at 320..463; the low words
+// live in the drain threads' registers.  Warp 0 issues TMA loads, warp 1 issues MMAs,
+// warps 2..13 drain: three warps per group of 32 tensor-memory lanes, one for each third
+// (48 columns) of the tile.  14 warps keep at most 4 warps on each SM sub-partition, so
+// each thread may hold 128 registers.  Every wait on an mbarrier is bounded; a
+// wait that runs out sets DEV_TIMEOUT and the CTA unwinds (waiting, again bounded, for its
+// own copies and MMAs) before freeing tensor memory.
+constexpr int TC_BM = 128, TC_BN = 144, TC_BK = 64, TC_STAGES = 6, TC_THREADS = 448;
+constexpr int TC_DRAIN_THREADS = TC_THREADS - 64;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per stage
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;       // 18 KB per stage
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // a multiple of 1024 (swizzle atoms)
+constexpr int TC_ACC1 = 160, TC_HI = 320;           // tensor-memory column offsets
+static_assert(TC_STAGE_BYTES % 1024 == 0, "stage buffers must stay 1024-byte aligned");
+static_assert(TC_HI + TC_BN <= 512 && TC_ACC1 + TC_BN <= TC_HI, "tensor-memory layout");
 constexpr long kMbarSpinLimit = 1L << 26;
 
 struct TcParams {
   int a_lower, c_lower;                      // as in OzParams
   int nkb, tiles_m, splits, Mp, Np, n_real;  // n_real: columns of B^ that hold data
+  int b_box_rows;                            // rows of the B box (<= TC_BN, multiple of 16)
   OzPairs pairs;
   double* part;
   int* status;
@@ -341,43 +368,17 @@ __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
 
-#define TC_R32(v) \
-  "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), \
-  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),      \
-  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),    \
-  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),    \
-  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-#define TC_W32(v) \
-  "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), \
-  "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),   \
-  "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),  \
-  "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      : TC_R32(v)
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n"
-      ::"r"(taddr), TC_W32(v));
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
+               ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
-
-// chunk boundaries of the flattened (pair, k-block) sequence q0..q1 of one CTA
-__device__ __forceinline__ bool tc_chunk_start(int q, int q0, int nkb) {
-  const int kb = q % nkb;
-  return q == q0 || (kb % OZ_CHUNK_KB) == 0;
-}
-__device__ __forceinline__ bool tc_chunk_end(int q, int q1, int nkb) {
-  const int kb = q % nkb;
-  return q == q1 - 1 || (kb % OZ_CHUNK_KB) == OZ_CHUNK_KB - 1 || kb == nkb - 1;
-}
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     oz_gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -385,8 +386,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ unsigned char tc_smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023;
   unsigned char* sA = reinterpret_cast<unsigned char*>(base);
-  unsigned char* sB = sA + TC_STAGES * TC_TILE_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_TILE_BYTES);
+  unsigned char* sB = sA + TC_STAGES * TC_A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_B_BYTES);
   // bars: full[STAGES], empty[STAGES], accf[2], acce[2], done[1]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -395,11 +396,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int tm = blockIdx.x % p.tiles_m, tn = blockIdx.x / p.tiles_m;
   const int m0 = tm * TC_BM, n0 = tn * TC_BN;
   if (p.c_lower && n0 > (m0 + TC_BM - 1) / 2) return;  // tile above the diagonal: not needed
+  // k-blocks of this CTA: split y takes [y per, (y + 1) per) of the tile's nonzero k-blocks.
+  // The work is ordered panel-major: for each panel of at most OZ_CHUNK_KB k-blocks, every
+  // slice pair in turn (one exact chunk each), so consecutive chunks reuse the same panel of
+  // an A slice from L2 while it is hot.
   const int nkb = p.a_lower ? min(p.nkb, m0 / TC_BK + TC_BM / TC_BK) : p.nkb;
   const int ncols = min(TC_BN, ((p.n_real - n0 + 15) / 16) * 16);  // MMA N for this tile
-  const int total = p.pairs.n * nkb;
-  const int per = (total + p.splits - 1) / p.splits;
-  const int q0 = min(total, (int)blockIdx.y * per), q1 = min(total, q0 + per);
+  const int per = (p.nkb + p.splits - 1) / p.splits;
+  const int kb_lo = min(nkb, (int)blockIdx.y * per), kb_hi = min(nkb, kb_lo + per);
 
   const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * TC_STAGES;
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 128);
+      mbar_init(acce0 + 8 * b, TC_DRAIN_THREADS);
     }
     mbar_init(done_bar, 1);
     *abort_flag = 0;
@@ -430,21 +434,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int issued = 0;
-      for (int q = q0; q < q1; ++q, ++issued) {
-        const int i = q - q0, stage = i % TC_STAGES;
-        if (i >= TC_STAGES && !mbar_wait(empty0 + 8 * stage, ((i / TC_STAGES) & 1) ^ 1, abort_flag, p.status))
-          break;
-        const int pr = q / nkb, kb = q - pr * nkb;
-        mbar_expect_tx(full0 + 8 * stage, 2 * TC_TILE_BYTES);
-        tma_load_2d(sA_u + stage * TC_TILE_BYTES, &tmA, kb * TC_BK, p.pairs.s[pr] * p.Mp + m0,
-                    full0 + 8 * stage);
-        tma_load_2d(sB_u + stage * TC_TILE_BYTES, &tmB, kb * TC_BK, p.pairs.t[pr] * p.Np + n0,
-                    full0 + 8 * stage);
+      int i = 0;
+      bool stop = false;
+      for (int k0 = kb_lo; k0 < kb_hi && !stop; k0 += OZ_CHUNK_KB) {
+        const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
+        for (int pr = 0; pr < p.pairs.n && !stop; ++pr) {
+          for (int kb = k0; kb < k1; ++kb, ++i) {
+            const int stage = i % TC_STAGES;
+            if (i >= TC_STAGES &&
+                !mbar_wait(empty0 + 8 * stage, ((i / TC_STAGES) & 1) ^ 1, abort_flag, p.status)) {
+              stop = true;
+              break;
+            }
+            mbar_expect_tx(full0 + 8 * stage, TC_A_BYTES + p.b_box_rows * TC_BK * 2);
+            tma_load_2d(sA_u + stage * TC_A_BYTES, &tmA, kb * TC_BK, p.pairs.s[pr] * p.Mp + m0,
+                        full0 + 8 * stage);
+            tma_load_2d(sB_u + stage * TC_B_BYTES, &tmB, kb * TC_BK, p.pairs.t[pr] * p.Np + n0,
+                        full0 + 8 * stage);
+          }
+        }
       }
-      // on abort: let the copies already issued land before the CTA can exit
+      // on abort: let the copies already issued (stages i - STAGES .. i - 1) land before the
+      // CTA can exit
       if (*abort_flag) {
-        for (int j = max(0, issued - TC_STAGES); j < issued; ++j) {
+        for (int j = max(0, i - TC_STAGES); j < i; ++j) {
           long it = 0;
           while (!mbar_try(full0 + 8 * (j % TC_STAGES), (j / TC_STAGES) & 1) && ++it < kMbarSpinLimit) {}
         }
@@ -454,26 +467,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(TC_BM, ncols);
-      int chunk = -1;
-      for (int q = q0; q < q1; ++q) {
-        const int i = q - q0, stage = i % TC_STAGES;
-        if (!mbar_wait(full0 + 8 * stage, (i / TC_STAGES) & 1, abort_flag, p.status)) break;
-        tc_fence_after();
-        const bool start = tc_chunk_start(q, q0, nkb);
-        if (start) {
-          ++chunk;
-          if (chunk >= 2 && !mbar_wait(acce0 + 8 * (chunk & 1), ((chunk >> 1) - 1) & 1, abort_flag, p.status))
+      int i = 0, chunk = 0;
+      bool stop = false;
+      for (int k0 = kb_lo; k0 < kb_hi && !stop; k0 += OZ_CHUNK_KB) {
+        const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
+        for (int pr = 0; pr < p.pairs.n && !stop; ++pr, ++chunk) {
+          // accumulator chunk & 1 is free once the drain has finished chunk - 2
+          if (chunk >= 2 && !mbar_wait(acce0 + 8 * (chunk & 1), ((chunk >> 1) - 1) & 1, abort_flag, p.status)) {
+            stop = true;
             break;
+          }
           tc_fence_after();
-        }
-        const uint32_t d = tmem + (uint32_t)((chunk & 1) * TC_BN);
-        const uint32_t a_s = sA_u + stage * TC_TILE_BYTES, b_s = sB_u + stage * TC_TILE_BYTES;
+          const uint32_t d = tmem + (uint32_t)((chunk & 1) * TC_ACC1);
+          for (int kb = k0; kb < k1; ++kb, ++i) {
+            const int stage = i % TC_STAGES;
+            if (!mbar_wait(full0 + 8 * stage, (i / TC_STAGES) & 1, abort_flag, p.status)) {
+              stop = true;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_s = sA_u + stage * TC_A_BYTES, b_s = sB_u + stage * TC_B_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < TC_BK / 16; ++kk)
-          tc_mma(d, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc,
-                 (start && kk == 0) ? 0u : 1u);
-        tc_commit(empty0 + 8 * stage);
-        if (tc_chunk_end(q, q1, nkb)) tc_commit(accf0 + 8 * (chunk & 1));
+            for (int kk = 0; kk < TC_BK / 16; ++kk)
+              tc_mma(d, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc,
+                     (kb == k0 && kk == 0) ? 0u : 1u);
+            tc_commit(empty0 + 8 * stage);
+            if (kb == k1 - 1) tc_commit(accf0 + 8 * (chunk & 1));
+          }
+        }
       }
       // all MMAs issued by this thread are complete once done_bar fires
       tc_commit(done_bar);
@@ -481,66 +502,75 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       while (!mbar_try(done_bar, 0) && ++it < kMbarSpinLimit) {}
     }
   } else {
-    // ------------------------------------------------------------ drain warps (2..5)
+    // ------------------------------------------------------------ drain warps (2..13)
+    // Thread (quarter, lane) of third h owns row 32 * quarter + lane of the tile and the 48
+    // columns from c0 = 48 h: the high words of its sums sit in tensor memory, the low words
+    // in lo[] (registers; the column loops below are unrolled so that every index into lo[]
+    // is a constant).  Tensor memory is moved in blocks of 8 columns to keep the live
+    // registers within the 128 that 14 warps allow.
     const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
+    constexpr int kCols = TC_BN / 3;  // 48 columns per third
+    const int c0 = ((warp - 2) >> 2) * kCols;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    uint32_t zero[32];
+    float lo[kCols];
+    {
+      uint32_t zero[8];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) zero[j] = 0u;
+      for (int j = 0; j < 8; ++j) zero[j] = 0u;
 #pragma unroll
-    for (int cb = 0; cb < TC_BN / 32; ++cb) {
-      tmem_st32(lane_base + 256 + cb * 32, zero);
-      tmem_st32(lane_base + 384 + cb * 32, zero);
+      for (int c = 0; c < kCols / 8; ++c) {
+        tmem_st8(lane_base + TC_HI + c0 + c * 8, zero);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) lo[c * 8 + j] = 0.f;
+      }
+      tmem_wait_st();
     }
-    tmem_wait_st();
-    int chunk = -1;
+    int chunk = 0;
     bool ok = true;
-    for (int q = q0; q < q1 && ok; ++q) {
-      if (tc_chunk_start(q, q0, nkb)) ++chunk;
-      if (!tc_chunk_end(q, q1, nkb)) continue;
+    const int nchunks = ((kb_hi - kb_lo + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB) * p.pairs.n;
+    for (; chunk < nchunks && ok; ++chunk) {
       const int b = chunk & 1;
       if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status, true)) { ok = false; break; }
       tc_fence_after();
-      const int pr = q / nkb;
+      const int pr = chunk % p.pairs.n;
       const float sc = ldexpf(1.0f, -OZ_BETA * (p.pairs.s[pr] + p.pairs.t[pr] + 2));
-#pragma unroll 1
-      for (int cb = 0; cb < TC_BN / 32; ++cb) {
-        if (cb * 32 >= ncols) break;
-        uint32_t acc[32], hi[32], lo[32];
-        tmem_ld32(lane_base + b * TC_BN + cb * 32, acc);
-        tmem_ld32(lane_base + 256 + cb * 32, hi);
-        tmem_ld32(lane_base + 384 + cb * 32, lo);
-        tmem_wait_ld();
+      const uint32_t acc_base = lane_base + (uint32_t)(b * TC_ACC1);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float h = __uint_as_float(hi[j]), l = __uint_as_float(lo[j]);
-          two_sum_acc(h, l, __uint_as_float(acc[j]) * sc);
-          hi[j] = __float_as_uint(h);
-          lo[j] = __float_as_uint(l);
+      for (int c = 0; c < kCols / 8; ++c) {
+        if (c0 + c * 8 < ncols) {
+          uint32_t acc[8], hi[8];
+          tmem_ld8(acc_base + c0 + c * 8, acc);
+          tmem_ld8(lane_base + TC_HI + c0 + c * 8, hi);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float h = __uint_as_float(hi[j]);
+            two_sum_acc(h, lo[c * 8 + j], __uint_as_float(acc[j]) * sc);
+            hi[j] = __float_as_uint(h);
+          }
+          tmem_st8(lane_base + TC_HI + c0 + c * 8, hi);
         }
-        tmem_st32(lane_base + 256 + cb * 32, hi);
-        tmem_st32(lane_base + 384 + cb * 32, lo);
       }
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(acce0 + 8 * b);
     }
     if (ok && !*abort_flag) {
-      // partial sums of this split: P[split][col * Mp + row]
-      double* P = p.part + (int64_t)blockIdx.y * p.Mp * p.Np;
+      // partial sums of this split as (hi, lo) pairs: P[split][col * Mp + row]
+      float2* P = reinterpret_cast<float2*>(p.part) + (int64_t)blockIdx.y * p.Mp * p.Np;
       const int row = m0 + quarter * 32 + lane;
-#pragma unroll 1
-      for (int cb = 0; cb < TC_BN / 32; ++cb) {
-        if (cb * 32 >= ncols) break;
-        uint32_t hi[32], lo[32];
-        tmem_ld32(lane_base + 256 + cb * 32, hi);
-        tmem_ld32(lane_base + 384 + cb * 32, lo);
-        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + cb * 32 + j;
-          if (col < p.Np)
-            P[(int64_t)col * p.Mp + row] = (double)__uint_as_float(hi[j]) + (double)__uint_as_float(lo[j]);
+      for (int c = 0; c < kCols / 8; ++c) {
+        if (c0 + c * 8 < ncols) {
+          uint32_t hi[8];
+          tmem_ld8(lane_base + TC_HI + c0 + c * 8, hi);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int col = n0 + c0 + c * 8 + j;
+            if (col < p.Np)
+              P[(int64_t)col * p.Mp + row] = make_float2(__uint_as_float(hi[j]), lo[c * 8 + j]);
+          }
         }
       }
     }
@@ -764,6 +794,27 @@ int choose_oz_splits(int tiles, int total_kb, size_t cap_elems, int64_t tile_ele
   return best;
 }
 
+// Split-K count for the tcgen05 kernel: split y takes k-blocks [y per, (y + 1) per) of every
+// tile.  Modelled CTA time in k-block units: every (panel, pair) chunk costs at least the
+// drain of one accumulator (about 5 k-blocks of MMA time), plus a pipeline fill; the launch
+// time is that times the number of waves of one CTA per SM.
+int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t tile_elems) {
+  const int sms = sm_count();
+  int best = 1;
+  double best_cost = 1e300;
+  for (int S = 1; S <= std::min(nkb, 64); ++S) {
+    if ((size_t)S * (size_t)tile_elems > cap_elems) break;
+    const int per = (nkb + S - 1) / S;
+    double cta = 6.0;
+    for (int k0 = 0; k0 < per; k0 += OZ_CHUNK_KB)
+      cta += (double)npairs * std::max(5, std::min(OZ_CHUNK_KB, per - k0));
+    const int64_t units = (int64_t)tiles * S;
+    const double cost = (double)((units + sms - 1) / sms) * cta;
+    if (cost < best_cost * 0.999) { best_cost = cost; best = S; }
+  }
+  return best;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------- host side
@@ -779,8 +830,9 @@ bool oz_use_tcgen05() {
 }
 
 // 2-D bf16 tensor map over `rows` rows of `inner` elements (row pitch inner * 2 bytes),
-// 64 x 128 boxes, 128-byte swizzle (the layout the tcgen05 descriptors expect).
-static bool encode_bf16_map(CUtensorMap* map, const void* ptr, int inner, uint64_t rows) {
+// boxes of 64 elements x box_rows rows, 128-byte swizzle (the layout the tcgen05
+// descriptors expect).
+static bool encode_bf16_map(CUtensorMap* map, const void* ptr, int inner, uint64_t rows, int box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -793,7 +845,7 @@ static bool encode_bf16_map(CUtensorMap* map, const void* ptr, int inner, uint64
   if (!encode) return false;
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -879,12 +931,18 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     tp.part = oz.part;
     tp.status = oz.status;
     const int tiles = tp.tiles_m * ((Np + TC_BN - 1) / TC_BN);
-    tp.splits = splits = choose_oz_splits(tiles, pairs.n * tp.nkb, oz.part_elems, (int64_t)Mp * Np);
+    tp.splits = splits = choose_tc_splits(tiles, tp.nkb, pairs.n, oz.part_elems, (int64_t)Mp * Np);
     CUtensorMap mapA, mapB;
-    if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)a.S * Mp) ||
-        !encode_bf16_map(&mapB, b.ptr, Kp, (uint64_t)b.S * Np))
+    // The B box is min(Np, TC_BN) rows high; a last tile narrower than that reads rows past
+    // its slice (the next slice, or the buffer's spare rows: the allocation holds at least
+    // TC_BN rows) that the MMA never uses, since its N covers only the tile's own columns.
+    tp.b_box_rows = std::min(Np, TC_BN);
+    const uint64_t b_rows = std::max<uint64_t>((uint64_t)b.S * Np, (uint64_t)TC_BN);
+    if ((int64_t)b_rows * Kp > (int64_t)b.S_max * b.Np_max * b.Kp_max) return cudaErrorInvalidValue;
+    if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)a.S * Mp, TC_BM) ||
+        !encode_bf16_map(&mapB, b.ptr, Kp, b_rows, tp.b_box_rows))
       return cudaErrorInvalidValue;
-    const size_t smem = 1024 + (size_t)TC_STAGES * 2 * TC_TILE_BYTES + 256;
+    const size_t smem = 1024 + (size_t)TC_STAGES * TC_STAGE_BYTES + 256;
     static bool tc_attr = false;
     if (!tc_attr) {
       e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -931,7 +989,8 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
   const int64_t tot = (int64_t)n * m;
   const int blocks = (int)std::min<int64_t>(4 * sm_count(), (tot + 255) / 256);
   oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, a.e, b.e, n, m, alpha, beta, Cin,
-                                            ldcin, gamma, D, ldd, out, ldo, c_lower);
+                                            ldcin, gamma, D, ldd, out, ldo, c_lower,
+                                            oz_use_tcgen05() ? 1 : 0);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -990,7 +1049,8 @@ cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max) {
   const int cols = std::max(n_max, blk_max);
   oz.B.S_max = S_max;
   oz.B.Kp_max = oz_padded_k(n_max);
-  oz.B.Np_max = ((cols + OZ_BN - 1) / OZ_BN) * OZ_BN;  // covers both kernels' paddings
+  // covers both kernels' paddings and at least one full B box of the tcgen05 kernel
+  oz.B.Np_max = ((std::max(cols, TC_BN) + OZ_BN - 1) / OZ_BN) * OZ_BN;
   e = cudaMalloc((void**)&oz.B.ptr, sizeof(__nv_bfloat16) * (size_t)S_max * oz.B.Np_max * oz.B.Kp_max);
   if (e != cudaSuccess) return e;
   e = cudaMalloc((void**)&oz.B.e, sizeof(int) * (size_t)oz.B.Np_max);

@@ -156,40 +156,162 @@ __global__ void cholqr_T_kernel(const zd* X, int64_t ldx, int m, const double* d
   }
 }
 
-// ------------------------------------------------------------------ Gram scaling for Cholesky QR
-// dscale_i = 1/sqrt(G_ii); G <- D G D on the lower triangle; backup (ld m) <- the scaled lower
-// triangle, kept for a shifted retry.  One CTA.
-__global__ void gram_scale_kernel(zd* G, int64_t ldg, int m, double* dscale, zd* backup) {
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+// ------------------------------------------------------------------ mixed-precision Cholesky QR
+// One pass of the re-orthonormalisation Y <- Y T used by the mixed-precision path.  G = Y^H Y
+// (m x m, lower triangle read) and e = ||G - I||_F decide the pass:
+//   e <= 1e-3: first-order Loewdin step T = I - (G - I)/2 in FP64 (full Hermitian T); the
+//              new Gram error is about 3/4 e^2, so e <= 1e-8 finishes (flags[0] = 1);
+//   e >  1e-3: Cholesky QR step in FP32 on the unit-diagonal scaled Gram,
+//              D G D + s I = L L^H (s = 0, then 1e-5, 1e-4, 1e-3 on breakdown),
+//              T = D L^{-H} (upper triangular), which reduces e to the FP32 level (or, when Y
+//              is ill-conditioned, reduces cond(Y) by about sqrt(1/s)).
+// Precision of T only affects how far Y T is from orthonormal, never its span: the product
+// Y T itself is formed in FP64-level arithmetic and the last step is always an FP64 Loewdin
+// step.  flags[1] counts FP32 Cholesky steps, flags[2] records a shifted one.  One CTA of
+// QR_THREADS threads; the FP32 factor lives in shared memory (m <= QR_SMEM_MMAX) or in the
+// global scratch `gs` (m*m + 32*m float2).
+constexpr int QR_THREADS = 1024;
+constexpr int QR_SMEM_MMAX = 144;
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void __launch_bounds__(QR_THREADS)
+    qr_pass_kernel(const zd* G, int64_t ldg, int m, zd* T, int64_t ldt, double* dscale, float2* gs,
+                   int* flags, int* status) {
+  extern __shared__ float2 qr_smem[];
+  __shared__ double red[QR_THREADS / 32];
+  __shared__ double e_all;
+  __shared__ int fail;
+  __shared__ float piv;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = nt >> 5;
+
+  // ---- e = ||G - I||_F from the lower triangle
+  double acc = 0.0;
+  for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    if (i < j) continue;
+    const zd g = G[i + (int64_t)j * ldg];
+    if (i == j) acc += (g.x - 1.0) * (g.x - 1.0) + g.y * g.y;
+    else acc += 2.0 * (g.x * g.x + g.y * g.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    e_all = sqrt(t);
+  }
+  __syncthreads();
+  const double e_f = e_all;
+
+  if (e_f <= 1e-3) {
+    // ---- first-order Loewdin step, FP64
+    for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+      const int i = (int)(e % m), j = (int)(e / m);
+      zd g = (i >= j) ? G[i + (int64_t)j * ldg] : zconj(G[j + (int64_t)i * ldg]);
+      zd t = zmk(-0.5 * g.x, -0.5 * g.y);
+      if (i == j) t = zmk(1.0 - 0.5 * (g.x - 1.0), 0.0);
+      T[i + (int64_t)j * ldt] = t;
+    }
+    if (tid == 0 && e_f <= 1e-8) flags[0] = 1;
+    return;
+  }
+  if (!(e_f < 1e300)) {  // NaN or Inf in the Gram matrix
+    if (tid == 0) atomicOr(status, DEV_NOTPD);
+    return;
+  }
+
+  // ---- FP32 Cholesky QR step
+  float2* A = (m <= QR_SMEM_MMAX) ? qr_smem : gs;
+  float2* xb = A + (int64_t)m * m;  // per-warp column buffers (32 x m)
+  for (int i = tid; i < m; i += nt) {
     const double d = G[i + (int64_t)i * ldg].x;
     dscale[i] = (d > 0.0 && isfinite(d)) ? rsqrt(d) : 1.0;
   }
+  if (tid == 0) atomicAdd(flags + 1, 1);
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-    const int i = (int)(e % m), j = (int)(e / m);
-    if (i < j) continue;
-    const zd v = zscale(G[i + (int64_t)j * ldg], dscale[i] * dscale[j]);
-    G[i + (int64_t)j * ldg] = v;
-    backup[i + (int64_t)j * m] = v;
+  const float shifts[4] = {0.f, 1e-5f, 1e-4f, 1e-3f};
+  int attempt = 0;
+  for (; attempt < 4; ++attempt) {
+    for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+      const int i = (int)(e % m), j = (int)(e / m);
+      if (i < j) continue;
+      const zd g = G[i + (int64_t)j * ldg];
+      const double sc = dscale[i] * dscale[j];
+      float2 v = make_float2((float)(g.x * sc), (float)(g.y * sc));
+      if (i == j) v = make_float2(v.x + shifts[attempt], 0.f);
+      A[i + (int64_t)j * m] = v;
+    }
+    if (tid == 0) fail = -1;
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+      if (tid == 0) {
+        const float d = A[j + (int64_t)j * m].x;
+        if (!(d > 0.f) || !isfinite(d)) fail = j;
+        else piv = sqrtf(d);
+      }
+      __syncthreads();
+      if (fail >= 0) break;
+      const float inv = 1.f / piv;
+      for (int i = j + 1 + tid; i < m; i += nt) {
+        const float2 v = A[i + (int64_t)j * m];
+        A[i + (int64_t)j * m] = make_float2(v.x * inv, v.y * inv);
+      }
+      if (tid == 0) A[j + (int64_t)j * m] = make_float2(piv, 0.f);
+      __syncthreads();
+      // trailing update of the lower triangle: A(i,k) -= L(i,j) conj(L(k,j)), j < k <= i
+      const int r = m - j - 1;
+      for (int e = tid; e < r * r; e += nt) {
+        const int ii = e % r, kk = e / r;
+        if (ii < kk) continue;
+        const int gi = j + 1 + ii, gk = j + 1 + kk;
+        const float2 lij = A[gi + (int64_t)j * m], lkj = A[gk + (int64_t)j * m];
+        float2 v = A[gi + (int64_t)gk * m];
+        v.x -= lij.x * lkj.x + lij.y * lkj.y;
+        v.y -= lij.y * lkj.x - lij.x * lkj.y;
+        A[gi + (int64_t)gk * m] = v;
+      }
+      __syncthreads();
+    }
+    if (fail < 0) break;
   }
-}
+  if (attempt == 4) {
+    if (tid == 0) atomicOr(status, DEV_NOTPD);
+    return;
+  }
+  if (attempt > 0 && tid == 0) flags[2] = 1;
 
-// G <- backup + s I (lower), s = shift_base * trace(backup).  One CTA.
-__global__ void gram_shift_kernel(const zd* backup, int m, double shift_base, zd* G, int64_t ldg) {
-  __shared__ double tr;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < m; ++i) t += backup[i + (int64_t)i * m].x;
-    tr = t;
-  }
-  __syncthreads();
-  const double sft = shift_base * tr;
-  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-    const int i = (int)(e % m), j = (int)(e / m);
-    if (i < j) continue;
-    zd v = backup[i + (int64_t)j * m];
-    if (i == j) v.x += sft;
-    G[i + (int64_t)j * ldg] = v;
+  // ---- X = L^{-1} column by column (one warp per column, forward substitution), and
+  // T = D X^H: row j of T holds d_j conj(X(:, j)).
+  float2* x = xb + (int64_t)warp * m;
+  for (int j = warp; j < m; j += nw) {
+    for (int i = j; i < m; ++i) {
+      float2 sacc = make_float2(0.f, 0.f);
+      for (int k = j + lane; k < i; k += 32) {
+        const float2 p = cmulf(A[i + (int64_t)k * m], x[k]);
+        sacc.x += p.x;
+        sacc.y += p.y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+        sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+      }
+      if (lane == 0) {
+        const float dinv = 1.f / A[i + (int64_t)i * m].x;
+        x[i] = (i == j) ? make_float2(dinv, 0.f) : make_float2(-sacc.x * dinv, -sacc.y * dinv);
+      }
+      __syncwarp();
+    }
+    const double dj = dscale[j];
+    for (int i = lane; i < m; i += 32)
+      T[j + (int64_t)i * ldt] = (i < j) ? zmk(0.0, 0.0) : zmk(dj * (double)x[i].x, -dj * (double)x[i].y);
+    __syncwarp();
   }
 }
 
@@ -434,16 +556,19 @@ cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m,
   return cudaGetLastError();
 }
 
-cudaError_t gram_scale(zd* G, int64_t ldg, int m, double* dscale, zd* backup, cudaStream_t s) {
+cudaError_t qr_pass(const zd* G, int64_t ldg, int m, zd* T, int64_t ldt, double* dscale, void* scratch,
+                    int* flags, int* status, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  gram_scale_kernel<<<1, 1024, 0, s>>>(G, ldg, m, dscale, backup);
-  CHFSI_COUNT_LAUNCH();
-  return cudaGetLastError();
-}
-
-cudaError_t gram_shift(const zd* backup, int m, double shift_base, zd* G, int64_t ldg, cudaStream_t s) {
-  if (m <= 0) return cudaSuccess;
-  gram_shift_kernel<<<1, 1024, 0, s>>>(backup, m, shift_base, G, ldg);
+  const size_t smem = (m <= QR_SMEM_MMAX) ? sizeof(float2) * ((size_t)m * m + 32 * (size_t)m) : 0;
+  static bool attr = false;
+  if (!attr) {
+    const size_t mx = sizeof(float2) * ((size_t)QR_SMEM_MMAX * QR_SMEM_MMAX + 32 * (size_t)QR_SMEM_MMAX);
+    cudaError_t e = cudaFuncSetAttribute(qr_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  qr_pass_kernel<<<1, QR_THREADS, smem, s>>>(G, ldg, m, T, ldt, dscale, static_cast<float2*>(scratch), flags,
+                                             status);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -180,13 +180,16 @@ def test_filter_fixed_degree_closed_form(ctx):
 
 
 # ---------------------------------------------------------------------------- QR, RR
-@pytest.mark.parametrize("n,m,k", [(300, 20, 0), (513, 40, 12), (640, 130, 30)])
-def test_orthonormalize_matches_oracle_span(ctx, n, m, k):
+@pytest.mark.parametrize("n,m,k", [(300, 20, 0), (513, 40, 12), (640, 130, 30), (700, 160, 0)])
+@pytest.mark.parametrize("mode", ["split", "fp64"])
+def test_orthonormalize_matches_oracle_span(ctx, ctx64, n, m, k, mode):
+    """Mixed precision (FP32 Cholesky QR steps, then FP64 Loewdin steps; m = 160 keeps the
+    FP32 factor in global memory) and plain FP64 Cholesky QR."""
     rng = _rng(n + m + k)
     YL = np.linalg.qr(_cgauss(rng, n, k))[0] if k else None
     # an ill-conditioned block (column scales spread over 1e6, as after filtering)
     Y = _cgauss(rng, n, m) * np.logspace(0, -6, m)[None, :]
-    got = _np(cb.chfsi_orthonormalize(ctx, _t(Y), _t(YL) if k else None))
+    got = _np(cb.chfsi_orthonormalize(ctx if mode == "split" else ctx64, _t(Y), _t(YL) if k else None))
     ref = O.orthonormalize(Y, YL)
     assert np.max(np.abs(got.conj().T @ got - np.eye(m))) < 1e-13
     if k:
@@ -194,15 +197,20 @@ def test_orthonormalize_matches_oracle_span(ctx, n, m, k):
     assert np.linalg.norm(got @ got.conj().T - ref @ ref.conj().T) < 1e-9
 
 
-def test_orthonormalize_survives_near_rank_deficiency(ctx):
+@pytest.mark.parametrize("mode", ["split", "fp64"])
+def test_orthonormalize_survives_near_rank_deficiency(ctx, ctx64, mode):
     """A Gram matrix beyond plain Cholesky QR takes the shifted path."""
     n, m = 400, 16
     rng = _rng(5)
     base = _cgauss(rng, n, m)
     Y = base.copy()
     Y[:, 5] = base[:, 4] + 1e-9 * _cgauss(rng, n)
-    got = _np(cb.chfsi_orthonormalize(ctx, _t(Y)))
+    got = _np(cb.chfsi_orthonormalize(ctx if mode == "split" else ctx64, _t(Y)))
     assert np.max(np.abs(got.conj().T @ got - np.eye(m))) < 1e-12
+    # the span still holds the well-determined directions of Y
+    keep = [j for j in range(m) if j != 5]
+    P = got @ got.conj().T
+    assert np.linalg.norm(P @ base[:, keep] - base[:, keep]) < 1e-6 * np.linalg.norm(base)
 
 
 @pytest.mark.parametrize("n,m", [(300, 25), (640, 130), (513, 131)])

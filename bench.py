@@ -232,13 +232,18 @@ def run_ours(args):
     g_ms = sum(s["t_filter_gemm_ms"] for s in all_stats)
     t_flops = sum(s["tensor_flops"] for s in all_stats)
     fp64_equiv = 8.0 * n * n * sum(s["filter_matvecs"] for s in all_stats)
+    # DRAM traffic per launch: one ncu capture of the kernel (profiles/oz_gemm_tc_traffic.json)
+    # gives DRAM bytes / bytes of Hs digit slices streamed (the launch's minimum traffic); the
+    # step's launches are scaled by the slice bytes they stream (counted by the library).
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "filter_gemm_traffic.json")
-    if os.path.exists(tfile):
+    tfile = os.path.join(ROOT, "profiles", "oz_gemm_tc_traffic.json")
+    products = sum(s["filter_products"] for s in all_stats)
+    if os.path.exists(tfile) and products > 0 and os.environ.get("CHFSI_OZ_KERNEL", "tc") != "mma":
         try:
             with open(tfile) as f:
-                traffic = json.load(f).get("dram_bytes_per_launch")
-        except (OSError, ValueError):
+                ratio = float(json.load(f)["dram_bytes_over_slice_bytes"])
+            traffic = ratio * sum(s["filter_slice_bytes"] for s in all_stats) / products
+        except (OSError, ValueError, KeyError):
             traffic = None
     if t_flops > 0:
         achieved = t_flops / (g_ms / 1e3) / 1e12
@@ -249,8 +254,12 @@ def run_ours(args):
         roofline = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": traffic,
                     "fp64_equivalent_tflops": fp64_equiv / (g_ms / 1e3) / 1e12,
+                    "launches": products,
+                    "algorithmic_bytes_per_launch": (sum(s["filter_slice_bytes"] for s in all_stats)
+                                                     / products) if products else None,
                     "peak_note": f"bf16 dense sustained ({peak_kind}); achieved counts the "
-                                 "slice-pair MMA flops executed (padded tiles)"}
+                                 "slice-pair products (2 x pairs x 2n x m x 2n flops each, "
+                                 "unpadded) over the product kernel's CUDA-event time"}
     else:
         fp64_peak = peaks["bf16_tflops_sustained"] * 1.25 / 2250.0
         achieved = fp64_equiv / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
@@ -317,14 +326,18 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (bf16 digit-slice tensor products)",
+            "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}: n={n} nev={nev} blk={blk} deg adaptive "
                                    f"{seq.deg_min}-{seq.deg_max} N={N} cond(B)=1e4, planted "
                                    f"spectrum, first problem cold, rest warm",
                        "l2": "inputs larger than L2 (A,B of 20 problems = 4.3 GB per step)",
-                       "filter_arithmetic": "split-BF16 digit slices (adaptive 2-7 per operand) "
-                                            "on tensor cores, exact fp32 chunks, double-float "
-                                            "sums; reduction, QR, Rayleigh-Ritz, residuals FP64",
+                       "filter_arithmetic": "FP64 results from bf16 digit-slice tensor-core "
+                                            "products (exact fp32 chunks, double-float sums): "
+                                            "filter 2-7 slices chosen per loop, Rayleigh-Ritz, "
+                                            "reduction and other large products 8 slices; FP32 "
+                                            "Cholesky QR + FP64 Loewdin steps; FP64 Jacobi "
+                                            "eigensolver, residuals and small products",
                        "tol": seq.tol, "max_resid": max_resid,
                        "loops_per_problem": [s["loops"] for s in all_stats[:N]],
                        "filtered_vectors_per_problem": [s["filtered_vectors"] for s in all_stats[:N]],

@@ -72,13 +72,17 @@ typedef struct {
   int64_t filter_matvecs;    /* column products Hs*y inside the Chebyshev filter only */
   int64_t launches;          /* CUDA kernels launched by the library for this problem */
   int64_t filter_matvecs_fp64; /* filter column products done with FP64 arithmetic */
-  double tensor_flops;       /* tensor-core flops of the split-BF16 filter products (padded) */
+  double tensor_flops;       /* tensor-core flops of the split-BF16 filter products, counted on the
+                                unpadded operands: 2 * pairs * (2n) * m * (2n) per product */
   double max_resid;          /* max_i ||A x_i - lambda_i B x_i|| / (||A||_est ||x_i||) */
   double lanczos_upper;      /* spectral upper bound b used by the filter */
   double t_reduce_ms, t_lanczos_ms, t_filter_ms, t_qr_ms, t_rr_ms, t_resid_ms, t_total_ms;
   double t_filter_gemm_ms;   /* device time of the filter's product kernels alone */
   double t_small_ms;         /* Cholesky QR factorisations of the Gram matrices (within t_qr) */
   double t_eig_ms;           /* Rayleigh-Ritz eigensolver (within t_rr) */
+  int64_t filter_products;   /* split-BF16 product launches of the filter */
+  double filter_slice_bytes; /* bytes of the Hs digit slices those launches stream (S * Mp * Kp * 2
+                                each): the launches' minimum DRAM traffic */
 } chfsi_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -47,7 +47,8 @@ class chfsi_stats(ctypes.Structure):
                 ("lanczos_upper", c_double), ("t_reduce_ms", c_double), ("t_lanczos_ms", c_double),
                 ("t_filter_ms", c_double), ("t_qr_ms", c_double), ("t_rr_ms", c_double),
                 ("t_resid_ms", c_double), ("t_total_ms", c_double), ("t_filter_gemm_ms", c_double),
-                ("t_small_ms", c_double), ("t_eig_ms", c_double)]
+                ("t_small_ms", c_double), ("t_eig_ms", c_double),
+                ("filter_products", c_int64), ("filter_slice_bytes", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -340,8 +340,9 @@ int filter_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya
       CK(oz_filter_product(cur, ld, n, mk, slices, al, be, cur, ld, k >= 2 ? ga : 0.0, out, ld, out,
                            ld, ws.oz, ctx->stream, gb, ge));
       if (st) {
-        st->tensor_flops += 2.0 * (double)oz_pair_count(slices) * ws.oz.H.Mp *
-                            (double)oz_padded_n(mk) * ws.oz.H.Kp;
+        st->tensor_flops += 2.0 * (double)oz_pair_count(slices) * (2.0 * n) * (double)mk * (2.0 * n);
+        st->filter_products += 1;
+        st->filter_slice_bytes += 2.0 * (double)slices * ws.oz.H.Mp * (double)ws.oz.H.Kp;
       }
     } else {
       GemmDesc g = gd(n, mk, n, H, ldh, OPN, cur, ld, OPN, out, ld, al);
@@ -392,7 +393,9 @@ int slices_for_loop(double hs_norm, double tau, double r_min, double a0, double 
   return std::min(s_max, std::max(2, S));
 }
 
-// CGS2 against YL (k columns) then Cholesky QR three times (shifted on breakdown).
+// CGS2 against YL (k columns), then re-orthonormalisation: in mixed precision FP32 Cholesky QR
+// steps and FP64 Loewdin steps chosen on the device (qr_pass); in FP64 Cholesky QR twice, three
+// times when the first pass needed the shifted retry.
 int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const zd* YL, int64_t ldyl,
                          int k) {
   Workspace& ws = ctx->ws;

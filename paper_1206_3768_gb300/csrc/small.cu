@@ -373,16 +373,42 @@ __device__ __forceinline__ zd ldcg(const zd* p) { return __ldcg(p); }
 // 2x2 products with the rotation U = [[c, s], [-s w, c w]], w = e^{-i phi}.
 struct Rot { double c, s; zd w; int active; };
 
-__global__ void __launch_bounds__(128) jacobi_kernel(const JacParams P) {
+constexpr int JAC_THREADS = 256;
+
+__device__ __forceinline__ Rot jacobi_rotation(const zd* src, int mp, int p, int q, double thresh) {
+  const double a = ldcg(src + p + (int64_t)p * mp).x;
+  const double d = ldcg(src + q + (int64_t)q * mp).x;
+  const zd b = ldcg(src + p + (int64_t)q * mp);
+  const double ab = sqrt(zabs2(b));
+  Rot R;
+  if (!(ab > thresh)) {
+    R.c = 1.0; R.s = 0.0; R.w = zmk(1.0, 0.0); R.active = 0;
+  } else {
+    const double zeta = (d - a) / (2.0 * ab);
+    const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+    R.c = 1.0 / sqrt(1.0 + t_ * t_);
+    R.s = t_ * R.c;
+    R.w = zmk(b.x / ab, -b.y / ab);  // e^{-i phi}
+    R.active = 1;
+  }
+  return R;
+}
+
+// One CTA per rotation pair.  Per round: thread e (< mp) owns output row (e & 1 ? q : p) of
+// this CTA's pair and column pair t = e >> 1; it loads its four source entries before the
+// rotations are computed (so the L2 latency overlaps them), then writes two entries.  The
+// CTA's two rows of V stay in shared memory for the whole run.
+__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) {
   extern __shared__ unsigned char smem_raw[];
-  Rot* rot = reinterpret_cast<Rot*>(smem_raw);
-  __shared__ double red[128];
-  const int tid = threadIdx.x, nt = blockDim.x;
   const int mp = P.mp, half = mp / 2;
+  Rot* rot = reinterpret_cast<Rot*>(smem_raw);
+  zd* vrow = reinterpret_cast<zd*>(smem_raw + sizeof(Rot) * (size_t)half);  // 2 x mp
+  __shared__ double red[JAC_THREADS];
+  const int tid = threadIdx.x, nt = blockDim.x;
   const unsigned nb = gridDim.x;
   const int cta = blockIdx.x;
 
-  // ---- set-up: rows 2cta, 2cta+1 of Ga (padded copy of G) and of Vw (identity)
+  // ---- set-up: rows 2cta, 2cta+1 of Ga (padded copy of G) and of V (identity)
   for (int rr = 0; rr < 2; ++rr) {
     const int i = 2 * cta + rr;
     for (int j = tid; j < mp; j += nt) {
@@ -390,7 +416,7 @@ __global__ void __launch_bounds__(128) jacobi_kernel(const JacParams P) {
       if (i < P.m && j < P.m) v = P.G[i + (int64_t)j * P.ldg];
       if (i == j) v.y = 0.0;
       P.Ga[i + (int64_t)j * mp] = v;
-      P.Vw[i + (int64_t)j * mp] = zmk(i == j ? 1.0 : 0.0, 0.0);
+      vrow[rr * mp + j] = zmk(i == j ? 1.0 : 0.0, 0.0);
     }
   }
   // threshold from ||G||_F (computed redundantly by every CTA)
@@ -432,78 +458,71 @@ __global__ void __launch_bounds__(128) jacobi_kernel(const JacParams P) {
     for (int round = 0; round < mp - 1; ++round) {
       const zd* src = parity ? P.Gb : P.Ga;
       zd* dst = parity ? P.Ga : P.Gb;
-      // all rotations of this round (same inputs, same result on every CTA)
-      for (int t = tid; t < half; t += nt) {
-        int p, q;
-        pair_of(round, t, mp, p, q);
-        const double a = ldcg(src + p + (int64_t)p * mp).x;
-        const double d = ldcg(src + q + (int64_t)q * mp).x;
-        const zd b = ldcg(src + p + (int64_t)q * mp);
-        const double ab = sqrt(zabs2(b));
-        Rot R;
-        if (!(ab > thresh)) {
-          R.c = 1.0; R.s = 0.0; R.w = zmk(1.0, 0.0); R.active = 0;
-        } else {
-          const double zeta = (d - a) / (2.0 * ab);
-          const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-          R.c = 1.0 / sqrt(1.0 + t_ * t_);
-          R.s = t_ * R.c;
-          R.w = zmk(b.x / ab, -b.y / ab);  // e^{-i phi}
-          R.active = 1;
-        }
-        rot[t] = R;
-      }
-      __syncthreads();
-      // my pair: rows p, q of dst = U_P^H src[P, R] U_R for every pair R
       int p, q;
       pair_of(round, cta, mp, p, q);
+      // this thread's first item: source entries of rows p, q at its column pair
+      zd m00, m01, m10, m11;
+      if (tid < mp) {
+        int r, s;
+        pair_of(round, tid >> 1, mp, r, s);
+        m00 = ldcg(src + p + (int64_t)r * mp); m01 = ldcg(src + p + (int64_t)s * mp);
+        m10 = ldcg(src + q + (int64_t)r * mp); m11 = ldcg(src + q + (int64_t)s * mp);
+      }
+      // all rotations of this round (same inputs, same result on every CTA)
+      for (int t = tid; t < half; t += nt) {
+        int a, b;
+        pair_of(round, t, mp, a, b);
+        rot[t] = jacobi_rotation(src, mp, a, b, thresh);
+      }
+      __syncthreads();
       const Rot RP = rot[cta];
       const zd wpc = zconj(RP.w);  // e^{+i phi}
-      for (int t = tid; t < half; t += nt) {
+      const zd sw = zscale(wpc, RP.s), cw = zscale(wpc, RP.c);
+      for (int e = tid; e < mp; e += nt) {
+        const int t = e >> 1, row = e & 1;
         int r, s;
         pair_of(round, t, mp, r, s);
+        if (e != tid) {
+          m00 = ldcg(src + p + (int64_t)r * mp); m01 = ldcg(src + p + (int64_t)s * mp);
+          m10 = ldcg(src + q + (int64_t)r * mp); m11 = ldcg(src + q + (int64_t)s * mp);
+        }
         const Rot RR = rot[t];
-        const zd m00 = ldcg(src + p + (int64_t)r * mp), m01 = ldcg(src + p + (int64_t)s * mp);
-        const zd m10 = ldcg(src + q + (int64_t)r * mp), m11 = ldcg(src + q + (int64_t)s * mp);
-        // left: U_P^H = [[c, -s e^{i phi}], [s, c e^{i phi}]]
-        const zd sw = zscale(wpc, RP.s), cw = zscale(wpc, RP.c);
-        const zd l00 = zsub(zscale(m00, RP.c), zmul(sw, m10));
-        const zd l01 = zsub(zscale(m01, RP.c), zmul(sw, m11));
-        const zd l10 = zadd(zscale(m00, RP.s), zmul(cw, m10));
-        const zd l11 = zadd(zscale(m01, RP.s), zmul(cw, m11));
+        // left: U_P^H = [[c, -s e^{i phi}], [s, c e^{i phi}]]; this thread's row only
+        zd l0, l1;
+        if (row == 0) {
+          l0 = zsub(zscale(m00, RP.c), zmul(sw, m10));
+          l1 = zsub(zscale(m01, RP.c), zmul(sw, m11));
+        } else {
+          l0 = zadd(zscale(m00, RP.s), zmul(cw, m10));
+          l1 = zadd(zscale(m01, RP.s), zmul(cw, m11));
+        }
         // right: U_R = [[c, s], [-s w, c w]]
         const zd rsw = zscale(RR.w, RR.s), rcw = zscale(RR.w, RR.c);
-        zd n00 = zsub(zscale(l00, RR.c), zmul(l01, rsw));
-        zd n01 = zadd(zscale(l00, RR.s), zmul(l01, rcw));
-        zd n10 = zsub(zscale(l10, RR.c), zmul(l11, rsw));
-        zd n11 = zadd(zscale(l10, RR.s), zmul(l11, rcw));
+        zd n0 = zsub(zscale(l0, RR.c), zmul(l1, rsw));
+        zd n1 = zadd(zscale(l0, RR.s), zmul(l1, rcw));
         if (t == cta) {  // diagonal block: exact diagonal result
-          n00.y = 0.0; n11.y = 0.0;
-          if (RP.active) { n01 = zmk(0.0, 0.0); n10 = zmk(0.0, 0.0); }
+          if (row == 0) { n0.y = 0.0; if (RP.active) n1 = zmk(0.0, 0.0); }
+          else { n1.y = 0.0; if (RP.active) n0 = zmk(0.0, 0.0); }
         }
-        dst[p + (int64_t)r * mp] = n00;
-        dst[p + (int64_t)s * mp] = n01;
-        dst[q + (int64_t)r * mp] = n10;
-        dst[q + (int64_t)s * mp] = n11;
-      }
-      // V rows 2cta, 2cta+1 (owned for the whole run): V[i, R] <- V[i, R] U_R
-      for (int e = tid; e < 2 * half; e += nt) {
-        const int i = 2 * cta + (e & 1);
-        const int t = e >> 1;
-        int r, s;
-        pair_of(round, t, mp, r, s);
-        const Rot RR = rot[t];
-        if (!RR.active) continue;
-        zd* vr = P.Vw + i + (int64_t)r * mp;
-        zd* vs = P.Vw + i + (int64_t)s * mp;
-        const zd a0 = *vr, a1 = *vs;
-        const zd rsw = zscale(RR.w, RR.s), rcw = zscale(RR.w, RR.c);
-        *vr = zsub(zscale(a0, RR.c), zmul(a1, rsw));
-        *vs = zadd(zscale(a0, RR.s), zmul(a1, rcw));
+        const int orow = row ? q : p;
+        dst[orow + (int64_t)r * mp] = n0;
+        dst[orow + (int64_t)s * mp] = n1;
+        // V rows 2cta, 2cta+1 (shared memory): V[i, R] <- V[i, R] U_R
+        if (RR.active) {
+          zd* vi = vrow + row * mp;
+          const zd a0 = vi[r], a1 = vi[s];
+          vi[r] = zsub(zscale(a0, RR.c), zmul(a1, rsw));
+          vi[s] = zadd(zscale(a0, RR.s), zmul(a1, rcw));
+        }
       }
       parity ^= 1;
       if (!grid_barrier(P.bar, nb, P.status)) return;
     }
+  }
+  __syncthreads();
+  for (int rr = 0; rr < 2; ++rr) {
+    const int i = 2 * cta + rr;
+    for (int j = tid; j < mp; j += nt) P.Vw[i + (int64_t)j * mp] = vrow[rr * mp + j];
   }
   if (cta == 0 && tid == 0) {
     if (sweep >= P.max_sweeps) atomicOr(P.status, DEV_NOCONV);
@@ -598,13 +617,13 @@ cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64
   cudaError_t e = cudaMemsetAsync(barrier, 0, 4 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   const int half = mp / 2;
-  const size_t smem = sizeof(Rot) * (size_t)half;
+  const size_t smem = sizeof(Rot) * (size_t)half + 2 * sizeof(zd) * (size_t)mp;
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   void* args[] = {(void*)&P};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(half), dim3(128), args, smem, s);
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(half), dim3(JAC_THREADS), args, smem, s);
   CHFSI_COUNT_LAUNCH();
   if (e != cudaSuccess) return e;
   const size_t smem2 = (size_t)m * (sizeof(double) + sizeof(int));

@@ -272,6 +272,44 @@ def run_ours(args):
              ("t_reduce_ms", "t_lanczos_ms", "t_filter_ms", "t_filter_gemm_ms", "t_qr_ms", "t_small_ms",
               "t_rr_ms", "t_eig_ms", "t_resid_ms", "t_total_ms")}
 
+    # ---- deviation angles between eigenvectors of adjacent problems (Section 2.2, Fig. 1),
+    # from the last timed step's eigenvectors (outside the timed region)
+    dev_angles = None
+    if not args.no_angles and evecs is not None and N > 1:
+        medians, maxs = [], []
+        for ell in range(1, N):
+            th, _ = cb.chfsi_deviation_angles(ctx, evecs[ell - 1], evecs[ell], Bs[ell])
+            medians.append(float(th.median()))
+            maxs.append(float(th.max()))
+        dev_angles = {"median": medians, "max": maxs,
+                      "note": "angle between x_i of problem l-1 and its associated x of problem l "
+                              "(B-inner product), l = 1..N-1; a max near pi/2 marks an "
+                              "eigenvalue crossing the nev boundary (its partner is not computed)"}
+
+    # ---- a direct solver on the same problem for context (library code, not this path):
+    # torch.linalg Cholesky, triangular solves and the dense Hermitian eigensolver (all
+    # eigenpairs, from which the nev lowest are kept), one cold problem
+    direct = None
+    if not args.no_direct:
+        A0 = seq.problems[0].A
+        B0 = seq.problems[0].B
+        torch.linalg.eigh(torch.eye(64, dtype=torch.complex128, device=dev))  # library warm-up
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        Lc = torch.linalg.cholesky(B0)
+        T1 = torch.linalg.solve_triangular(Lc, A0, upper=False)
+        Hd = torch.linalg.solve_triangular(Lc, T1.mH, upper=False).mH
+        wd, _ = torch.linalg.eigh(0.5 * (Hd + Hd.mH))
+        d1.record(stream)
+        torch.cuda.synchronize()
+        dms = d0.elapsed_time(d1)
+        err = float((wd[:nev].cpu().numpy() - seq.problems[0].lam[:nev]).__abs__().max())
+        direct = {"value": nev / (dms / 1e3), "unit": UNIT, "ms_per_problem": dms,
+                  "kind": "torch.linalg cholesky + solve_triangular + eigh (cuSOLVER), one cold problem",
+                  "max_abs_eig_err": err}
+
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
     e2e = None
     if not args.no_e2e:
@@ -346,6 +384,8 @@ def run_ours(args):
             "plain_fp64": plain,
             "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
             "cpu_baseline": cpu,
+            "direct_solver": direct,
+            "deviation_angles": dev_angles,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -428,6 +468,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-angles", action="store_true")
+    ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--problems", type=int, default=None,
                     help="solve only the first N problems of the sequence (profiling runs)")
     ap.add_argument("--kernel-case", choices=["filter", "heev"], default=None)

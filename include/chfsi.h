@@ -166,8 +166,10 @@ int chfsi_filter_split(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, i
                        double b, int32_t slices);
 
 /* Re-orthonormalisation (Algorithm 1): Y <- orthonormal basis of (I - YL YL^H) Y, by two
- * passes of classical Gram-Schmidt against the k locked columns YL (may be 0) and
- * Cholesky QR repeated three times (shifted on breakdown).  In place, n x m. */
+ * passes of classical Gram-Schmidt against the k locked columns YL (may be 0), then with
+ * precision 1 FP32 Cholesky QR steps and FP64 first-order Loewdin steps chosen from the
+ * Gram matrix on the device (orthonormal to about 1e-15), with precision 0 Cholesky QR
+ * twice (three times, shifted, on breakdown).  In place, n x m. */
 int chfsi_orthonormalize(chfsi_ctx* ctx, int64_t n, int32_t m, chfsi_z* Y, int64_t ldy,
                          int32_t k, const chfsi_z* YL, int64_t ldyl);
 
@@ -181,6 +183,22 @@ int chfsi_rayleigh_ritz(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, 
  * theta, r: device, m doubles. */
 int chfsi_residuals(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* HY, int64_t ldhy,
                     const chfsi_z* Y, int64_t ldy, const double* theta, double* r);
+
+/* Deviation angles between eigenvectors of adjacent problems of a sequence (Section 2.2:
+ * the scalar products <x_i^(l) x_j^(l+1)> of eigenvectors of neighbouring pencils and the
+ * angles theta_i^(l) plotted in Fig. 1).  With a common overlap matrix B (lower triangle
+ * read) the paper's product c^(l)H L L^H c^(l+1) is the B-inner product, so
+ * M = X_prev^H B X_cur (k x k).  Previous vector i is associated with current vector
+ * assoc[i] by repeatedly taking the largest |M_ij| over unassigned rows and columns (ties:
+ * smallest row, then smallest column), the one-to-one matching the paper bases on the
+ * diagonal dominance of M; theta_i = asin(min(1, ||r_i||_B)) with
+ * r_i = u_c - u_p (u_p^H B u_c), u_p and u_c the B-normalised x_prev_i and x_cur_assoc[i]
+ * (full relative accuracy for small angles).  X_prev, X_cur: device, n x k; B: device,
+ * n x n; theta: device, k doubles; assoc: device, k int32.  k <= blk_max, n <= n_max.
+ * Uses the context's scratch buffers; the warm state and the stored factor of B are kept. */
+int chfsi_deviation_angles(chfsi_ctx* ctx, int64_t n, int32_t k, const chfsi_z* X_prev, int64_t ldp,
+                           const chfsi_z* X_cur, int64_t ldc, const chfsi_z* B, int64_t ldb,
+                           double* theta, int32_t* assoc);
 
 /* Closed-form per-vector degrees (not in the paper; the adaptive mode):
  * d_i = clamp(ceil(ln(r_i/tau)/ln rho_i), dmin, dmax), rho_i = |t_i| + sqrt(t_i^2-1),

@@ -466,3 +466,58 @@ def chfsi_solve_sequence(As, Bs, nev: int, blk: int, tol: float = 1e-10, deg: in
                                        seed=seed, **kw)
         out.append((lam, X, st))
     return out
+
+
+# --------------------------------------------------------------------------------------
+# Deviation angles between eigenvectors of adjacent problems (Section 2.2, the relation
+# for the scalar products <x_i^(l) x_j^(l+1)> and the angles theta_i^(l) of Fig. 1).
+# --------------------------------------------------------------------------------------
+def scalar_products(X_prev: np.ndarray, X_cur: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """M_ij = <x_i^(l) x_j^(l+1)>.  With the Cholesky factor L of a fixed B the paper's
+    product c^(l)H L L^H c^(l+1) is the B-inner product x_i^H B x_j."""
+    return X_prev.conj().T @ (B @ X_cur)
+
+
+def associate(M: np.ndarray) -> np.ndarray:
+    """One-to-one association of previous to current eigenvectors from the dominant
+    entries of |M| (Section 2.2): repeatedly take the largest |M_ij| among unassigned
+    rows and columns (ties: smallest row, then smallest column).  Returns assoc with
+    assoc[i] = j, the current vector matched to previous vector i."""
+    A = np.abs(M).astype(np.float64)
+    k = A.shape[0]
+    assoc = np.full(k, -1, dtype=np.int64)
+    free_r = np.ones(k, dtype=bool)
+    free_c = np.ones(k, dtype=bool)
+    for _ in range(k):
+        best, bi, bj = -1.0, -1, -1
+        for i in range(k):
+            if not free_r[i]:
+                continue
+            for j in range(k):
+                if free_c[j] and A[i, j] > best:
+                    best, bi, bj = A[i, j], i, j
+        assoc[bi] = bj
+        free_r[bi] = False
+        free_c[bj] = False
+    return assoc
+
+
+def deviation_angles(X_prev: np.ndarray, X_cur: np.ndarray, B: np.ndarray):
+    """theta_i = angle between x_i^(l) and its associated x_assoc(i)^(l+1) in the B-inner
+    product (B-normalised columns), computed as asin of the B-norm of the component of
+    x_assoc(i) orthogonal to x_i, so that small angles keep full relative accuracy.
+    Returns (theta, assoc)."""
+    M = scalar_products(X_prev, X_cur, B)
+    assoc = associate(M)
+    k = M.shape[0]
+    theta = np.empty(k)
+    for i in range(k):
+        xp = X_prev[:, i]
+        xc = X_cur[:, assoc[i]]
+        npv = math.sqrt(max(np.real(np.vdot(xp, B @ xp)), 0.0))
+        ncv = math.sqrt(max(np.real(np.vdot(xc, B @ xc)), 0.0))
+        up, uc = xp / npv, xc / ncv
+        r = uc - up * np.vdot(up, B @ uc)
+        s = math.sqrt(max(np.real(np.vdot(r, B @ r)), 0.0))
+        theta[i] = math.asin(min(1.0, s))
+    return theta, assoc

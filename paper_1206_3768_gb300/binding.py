@@ -80,6 +80,8 @@ _SIGS = {
     "chfsi_degrees": (c_int32, [_P, c_int32, _P, _P, c_double, c_double, c_double, c_int32,
                                 c_int32, c_int32, _P]),
     "chfsi_heev": (c_int32, [_P, c_int32, _P, c_int64, _P, _P, c_int64]),
+    "chfsi_deviation_angles": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64, _P, c_int64,
+                                         _P, _P]),
     "chfsi_heev_noalloc": (c_int32, [c_int32, _P, c_int64, _P, _P, c_int64, _P]),
     "chfsi_zgemm": (c_int32, [_P, c_char, c_char, c_int32, c_int32, c_int32, c_double, _P, c_int64,
                               _P, c_int64, c_double, _P, c_int64]),
@@ -323,6 +325,18 @@ def chfsi_degrees(ctx, theta: torch.Tensor, r: torch.Tensor, a: float, b: float,
     _check(ctx, load().chfsi_degrees(ctx, m, _ptr(theta.contiguous()), _ptr(r.contiguous()), a, b,
                                      tau, dmin, dmax, n_wanted, _ptr(d)))
     return d
+
+
+def chfsi_deviation_angles(ctx, X_prev: torch.Tensor, X_cur: torch.Tensor, B: torch.Tensor):
+    """Deviation angles theta_i between x_prev_i and its associated current vector
+    x_cur[:, assoc[i]] in the B-inner product (Section 2.2, Fig. 1).  Returns (theta, assoc)."""
+    n, k = X_prev.shape
+    Pf, Cf, Bf = fortran(X_prev), fortran(X_cur), fortran(B)
+    theta = torch.empty(k, dtype=torch.float64, device=X_prev.device)
+    assoc = torch.empty(k, dtype=torch.int32, device=X_prev.device)
+    _check(ctx, load().chfsi_deviation_angles(ctx, n, k, _ptr(Pf), _ld(Pf), _ptr(Cf), _ld(Cf), _ptr(Bf),
+                                              _ld(Bf), _ptr(theta), _ptr(assoc)))
+    return theta, assoc
 
 
 def chfsi_heev(ctx, G: torch.Tensor):

@@ -1194,6 +1194,34 @@ int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* 
   return CHFSI_OK;
 }
 
+int chfsi_deviation_angles(chfsi_ctx* ctx, int64_t n, int32_t k, const chfsi_z* X_prev, int64_t ldp,
+                           const chfsi_z* X_cur, int64_t ldc, const chfsi_z* B, int64_t ldb,
+                           double* theta, int32_t* assoc) {
+  entry_guard("chfsi_deviation_angles");
+  if (!ctx || !X_prev || !X_cur || !B || !theta || !assoc || n <= 0 || k <= 0 || k > n || ldp < n ||
+      ldc < n || ldb < n)
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  Workspace& ws = ctx->ws;
+  if (n > ws.n_max || k > ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "n > n_max or k > blk_max");
+  cudaSetDevice(ws.dev);
+  CKS(reset_status(ctx));
+  const int64_t ld = ws.n_max, ldm = ws.blk_max;
+  const int ni = (int)n;
+  // Hermitian completion of B in the product scratch (not ws.Bf, which keys the reuse of L)
+  CK(herm_from_lower(Z(B), ldb, ws.T, ld, ni, ws.status, ctx->stream));
+  CKS(gemm_auto(ctx, gd(ni, k, ni, ws.T, ld, OPN, Z(X_cur), ldc, OPN, ws.W, ld)));
+  CKS(gemm_auto(ctx, gd(ni, k, ni, ws.T, ld, OPN, Z(X_prev), ldp, OPN, ws.Z, ld)));
+  CKS(gemm_auto(ctx, gd(k, k, ni, Z(X_prev), ldp, OPC, ws.W, ld, OPN, ws.G, ldm)));
+  CK(bnorms(Z(X_prev), ldp, ws.Z, ld, ni, k, ws.resid, ctx->stream));
+  CK(bnorms(Z(X_cur), ldc, ws.W, ld, ni, k, ws.resid2, ctx->stream));
+  CK(associate(ws.G, ldm, k, assoc, ctx->stream));
+  CK(deviation_residual(Z(X_prev), ldp, Z(X_cur), ldc, ws.G, ldm, ws.resid, ws.resid2, assoc, ni, k,
+                        ws.F, ld, ctx->stream));
+  CKS(gemm_auto(ctx, gd(ni, k, ni, ws.T, ld, OPN, ws.F, ld, OPN, ws.Y0, ld)));
+  CK(deviation_theta(ws.F, ld, ws.Y0, ld, ni, k, theta, ctx->stream));
+  return check_status(ctx, "chfsi_deviation_angles");
+}
+
 int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double* w, chfsi_z* V,
                int64_t ldv) {
   entry_guard("chfsi_heev");

@@ -90,6 +90,18 @@ cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* 
 cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64_t ldv,
                         zd* work, unsigned* barrier, int* status, cudaStream_t s);
 
+// Deviation angles (Section 2.2, Fig. 1): B-norms of columns from W = B X; greedy
+// one-to-one association from |M|; the B-orthogonal parts R of the associated current
+// vectors; theta_i = asin(min(1, ||r_i||_B)) from BR = B R.
+cudaError_t bnorms(const zd* X, int64_t ldx, const zd* W, int64_t ldw, int n, int k, double* nrm,
+                   cudaStream_t s);
+cudaError_t associate(const zd* M, int64_t ldm, int k, int* assoc, cudaStream_t s);
+cudaError_t deviation_residual(const zd* Xp, int64_t ldp, const zd* Xc, int64_t ldc, const zd* M,
+                               int64_t ldm, const double* np_, const double* nc_, const int* assoc,
+                               int n, int k, zd* R, int64_t ldr, cudaStream_t s);
+cudaError_t deviation_theta(const zd* R, int64_t ldr, const zd* BR, int64_t ldbr, int n, int k,
+                            double* theta, cudaStream_t s);
+
 // ------------------------------------------------------------------ vector kernels
 cudaError_t herm_from_lower(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n,
                             int* status, cudaStream_t s);

@@ -376,6 +376,92 @@ inline int grid_for(int64_t total, int threads = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(8 * sm_count(), (total + threads - 1) / threads));
 }
 
+// ------------------------------------------------------------------ deviation angles
+// Deviation angles between eigenvectors of adjacent problems (Section 2.2 and Fig. 1).
+// nrm[j] = sqrt(Re(x_j^H w_j)), w_j = B x_j: the B-norm of column j.
+__global__ void bnorm_kernel(const zd* X, int64_t ldx, const zd* W, int64_t ldw, int n, double* nrm) {
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const zd x = X[i + (int64_t)j * ldx], w = W[i + (int64_t)j * ldw];
+    acc += x.x * w.x + x.y * w.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) nrm[j] = sqrt(fmax(acc, 0.0));
+}
+
+// One-to-one association from |M| (k x k): k times, the largest |M_ij| over unassigned
+// rows and columns (ties: smallest row, then smallest column) is assigned.  One CTA; the
+// free flags of rows and columns live in shared memory (2k ints).
+__global__ void associate_kernel(const zd* M, int64_t ldm, int k, int* assoc) {
+  extern __shared__ int free_rc[];
+  int* free_r = free_rc;
+  int* free_c = free_rc + k;
+  __shared__ double bv[32];
+  __shared__ long long bi[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < k; i += blockDim.x) { free_r[i] = 1; free_c[i] = 1; }
+  __syncthreads();
+  for (int step = 0; step < k; ++step) {
+    double best = -1.0;
+    long long idx = 0x7fffffffffffffffLL;
+    for (long long e = tid; e < (long long)k * k; e += blockDim.x) {
+      const int i = (int)(e / k), j = (int)(e % k);  // e = i k + j: lexicographic (i, j)
+      if (!free_r[i] || !free_c[j]) continue;
+      const zd v = M[i + (int64_t)j * ldm];
+      const double a = sqrt(v.x * v.x + v.y * v.y);
+      if (a > best || (a == best && e < idx)) { best = a; idx = e; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const long long oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ob > best || (ob == best && oi < idx)) { best = ob; idx = oi; }
+    }
+    if (lane == 0) { bv[w] = best; bi[w] = idx; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = bv[0];
+      long long x = bi[0];
+      for (int q = 1; q < nw; ++q)
+        if (bv[q] > b || (bv[q] == b && bi[q] < x)) { b = bv[q]; x = bi[q]; }
+      const int i = (int)(x / k), j = (int)(x % k);
+      assoc[i] = j;
+      free_r[i] = 0;
+      free_c[j] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// R[:, i] = u_c - u_p (u_p^H B u_c) with u_p = x_prev_i / np_i, u_c = x_cur_a / nc_a,
+// a = assoc[i], and u_p^H B u_c = M(i, a) / (np_i nc_a).
+__global__ void dev_residual_kernel(const zd* Xp, int64_t ldp, const zd* Xc, int64_t ldc, const zd* M,
+                                    int64_t ldm, const double* np_, const double* nc_, const int* assoc,
+                                    int n, zd* R, int64_t ldr) {
+  const int i = blockIdx.x;
+  const int a = assoc[i];
+  const double ip = 1.0 / np_[i], ic = 1.0 / nc_[a];
+  const zd mu = zscale(M[i + (int64_t)a * ldm], ip * ic);
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const zd up = zscale(Xp[r + (int64_t)i * ldp], ip);
+    const zd uc = zscale(Xc[r + (int64_t)a * ldc], ic);
+    R[r + (int64_t)i * ldr] = zsub(uc, zmul(up, mu));
+  }
+}
+
+// theta_i = asin(min(1, sqrt(Re(r_i^H (B r_i))))).
+__global__ void dev_theta_kernel(const zd* R, int64_t ldr, const zd* BR, int64_t ldbr, int n, double* theta) {
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const zd x = R[r + (int64_t)i * ldr], w = BR[r + (int64_t)i * ldbr];
+    acc += x.x * w.x + x.y * w.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) theta[i] = asin(fmin(1.0, sqrt(fmax(acc, 0.0))));
+}
+
 }  // namespace
 
 cudaError_t herm_from_lower(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int* status,
@@ -508,6 +594,36 @@ cudaError_t lanczos_record(const zd* c, int j, const double* nrm, double* alpha,
 cudaError_t tridiag_extremes(const double* alpha, const double* beta, int k, double* out3,
                              cudaStream_t s) {
   tridiag_extremes_kernel<<<1, 32, 0, s>>>(alpha, beta, k, out3);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t bnorms(const zd* X, int64_t ldx, const zd* W, int64_t ldw, int n, int k, double* nrm,
+                   cudaStream_t s) {
+  bnorm_kernel<<<k, 256, 0, s>>>(X, ldx, W, ldw, n, nrm);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+cudaError_t associate(const zd* M, int64_t ldm, int k, int* assoc, cudaStream_t s) {
+  const size_t smem = 2 * sizeof(int) * (size_t)k;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(associate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  associate_kernel<<<1, 1024, smem, s>>>(M, ldm, k, assoc);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+cudaError_t deviation_residual(const zd* Xp, int64_t ldp, const zd* Xc, int64_t ldc, const zd* M,
+                               int64_t ldm, const double* np_, const double* nc_, const int* assoc,
+                               int n, int k, zd* R, int64_t ldr, cudaStream_t s) {
+  dev_residual_kernel<<<k, 256, 0, s>>>(Xp, ldp, Xc, ldc, M, ldm, np_, nc_, assoc, n, R, ldr);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+cudaError_t deviation_theta(const zd* R, int64_t ldr, const zd* BR, int64_t ldbr, int n, int k,
+                            double* theta, cudaStream_t s) {
+  dev_theta_kernel<<<k, 256, 0, s>>>(R, ldr, BR, ldbr, n, theta);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

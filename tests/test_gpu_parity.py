@@ -423,3 +423,53 @@ def test_solve_plain_fp64_mode_matches_mixed_mode():
     assert np.max(np.abs(res[0][0] - res[1][0])) < 1e-10
     assert all(s["filter_matvecs_fp64"] == s["filter_matvecs"] for s in res[0][1])
     assert all(s["tensor_flops"] > 0 for s in res[1][1])
+
+
+# ---------------------------------------------------------------------------- deviation angles
+def _b_orthonormal(rng, n, k, B):
+    Z = _cgauss(rng, n, k)
+    R = np.linalg.cholesky(Z.conj().T @ B @ Z).conj().T
+    return Z @ np.linalg.inv(R)
+
+
+@pytest.mark.parametrize("n,k", [(300, 8), (700, 160)])
+def test_deviation_angles_planted(ctx, n, k):
+    """Pairwise rotations by known angles from 0.3 down to 1e-9 inside a B-orthonormal
+    basis, with the current vectors shuffled: angles and association match the oracle."""
+    rng = _rng(n + k)
+    B = _hpd(rng, n)
+    X = _b_orthonormal(rng, n, k, B)
+    phis = np.logspace(math.log10(0.3), -9, k // 2)
+    Y = X.copy()
+    for p, phi in enumerate(phis):
+        a, b = 2 * p, 2 * p + 1
+        c, s = math.cos(phi), math.sin(phi)
+        Y[:, a] = c * X[:, a] + s * np.exp(0.7j) * X[:, b]
+        Y[:, b] = -s * np.exp(-0.7j) * X[:, a] + c * X[:, b]
+    perm = rng.permutation(k)
+    Y = Y[:, perm] * np.exp(1j * rng.uniform(0, 6, k))[None, :]
+    th_o, as_o = O.deviation_angles(X, Y, B)
+    th, assoc = cb.chfsi_deviation_angles(ctx, _t(X), _t(Y), _t(B))
+    th, assoc = _np(th), _np(assoc)
+    assert list(assoc) == list(as_o)
+    assert np.all(np.abs(th - th_o) <= 1e-9 * th_o + 1e-14)
+    assert np.allclose(np.sort(th), np.sort(np.repeat(phis, 2)), rtol=1e-8, atol=1e-14)
+
+
+def test_deviation_angles_along_planted_sequence(ctx):
+    """Eigenvectors solved by the library along a planted sequence: the angles between
+    adjacent problems match the oracle's on the same vectors and shrink along the sequence
+    (the trend of Fig. 1)."""
+    seq = inputs.planted_sequence("c1", n=256, N=4, nev=10, blk=16, device="cuda")
+    As = [p.A for p in seq.problems]
+    Bs = [p.B for p in seq.problems]
+    cb.chfsi_reset_warm_state(ctx)
+    _, evecs, _ = cb.chfsi_solve_sequence(ctx, As, Bs, 10, 16, 10, 1e-10)
+    means = []
+    for l in range(1, 4):
+        th, assoc = cb.chfsi_deviation_angles(ctx, evecs[l - 1], evecs[l], Bs[l])
+        th_o, as_o = O.deviation_angles(_np(evecs[l - 1]), _np(evecs[l]), _np(Bs[l]))
+        assert list(_np(assoc)) == list(as_o)
+        assert np.max(np.abs(_np(th) - th_o)) <= 1e-8 * np.max(th_o) + 1e-13
+        means.append(float(np.mean(th_o)))
+    assert means[0] > means[1] > means[2]

@@ -337,3 +337,74 @@ def test_table3_defaults_golden():
     assert sig.parameters["deg"].default == vals["degree"]
     assert sig.parameters["tol"].default == vals["tol"]
     assert sig.parameters["lanczos_k_warm"].default == vals["lanczos_iter_min"]
+
+
+# ---------------------------------------------------------------------------- deviation angles
+def _bo_basis(rng, n, k, B):
+    """k B-orthonormal columns (B-Gram-Schmidt via Cholesky of the Gram matrix)."""
+    Z = (rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))) / np.sqrt(2)
+    G = Z.conj().T @ B @ Z
+    R = np.linalg.cholesky(G).conj().T
+    return Z @ np.linalg.inv(R)
+
+
+def test_deviation_angles_planted_rotations():
+    """Columns rotated pairwise by known angles inside a B-orthonormal basis: the angles
+    come back exactly and each vector is associated with its rotated self."""
+    rng = np.random.default_rng(31)
+    n, k = 60, 8
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    B = np.eye(n) + 0.05 * (G.conj().T @ G) / n
+    X = _bo_basis(rng, n, k, B)
+    phis = np.array([1e-1, 3e-3, 1e-5, 2e-8])
+    Y = X.copy()
+    for p, phi in enumerate(phis):
+        a, b = 2 * p, 2 * p + 1
+        c, s = math.cos(phi), math.sin(phi)
+        Y[:, a] = c * X[:, a] + s * np.exp(0.3j) * X[:, b]
+        Y[:, b] = -s * np.exp(-0.3j) * X[:, a] + c * X[:, b]
+    theta, assoc = O.deviation_angles(X, Y, B)
+    assert list(assoc) == list(range(k))
+    expect = np.repeat(phis, 2)
+    assert np.allclose(theta, expect, rtol=1e-9, atol=1e-15)
+
+
+def test_deviation_angles_permutation_and_phases():
+    """Reordered eigenvectors with arbitrary phases: zero angles, association = the
+    permutation (the one-to-one matching of Section 2.2)."""
+    rng = np.random.default_rng(32)
+    n, k = 40, 6
+    B = np.eye(n)
+    X = _bo_basis(rng, n, k, B)
+    perm = np.array([2, 0, 1, 5, 3, 4])
+    Y = X[:, perm] * np.exp(1j * rng.uniform(0, 6, k))[None, :]
+    theta, assoc = O.deviation_angles(X, Y, B)
+    # previous vector i sits at position j of Y where perm[j] == i
+    inv = np.argsort(perm)
+    assert list(assoc) == list(inv)
+    assert np.max(theta) < 1e-7
+
+
+def test_deviation_angles_match_scipy_subspace_angles():
+    """For single vectors the angle is scipy's principal angle between the spans."""
+    rng = np.random.default_rng(33)
+    n = 30
+    B = np.eye(n)
+    x = (rng.standard_normal((n, 1)) + 1j * rng.standard_normal((n, 1)))
+    y = x + 0.2 * (rng.standard_normal((n, 1)) + 1j * rng.standard_normal((n, 1)))
+    x /= np.linalg.norm(x)
+    y /= np.linalg.norm(y)
+    theta, _ = O.deviation_angles(x, y, B)
+    assert abs(theta[0] - sla.subspace_angles(x, y)[0]) < 1e-12
+
+
+def test_deviation_angles_decrease_along_planted_sequence():
+    """On the planted sequences the angles shrink with the rotation scale eps_l (the
+    trend of Fig. 1)."""
+    seq = inputs.planted_sequence("c1", n=96, N=4, nev=6, blk=8, device="cpu")
+    means = []
+    for l in range(1, 4):
+        P0, P1 = seq.problems[l - 1], seq.problems[l]
+        th, _ = O.deviation_angles(P0.X.numpy()[:, :6], P1.X.numpy()[:, :6], P1.B.numpy())
+        means.append(float(np.mean(th)))
+    assert means[0] > means[1] > means[2]

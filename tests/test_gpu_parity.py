@@ -473,3 +473,33 @@ def test_deviation_angles_along_planted_sequence(ctx):
         assert np.max(np.abs(_np(th) - th_o)) <= 1e-8 * np.max(th_o) + 1e-13
         means.append(float(np.mean(th_o)))
     assert means[0] > means[1] > means[2]
+
+
+def test_solve_n9300_mixed_precision_workload():
+    """The n = 9300 mixed-precision workload (nev 256, blk 320, degree 20) at full size, two
+    problems (cold + warm): eigenvalues against the planted spectrum, generalized residuals
+    against a lower bound of ||A||_2 (power iteration), and B-orthonormality, all on the GPU."""
+    seq = inputs.planted_sequence("c3", N=2, device="cuda", keep_vectors=False)
+    n, nev, blk = seq.n, seq.nev, seq.blk
+    As = [cb.fortran(torch.tril(p.A)) for p in seq.problems]
+    Bs = [cb.fortran(torch.tril(p.B)) for p in seq.problems]
+    with cb.Solver(n, blk) as s:
+        evals, evecs, stats = cb.chfsi_solve_sequence(s.ctx, As, Bs, nev, blk, seq.deg, seq.tol)
+    scale = max(float(np.max(np.abs(p.lam))) for p in seq.problems)
+    for ell, p in enumerate(seq.problems):
+        lam = evals[ell]
+        assert stats[ell]["converged"] == nev
+        assert np.max(np.abs(lam.numpy() - p.lam[:nev])) <= 1e-10 * scale
+        A, B, X = p.A, p.B, evecs[ell]
+        assert stats[ell]["max_resid"] <= seq.tol
+        v = torch.ones(n, 1, dtype=torch.complex128, device=A.device)
+        for _ in range(30):
+            v = A @ v
+            v = v / torch.linalg.vector_norm(v)
+        a_low = float(torch.linalg.vector_norm(A @ v))  # ||A v|| with ||v|| = 1: <= ||A||_2
+        lam_d = lam.to(A.device).to(torch.complex128)
+        R = A @ X - (B @ X) * lam_d[None, :]
+        res = torch.linalg.vector_norm(R, dim=0) / (a_low * torch.linalg.vector_norm(X, dim=0))
+        assert float(res.max()) <= 1e-10, float(res.max())
+        E = X.mH @ (B @ X) - torch.eye(nev, dtype=torch.complex128, device=A.device)
+        assert float(E.abs().max()) < 1e-10

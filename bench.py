@@ -434,6 +434,61 @@ def run_heev_case(args):
     print(json.dumps({"case": "heev", "m": m, "ms": ms, "rel_resid": resid}))
 
 
+def run_batch(args):
+    """The batched k-point workload: K independent sequences of uneven size (n_k uniform in
+    [3000, 6000], nev_k = ceil(0.04 n_k), blk_k = ceil(1.3 nev_k), degree 20), solved by a
+    batch of --workers contexts on their own streams, against the same sequences solved one
+    after another on one context.  Host wall time around each solve (both return only after
+    their streams are synchronised)."""
+    from paper_1206_3768_gb300 import binding as cb
+    from paper_1206_3768_gb300 import inputs
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    K, N = args.kpoints, args.problems or 10
+    seqs = inputs.kpoint_sequences(K=K, N=N, device=dev)
+    data = [([cb.fortran(torch.tril(p.A)) for p in q.problems],
+             [cb.fortran(torch.tril(p.B)) for p in q.problems]) for q in seqs]
+    nev = [q.nev for q in seqs]
+    blk = [q.blk for q in seqs]
+    n_max, blk_max = max(q.n for q in seqs), max(blk)
+    torch.cuda.synchronize()
+    pairs = sum(N * v for v in nev)
+    with cb.Batch(args.workers, n_max, blk_max) as batch:
+        for _ in range(max(1, args.warmup)):
+            batch.solve(data[:args.workers], nev[:args.workers], blk[:args.workers], 20, 1e-10,
+                        want_vectors=False)
+        t0 = time.perf_counter()
+        res = batch.solve(data, nev, blk, 20, 1e-10, want_vectors=False)
+        t_batch = time.perf_counter() - t0
+    conv_b = sum(int(torch.isfinite(ev).sum()) for ev, _, _ in res)
+    max_resid = max(st["max_resid"] for _, _, sts in res for st in sts)
+    with cb.Solver(n_max, blk_max) as s:
+        cb.chfsi_reset_warm_state(s.ctx)
+        cb.chfsi_solve_sequence(s.ctx, data[0][0], data[0][1], nev[0], blk[0], 20, 1e-10,
+                                want_vectors=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv_s = 0
+        for (As, Bs), v, b in zip(data, nev, blk):
+            cb.chfsi_reset_warm_state(s.ctx)
+            ev, _, _ = cb.chfsi_solve_sequence(s.ctx, As, Bs, v, b, 20, 1e-10, want_vectors=False)
+            conv_s += int(torch.isfinite(ev).sum())
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": "batched k-point sequences, converged eigenpairs/s", "value": conv_b / t_batch,
+        "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+        "sequential": {"value": conv_s / t_seq, "seconds": t_seq},
+        "speedup_vs_sequential": (conv_b / t_batch) / (conv_s / t_seq), "seconds": t_batch,
+        "pairs": pairs, "max_resid": max_resid,
+        "config": {"workload": f"c4: K={K} k-point sequences, N={N} problems each, n_k in "
+                               f"[3000, 6000] ({min(q.n for q in seqs)}..{n_max}), nev_k = "
+                               f"ceil(0.04 n_k), blk_k = ceil(1.3 nev_k), deg 20, first problem "
+                               f"cold, rest warm", "workers": args.workers},
+    }), flush=True)
+
+
 def run_kernel_case(args):
     """One Chebyshev filter call (deg launches of the filter GEMM) through the C ABI on a
     seeded n x n Hermitian matrix and n x m block: the small case used for kernel profiles."""
@@ -481,9 +536,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-angles", action="store_true")
-    ap.add_argument("--workload", choices=["c2", "c3"], default=WORKLOAD,
+    ap.add_argument("--kpoints", type=int, default=32)
+    ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--workload", choices=["c2", "c3", "c4"], default=WORKLOAD,
                     help="c2: n=2600 adaptive degree (the headline); c3: n=9300, nev=256, blk=320, "
-                         "deg 20 (the mixed-precision workload; use --problems to bound it)")
+                         "deg 20 (the mixed-precision workload; use --problems to bound it); c4: "
+                         "--kpoints sequences of uneven size solved by a batch of --workers "
+                         "contexts against one context (a separate line, not the headline)")
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--problems", type=int, default=None,
                     help="solve only the first N problems of the sequence (profiling runs)")
@@ -494,7 +553,9 @@ def main():
     ap.add_argument("--case-reps", type=int, default=1)
     ap.add_argument("--case-slices", type=int, default=0)
     args = ap.parse_args()
-    if args.kernel_case == "heev":
+    if args.workload == "c4" and args.impl == "ours" and not args.kernel_case:
+        run_batch(args)
+    elif args.kernel_case == "heev":
         run_heev_case(args)
     elif args.kernel_case:
         run_kernel_case(args)

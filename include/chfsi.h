@@ -243,6 +243,33 @@ int chfsi_zgemm(chfsi_ctx* ctx, char opa, char opb, int32_t M, int32_t N, int32_
                 double alpha, const chfsi_z* A, int64_t lda, const chfsi_z* B, int64_t ldb,
                 double beta, chfsi_z* C, int64_t ldc);
 
+/* ---------------------------------------------------------------- batched sequences */
+/* Independent sequences solved concurrently on one GPU: the k-points of one
+ * self-consistent cycle each give their own sequence of pencils (Section 1), with uneven
+ * sizes.  A batch owns `workers` contexts (each with its own stream and the workspace of
+ * chfsi_create(n_max, blk_max)) and solves with one host thread per context; whole
+ * sequences are handed to the workers in order, so one sequence's host synchronisations
+ * and latency-bound kernels overlap another's products.  opts: as chfsi_create, except
+ * cuda_stream, which is ignored.  Errors of create: as chfsi_create. */
+typedef struct chfsi_batch chfsi_batch;
+int chfsi_batch_create(chfsi_batch** out, int32_t workers, int64_t n_max, int32_t blk_max,
+                       const chfsi_opts* opts);
+void chfsi_batch_destroy(chfsi_batch* batch);
+const char* chfsi_batch_last_error(const chfsi_batch* batch);
+
+/* K sequences of N problems each; sequence s has size n[s], nev[s], blk[s] (each within
+ * the batch's n_max, blk_max), its problems at A[s*N + l], B[s*N + l] (lower triangles,
+ * leading dimension ld[s], host or device as in chfsi_solve_next), outputs evals[s]
+ * (N x nev[s], host), evecs[s*N + l] (n[s] x nev[s], or evecs == NULL) and st[s*N + l] (or
+ * st == NULL).  Every sequence starts cold (each worker resets its warm state) and
+ * problem l of a sequence is warm-started from problem l-1 (Section 4.1).  deg, tol as in
+ * chfsi_solve_next.  Returns the first failing sequence's status (message in
+ * chfsi_batch_last_error); sequences not yet started are then skipped. */
+int chfsi_batch_solve(chfsi_batch* batch, int32_t K, int32_t N, const int64_t* n, const int32_t* nev,
+                      const int32_t* blk, int32_t deg, double tol, const chfsi_z* const* A,
+                      const chfsi_z* const* B, const int64_t* ld, double* const* evals,
+                      chfsi_z* const* evecs, chfsi_stats* st);
+
 #ifdef __cplusplus
 }
 #endif

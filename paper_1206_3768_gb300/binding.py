@@ -80,6 +80,11 @@ _SIGS = {
     "chfsi_degrees": (c_int32, [_P, c_int32, _P, _P, c_double, c_double, c_double, c_int32,
                                 c_int32, c_int32, _P]),
     "chfsi_heev": (c_int32, [_P, c_int32, _P, c_int64, _P, _P, c_int64]),
+    "chfsi_batch_create": (c_int32, [POINTER(c_void_p), c_int32, c_int64, c_int32, POINTER(chfsi_opts)]),
+    "chfsi_batch_destroy": (None, [_P]),
+    "chfsi_batch_last_error": (c_char_p, [_P]),
+    "chfsi_batch_solve": (c_int32, [_P, c_int32, c_int32, _P, _P, _P, c_int32, c_double, _P, _P, _P, _P, _P,
+                                    _P]),
     "chfsi_deviation_angles": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64, _P, c_int64,
                                          _P, _P]),
     "chfsi_heev_noalloc": (c_int32, [c_int32, _P, c_int64, _P, _P, c_int64, _P]),
@@ -379,6 +384,104 @@ def chfsi_zgemm(ctx, opa: str, opb: str, alpha: float, A: torch.Tensor, B: torch
     _check(ctx, load().chfsi_zgemm(ctx, opa.encode(), opb.encode(), M, N, K, alpha, _ptr(Af),
                                    _ld(Af), _ptr(Bf), _ld(Bf), beta, _ptr(C), _ld(C)))
     return C
+
+
+def chfsi_batch_create(workers: int, n_max: int, blk_max: int, **kw):
+    o = default_opts(**kw)
+    ptr = ctypes.c_void_p()
+    rc = load().chfsi_batch_create(ctypes.byref(ptr), int(workers), int(n_max), int(blk_max),
+                                   ctypes.byref(o))
+    if rc != CHFSI_OK:
+        raise ChfsiError(rc, "chfsi_batch_create failed")
+    return ptr
+
+
+def chfsi_batch_destroy(batch):
+    load().chfsi_batch_destroy(batch)
+
+
+def chfsi_batch_last_error(batch) -> str:
+    return load().chfsi_batch_last_error(batch).decode()
+
+
+def chfsi_batch_solve(batch, seqs, nev, blk, deg: int, tol: float = 1e-10, want_vectors: bool = True):
+    """K independent sequences on a batch.  seqs: list of (As, Bs) per sequence (N problems
+    each, lists of n_s x n_s tensors, one device and leading dimension per sequence); nev,
+    blk: lists.  Returns a list of (evals [N, nev_s], evecs list or None, stats dicts)."""
+    return Batch.solve_on(batch, seqs, nev, blk, deg, tol, want_vectors)
+
+
+class Batch:
+    """Several contexts (own streams, one host worker thread each) solving independent
+    sequences of uneven sizes concurrently (chfsi_batch_*)."""
+
+    def __init__(self, workers: int, n_max: int, blk_max: int, **kw):
+        self.ptr = chfsi_batch_create(workers, n_max, blk_max, **kw)
+
+    def solve(self, seqs, nev, blk, deg: int, tol: float = 1e-10, want_vectors: bool = True):
+        return Batch.solve_on(self.ptr, seqs, nev, blk, deg, tol, want_vectors)
+
+    @staticmethod
+    def solve_on(ptr, seqs, nev, blk, deg: int, tol: float = 1e-10, want_vectors: bool = True):
+        K = len(seqs)
+        N = len(seqs[0][0])
+        if any(len(a) != N or len(b) != N for a, b in seqs):
+            raise ValueError("every sequence needs the same number of problems")
+        keep = []
+        n_arr = (c_int64 * K)()
+        ld_arr = (c_int64 * K)()
+        Ap = (c_void_p * (K * N))()
+        Bp = (c_void_p * (K * N))()
+        Ev = (c_void_p * K)()
+        Xp = (c_void_p * (K * N))() if want_vectors else None
+        out = []
+        for s_i, (As, Bs) in enumerate(seqs):
+            Af = [fortran(a) for a in As]
+            Bf = [fortran(b) for b in Bs]
+            ld = _ld(Af[0])
+            if any(_ld(x) != ld for x in Af + Bf):
+                raise ValueError("matrices of one sequence must share one leading dimension")
+            n = Af[0].shape[0]
+            n_arr[s_i], ld_arr[s_i] = n, ld
+            ev = torch.empty((N, nev[s_i]), dtype=torch.float64, device="cpu")
+            Ev[s_i] = ev.data_ptr()
+            X = [fortran_empty(n, nev[s_i], Af[0].device) for _ in range(N)] if want_vectors else None
+            for l in range(N):
+                Ap[s_i * N + l] = Af[l].data_ptr()
+                Bp[s_i * N + l] = Bf[l].data_ptr()
+                if X is not None:
+                    Xp[s_i * N + l] = X[l].data_ptr()
+            keep += [Af, Bf]
+            out.append((ev, X))
+        nev_arr = (c_int32 * K)(*nev)
+        blk_arr = (c_int32 * K)(*blk)
+        sts = (chfsi_stats * (K * N))()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()  # inputs written on torch's streams; the batch has its own
+        lib = load()
+        rc = lib.chfsi_batch_solve(ptr, K, N, n_arr, nev_arr, blk_arr, deg, tol, Ap, Bp, ld_arr, Ev, Xp,
+                                   sts)
+        if rc != CHFSI_OK:
+            raise ChfsiError(rc, lib.chfsi_batch_last_error(ptr).decode())
+        return [(ev, X, [sts[s_i * N + l].as_dict() for l in range(N)])
+                for s_i, (ev, X) in enumerate(out)]
+
+    def close(self):
+        if self.ptr:
+            chfsi_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

@@ -44,6 +44,9 @@ CONFIGS = {
     # n=9300 mixed-precision workload, generated like c1.
     "c3": dict(config_id=3, n=9300, nev=256, blk=320, deg=20, deg_min=20, deg_max=20, N=20,
                spectrum="uniform_cluster", overlap="mild", tol=1e-10),
+    # one k-point of the batched workload (kpoint_sequences draws n per k-point), like c1.
+    "c4": dict(config_id=4, n=4500, nev=180, blk=234, deg=20, deg_min=20, deg_max=20, N=10,
+               spectrum="uniform_cluster", overlap="mild", tol=1e-10),
 }
 
 
@@ -207,3 +210,19 @@ def gaussian_block(n: int, m: int, seed: int) -> torch.Tensor:
     """Seeded complex Gaussian n x m start block (the caller-supplied V0 of a cold start)."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_BASE, 7, seed])))
     return torch.from_numpy(complex_gaussian(rng, (n, m)))
+
+
+def kpoint_sequences(K: int = 32, N: int = 10, n_range=(3000, 6000), device="cpu",
+                     keep_vectors: bool = False, seed: int = 0) -> list:
+    """K independent k-point sequences of uneven size (the batched workload): n_k drawn
+    uniformly from n_range (seeded), nev_k = ceil(0.04 n_k), blk_k = ceil(1.3 nev_k),
+    each generated like "c4" with its own seed offset."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_BASE, 4, seed])))
+    ns = rng.integers(int(n_range[0]), int(n_range[1]) + 1, size=K)
+    out = []
+    for k, n in enumerate(ns):
+        nev = int(math.ceil(0.04 * int(n)))
+        blk = int(math.ceil(1.3 * nev))
+        out.append(planted_sequence("c4", n=int(n), N=N, nev=nev, blk=blk, device=device,
+                                    keep_vectors=keep_vectors, seed_offset=k + 1))
+    return out

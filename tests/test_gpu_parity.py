@@ -503,3 +503,25 @@ def test_solve_n9300_mixed_precision_workload():
         assert float(res.max()) <= 1e-10, float(res.max())
         E = X.mH @ (B @ X) - torch.eye(nev, dtype=torch.complex128, device=A.device)
         assert float(E.abs().max()) < 1e-10
+
+
+def test_batch_uneven_sequences_match_sequential():
+    """Five k-point sequences of uneven size solved by a batch of three workers: every
+    eigenvalue equals the one-context sequential solve's and the planted spectrum."""
+    seqs = inputs.kpoint_sequences(K=5, N=2, n_range=(200, 460), device="cuda")
+    data = [([torch.tril(p.A) for p in q.problems], [torch.tril(p.B) for p in q.problems]) for q in seqs]
+    nev = [q.nev for q in seqs]
+    blk = [q.blk for q in seqs]
+    n_max = max(q.n for q in seqs)
+    with cb.Batch(3, n_max, max(blk)) as batch:
+        res = batch.solve(data, nev, blk, 20, 1e-10)
+    with cb.Solver(n_max, max(blk)) as s:
+        for q, (As, Bs), (ev_b, X_b, st_b) in zip(seqs, data, res):
+            cb.chfsi_reset_warm_state(s.ctx)
+            ev_s, _, _ = cb.chfsi_solve_sequence(s.ctx, As, Bs, q.nev, q.blk, 20, 1e-10)
+            scale = max(float(np.max(np.abs(p.lam))) for p in q.problems)
+            assert np.max(np.abs(ev_b.numpy() - ev_s.numpy())) <= 1e-12 * scale
+            for ell, p in enumerate(q.problems):
+                assert np.max(np.abs(ev_b[ell].numpy() - p.lam[:q.nev])) <= 1e-10 * scale
+                assert st_b[ell]["converged"] == q.nev
+                assert st_b[ell]["max_resid"] <= 1e-10

@@ -145,7 +145,9 @@ int chfsi_reduce(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const
 /* k-step Lanczos with full re-orthogonalisation on the Hermitian H (full storage),
  * starting from v0 (device, n) or, if v0 is NULL, from the SplitMix64 start vector of
  * the context seed (Algorithm 1, first step).  upper = max eig(T_k) + |beta_k|,
- * theta_min = min eig(T_k), theta_max = max eig(T_k) (host doubles). */
+ * theta_min = min eig(T_k), theta_max = max eig(T_k) (host doubles).  With precision 1 the
+ * products H v use FP32 multiply-adds on the FP64 data (relative error ~1e-7, ample for a
+ * spectral bound); with precision 0 FP64. */
 int chfsi_lanczos(chfsi_ctx* ctx, int64_t n, const chfsi_z* H, int64_t ldh, int32_t k,
                   const chfsi_z* v0, double* upper, double* theta_min, double* theta_max);
 

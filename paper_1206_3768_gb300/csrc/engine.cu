@@ -266,7 +266,9 @@ int reduce_to_standard(chfsi_ctx* ctx, const zd* Af, int64_t lda, const zd* Linv
   return CHFSI_OK;
 }
 
-// k-step Lanczos with full re-orthogonalisation (two classical Gram-Schmidt passes).
+// k-step Lanczos with full re-orthogonalisation (two classical Gram-Schmidt passes).  In
+// mixed precision the products H v use FP32 multiply-adds on the FP64 data (a bound of the
+// spectrum and a norm estimate need no more); the vectors and T_k stay FP64.
 // v0: device start vector or nullptr (SplitMix64 with `seed`).  out3 (device):
 // [theta_min, theta_max, theta_max + |beta_k|].
 int lanczos_run(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int k, const zd* v0,
@@ -283,7 +285,7 @@ int lanczos_run(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int k, const zd
   CK(vec_norm(ws.lw, n, nrm, ctx->stream));
   CK(vec_scale_into(ws.lw, n, nrm, V, ctx->stream));
   for (int j = 0; j < k; ++j) {
-    CK(hemv_rows(H, ldh, V + (int64_t)j * ldv, ws.lw, n, ctx->stream));
+    CK(hemv_rows(H, ldh, V + (int64_t)j * ldv, ws.lw, n, ctx->stream, ctx->opts.precision == 1));
     CK(block_dots(V, ldv, j, ws.lw, n, ws.lc, ctx->stream));
     CK(block_update(V, ldv, j, ws.lc, ws.lw, n, ctx->stream));
     CK(block_dots(V, ldv, j, ws.lw, n, ws.lc + (ws.lanczos_kmax + 1), ctx->stream));

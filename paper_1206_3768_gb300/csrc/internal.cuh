@@ -131,7 +131,8 @@ cudaError_t lock_scan(const double* r, int m, double tau, int max_lock, int* nlo
 cudaError_t fill_nan(double* x, int m, cudaStream_t s);
 
 // Lanczos pieces
-cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s);
+// w = H v for Hermitian H (row i read as column i); f32: FP32 multiply-adds (bound estimates).
+cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s, bool f32 = false);
 cudaError_t block_dots(const zd* V, int64_t ldv, int j, const zd* w, int n, zd* c,
                        cudaStream_t s);
 cudaError_t block_update(const zd* V, int64_t ldv, int j, const zd* c, zd* w, int n,

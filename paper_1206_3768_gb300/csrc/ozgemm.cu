@@ -258,7 +258,7 @@ __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int N
 
 // ============================================================================ tcgen05 path
 // The same digit products on the 5th-generation tensor cores: TMA (128-byte swizzle) stages
-// a 128 x 64 bf16 tile of A and a 144 x 64 tile of B in shared memory, one elected thread
+// a 128 x 64 bf16 tile of A and an (up to) 144 x 64 tile of B in shared memory, one elected thread
 // issues tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor memory, N up to
 // 144 so that a 130-column block is one tile and the large operand is streamed once), and
 // twelve drain warps fold each exact 960-term chunk into double-float sums.  Tensor memory
@@ -270,13 +270,15 @@ __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int N
 // each thread may hold 128 registers.  Every wait on an mbarrier is bounded; a
 // wait that runs out sets DEV_TIMEOUT and the CTA unwinds (waiting, again bounded, for its
 // own copies and MMAs) before freeing tensor memory.
-constexpr int TC_BM = 128, TC_BN = 144, TC_BK = 64, TC_STAGES = 6, TC_THREADS = 448;
+constexpr int TC_BM = 128, TC_BN = 144, TC_BK = 64, TC_THREADS = 448;
+// The ring holds as many stages as fit: 6 for a 144-row B box, up to TC_MAX_STAGES for narrow
+// blocks, whose smaller B boxes leave room for more of the (dominant) A stream in flight.
+constexpr int TC_MAX_STAGES = 12;
+constexpr int TC_SMEM_BUDGET = 227 * 1024 - 1024 - 512;  // dynamic shared memory for the ring
 constexpr int TC_DRAIN_THREADS = TC_THREADS - 64;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per stage
-constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;       // 18 KB per stage
-constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // a multiple of 1024 (swizzle atoms)
 constexpr int TC_ACC1 = 160, TC_HI = 320;           // tensor-memory column offsets
-static_assert(TC_STAGE_BYTES % 1024 == 0, "stage buffers must stay 1024-byte aligned");
+static_assert((16 * TC_BK * 2) % 1024 == 0, "B stages (16-row multiples) stay 1024-byte aligned");
 static_assert(TC_HI + TC_BN <= 512 && TC_ACC1 + TC_BN <= TC_HI, "tensor-memory layout");
 constexpr long kMbarSpinLimit = 1L << 26;
 
@@ -284,6 +286,7 @@ struct TcParams {
   int a_lower, c_lower;                      // as in OzParams
   int nkb, tiles_m, splits, Mp, Np, n_real;  // n_real: columns of B^ that hold data
   int b_box_rows;                            // rows of the B box (<= TC_BN, multiple of 16)
+  int stages;                                // TMA ring depth (<= TC_MAX_STAGES)
   OzPairs pairs;
   double* part;
   int* status;
@@ -386,10 +389,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ unsigned char tc_smem_raw[];
   const uintptr_t base = (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023;
   unsigned char* sA = reinterpret_cast<unsigned char*>(base);
-  unsigned char* sB = sA + TC_STAGES * TC_A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_B_BYTES);
+  const int NS = p.stages, b_stage = p.b_box_rows * TC_BK * 2;  // B stage bytes: a multiple of 2048
+  unsigned char* sB = sA + NS * TC_A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + NS * b_stage);
   // bars: full[STAGES], empty[STAGES], accf[2], acce[2], done[1]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 5);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -406,11 +410,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int kb_lo = min(nkb, (int)blockIdx.y * per), kb_hi = min(nkb, kb_lo + per);
 
   const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * TC_STAGES;
-  const uint32_t accf0 = empty0 + 8 * TC_STAGES, acce0 = accf0 + 16, done_bar = acce0 + 16;
+  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NS;
+  const uint32_t accf0 = empty0 + 8 * NS, acce0 = accf0 + 16, done_bar = acce0 + 16;
 
   if (tid == 0) {
-    for (int i = 0; i < TC_STAGES; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(full0 + 8 * i, 1);
       mbar_init(empty0 + 8 * i, 1);
     }
@@ -434,32 +438,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int i = 0;
+      // ring position kept incrementally (no division on this single-thread issue path)
+      int i = 0, stage = 0;
+      uint32_t phase = 0;
       bool stop = false;
       for (int k0 = kb_lo; k0 < kb_hi && !stop; k0 += OZ_CHUNK_KB) {
         const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
         for (int pr = 0; pr < p.pairs.n && !stop; ++pr) {
+          const int arow = p.pairs.s[pr] * p.Mp + m0, brow = p.pairs.t[pr] * p.Np + n0;
           for (int kb = k0; kb < k1; ++kb, ++i) {
-            const int stage = i % TC_STAGES;
-            if (i >= TC_STAGES &&
-                !mbar_wait(empty0 + 8 * stage, ((i / TC_STAGES) & 1) ^ 1, abort_flag, p.status)) {
+            const uint32_t fb = full0 + 8 * stage;
+            if (i >= NS && !mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status)) {
               stop = true;
               break;
             }
-            mbar_expect_tx(full0 + 8 * stage, TC_A_BYTES + p.b_box_rows * TC_BK * 2);
-            tma_load_2d(sA_u + stage * TC_A_BYTES, &tmA, kb * TC_BK, p.pairs.s[pr] * p.Mp + m0,
-                        full0 + 8 * stage);
-            tma_load_2d(sB_u + stage * TC_B_BYTES, &tmB, kb * TC_BK, p.pairs.t[pr] * p.Np + n0,
-                        full0 + 8 * stage);
+            mbar_expect_tx(fb, TC_A_BYTES + b_stage);
+            tma_load_2d(sA_u + stage * TC_A_BYTES, &tmA, kb * TC_BK, arow, fb);
+            tma_load_2d(sB_u + stage * b_stage, &tmB, kb * TC_BK, brow, fb);
+            if (++stage == NS) {
+              stage = 0;
+              phase ^= 1;
+            }
           }
         }
       }
       // on abort: let the copies already issued (stages i - STAGES .. i - 1) land before the
       // CTA can exit
       if (*abort_flag) {
-        for (int j = max(0, i - TC_STAGES); j < i; ++j) {
+        for (int j = max(0, i - NS); j < i; ++j) {
           long it = 0;
-          while (!mbar_try(full0 + 8 * (j % TC_STAGES), (j / TC_STAGES) & 1) && ++it < kMbarSpinLimit) {}
+          while (!mbar_try(full0 + 8 * (j % NS), (j / NS) & 1) && ++it < kMbarSpinLimit) {}
         }
       }
     }
@@ -467,7 +475,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(TC_BM, ncols);
-      int i = 0, chunk = 0;
+      int chunk = 0, stage = 0;
+      uint32_t phase = 0;
       bool stop = false;
       for (int k0 = kb_lo; k0 < kb_hi && !stop; k0 += OZ_CHUNK_KB) {
         const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
@@ -479,20 +488,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)((chunk & 1) * TC_ACC1);
-          for (int kb = k0; kb < k1; ++kb, ++i) {
-            const int stage = i % TC_STAGES;
-            if (!mbar_wait(full0 + 8 * stage, (i / TC_STAGES) & 1, abort_flag, p.status)) {
+          for (int kb = k0; kb < k1; ++kb) {
+            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.status)) {
               stop = true;
               break;
             }
             tc_fence_after();
-            const uint32_t a_s = sA_u + stage * TC_A_BYTES, b_s = sB_u + stage * TC_B_BYTES;
+            const uint32_t a_s = sA_u + stage * TC_A_BYTES, b_s = sB_u + stage * b_stage;
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk)
               tc_mma(d, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc,
                      (kb == k0 && kk == 0) ? 0u : 1u);
             tc_commit(empty0 + 8 * stage);
             if (kb == k1 - 1) tc_commit(accf0 + 8 * (chunk & 1));
+            if (++stage == NS) {
+              stage = 0;
+              phase ^= 1;
+            }
           }
         }
       }
@@ -942,10 +954,13 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)a.S * Mp, TC_BM) ||
         !encode_bf16_map(&mapB, b.ptr, Kp, b_rows, tp.b_box_rows))
       return cudaErrorInvalidValue;
-    const size_t smem = 1024 + (size_t)TC_STAGES * TC_STAGE_BYTES + 256;
+    const int b_stage = tp.b_box_rows * TC_BK * 2;
+    tp.stages = std::min(TC_MAX_STAGES, TC_SMEM_BUDGET / (TC_A_BYTES + b_stage));
+    const size_t smem = 1024 + (size_t)tp.stages * (TC_A_BYTES + b_stage) + 256;
     static bool tc_attr = false;
     if (!tc_attr) {
-      e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               1024 + TC_SMEM_BUDGET + 256);
       if (e != cudaSuccess) return e;
       tc_attr = true;
     }

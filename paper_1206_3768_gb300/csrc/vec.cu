@@ -280,6 +280,36 @@ __global__ void hemv_rows_kernel(const zd* H, int64_t ldh, const zd* v, zd* w, i
   }
 }
 
+// The same product with FP32 multiply-adds on the FP64 data (per-lane FP32 partial sums of
+// at most 8 terms, then FP64): relative error ~1e-7, enough for a spectral bound, and no
+// longer limited by this part's FP64 issue rate.
+__global__ void hemv_rows_f32_kernel(const zd* H, int64_t ldh, const zd* v, zd* w, int n) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (blockDim.x >> 5) * gridDim.x;
+  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+    const zd* col = H + (int64_t)i * ldh;
+    double sr = 0.0, si = 0.0;
+    for (int j0 = 0; j0 < n; j0 += 256) {
+      float fr = 0.f, fi = 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = j0 + u * 32 + lane;
+        if (j < n) {
+          const zd h = col[j], x = v[j];
+          const float hx = (float)h.x, hy = (float)h.y, xx = (float)x.x, xy = (float)x.y;
+          fr = fmaf(hx, xx, fmaf(hy, xy, fr));
+          fi = fmaf(hx, xy, fmaf(-hy, xx, fi));
+        }
+      }
+      sr += (double)fr;
+      si += (double)fi;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) w[i] = zmk(sr, si);
+  }
+}
+
 // c_l = V_l^H w for l = 0..j  (one CTA per l)
 __global__ void block_dots_kernel(const zd* V, int64_t ldv, const zd* w, int n, zd* c) {
   const int l = blockIdx.x;
@@ -558,10 +588,11 @@ cudaError_t fill_nan(double* x, int m, cudaStream_t s) {
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
-cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s) {
+cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s, bool f32) {
   const int warps_per_block = 8;
   const int blocks = std::max(1, std::min((n + warps_per_block - 1) / warps_per_block, 16 * sm_count()));
-  hemv_rows_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(H, ldh, v, w, n);
+  if (f32) hemv_rows_f32_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(H, ldh, v, w, n);
+  else hemv_rows_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(H, ldh, v, w, n);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

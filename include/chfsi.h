@@ -206,7 +206,8 @@ int chfsi_deviation_angles(chfsi_ctx* ctx, int64_t n, int32_t k, const chfsi_z* 
  * d_i = clamp(ceil(ln(r_i/tau)/ln rho_i), dmin, dmax), rho_i = |t_i| + sqrt(t_i^2-1),
  * t_i = (theta_i - c)/e; d_i = dmin when r_i <= tau, dmax when |t_i| <= 1; columns
  * i >= n_wanted take the largest degree of the first n_wanted.  theta, r device;
- * degrees: device, m int32. */
+ * degrees: device, m int32.  With a model installed by chfsi_set_degree_model the learned
+ * rate replaces ln rho_i (see below). */
 int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* r, double a,
                   double b, double tau, int32_t dmin, int32_t dmax, int32_t n_wanted,
                   int32_t* degrees);
@@ -271,6 +272,58 @@ int chfsi_batch_solve(chfsi_batch* batch, int32_t K, int32_t N, const int64_t* n
                       const int32_t* blk, int32_t deg, double tol, const chfsi_z* const* A,
                       const chfsi_z* const* B, const int64_t* ld, double* const* evals,
                       chfsi_z* const* evecs, chfsi_stats* st);
+
+/* ---------------------------------------------------------------- learned degree model */
+/* Not in the paper: a learned form of the adaptive per-vector degree (the degree / block
+ * size trade-off of Section 3).  The closed-form rule assumes a degree-d filter reduces the
+ * residual of Ritz vector i by rho_i^d, rho_i = exp(acosh|t_i|), t_i = (theta_i - c)/e.  The
+ * model predicts a correction g(x) of that rate, rate_i = ln(rho_i) exp(g(x_i)), from
+ * x = [acosh|t_i|, log10(r_i/tau), i/m, log10(max(gap_i/e, 1e-12))] (gap_i = theta_{i+1} -
+ * theta_i, e for the last column), x normalised as (x - mean) * scale, with a perceptron
+ * 4 -> 64 -> 64 -> 1 (tanh hidden units, linear output); d_i = clamp(ceil(ln(r_i/tau) /
+ * rate_i), deg_min, deg_max), g clamped to [-3, 3], the closed form wherever the result is
+ * not finite.  The solver evaluates it with FP16 weights. */
+#define CHFSI_MLP_IN 4
+#define CHFSI_MLP_HID 64
+/* trainable parameters (w1 .. b3): 4545 */
+#define CHFSI_MLP_NPARAM                                                                   \
+  (CHFSI_MLP_HID * CHFSI_MLP_IN + CHFSI_MLP_HID + CHFSI_MLP_HID * CHFSI_MLP_HID +          \
+   2 * CHFSI_MLP_HID + 1)
+typedef struct {
+  float w1[CHFSI_MLP_HID * CHFSI_MLP_IN]; /* row j: weights of hidden unit j of layer 1 */
+  float b1[CHFSI_MLP_HID];
+  float w2[CHFSI_MLP_HID * CHFSI_MLP_HID]; /* row j: weights of hidden unit j of layer 2 */
+  float b2[CHFSI_MLP_HID];
+  float w3[CHFSI_MLP_HID];
+  float b3;
+  float mean[CHFSI_MLP_IN], scale[CHFSI_MLP_IN];
+} chfsi_mlp;
+
+/* Uniform (Glorot) hidden weights from SplitMix64(seed), zero biases and output layer (the
+ * untrained model predicts g = 0, i.e. the closed form), mean 0, scale 1. */
+void chfsi_mlp_init(chfsi_mlp* model, uint64_t seed);
+/* Training: sets mean/scale from X, then `epochs` epochs of Adam (lr, minibatches of
+ * `batch`, order shuffled by SplitMix64(seed)) on L = 1/(2n) sum (g(x_k) - z_k)^2, in place
+ * on *model.  X: host, n x 4 (row-major), z: host, n.  *loss: mean loss of the last epoch. */
+int chfsi_mlp_train(chfsi_ctx* ctx, chfsi_mlp* model, const float* X, const float* z, int64_t n,
+                    int32_t epochs, int32_t batch, float lr, uint64_t seed, float* loss);
+/* dL/dparameters over all n samples (host, CHFSI_MLP_NPARAM floats in the order of chfsi_mlp's fields
+ * w1 .. b3) and L, for the given model and its mean/scale. */
+int chfsi_mlp_gradient(chfsi_ctx* ctx, const chfsi_mlp* model, const float* X, const float* z,
+                       int64_t n, float* grad, float* loss);
+/* g(x_k) for n host samples (FP32 weights). */
+int chfsi_mlp_predict(chfsi_ctx* ctx, const chfsi_mlp* model, const float* X, int64_t n, float* y);
+/* Install the model for the context's adaptive degrees (NULL: the closed form). */
+int chfsi_set_degree_model(chfsi_ctx* ctx, const chfsi_mlp* model);
+
+/* Degree log: from now on, every adaptive filter loop appends one record of
+ * CHFSI_DEGREE_LOG_FIELDS doubles per active column, [problem, loop, g, i, m, theta, r,
+ * tau, d, c, e, gap] (problem counts solves of the context, g = locked count + i), up to
+ * `capacity` records; capacity 0 stops logging and clears it. */
+#define CHFSI_DEGREE_LOG_FIELDS 12
+int chfsi_degree_log_start(chfsi_ctx* ctx, int64_t capacity);
+/* Copies up to cap records to out (host) and returns the number of records logged. */
+int64_t chfsi_degree_log_read(chfsi_ctx* ctx, double* out, int64_t cap);
 
 #ifdef __cplusplus
 }

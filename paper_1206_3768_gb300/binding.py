@@ -32,6 +32,24 @@ class ChfsiError(RuntimeError):
         self.code = code
 
 
+MLP_IN, MLP_HID = 4, 64
+MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + 2 * MLP_HID + 1  # 4545
+DEGREE_LOG_FIELDS = 12
+
+
+class chfsi_mlp(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_float * (MLP_HID * MLP_IN)), ("b1", ctypes.c_float * MLP_HID),
+                ("w2", ctypes.c_float * (MLP_HID * MLP_HID)), ("b2", ctypes.c_float * MLP_HID),
+                ("w3", ctypes.c_float * MLP_HID), ("b3", ctypes.c_float),
+                ("mean", ctypes.c_float * MLP_IN), ("scale", ctypes.c_float * MLP_IN)]
+
+    def params(self):
+        """The MLP_NPARAM trainable parameters in the order w1, b1, w2, b2, w3, b3 (numpy copy)."""
+        import numpy as np
+
+        return np.ctypeslib.as_array((ctypes.c_float * MLP_NPARAM).from_address(ctypes.addressof(self))).copy()
+
+
 class chfsi_opts(ctypes.Structure):
     _fields_ = [("deg_min", c_int32), ("deg_max", c_int32), ("max_loops", c_int32),
                 ("lanczos_k_warm", c_int32), ("lanczos_k_cold", c_int32),
@@ -80,6 +98,13 @@ _SIGS = {
     "chfsi_degrees": (c_int32, [_P, c_int32, _P, _P, c_double, c_double, c_double, c_int32,
                                 c_int32, c_int32, _P]),
     "chfsi_heev": (c_int32, [_P, c_int32, _P, c_int64, _P, _P, c_int64]),
+    "chfsi_mlp_init": (None, [_P, c_uint64]),
+    "chfsi_mlp_train": (c_int32, [_P, _P, _P, _P, c_int64, c_int32, c_int32, ctypes.c_float, c_uint64, _P]),
+    "chfsi_mlp_gradient": (c_int32, [_P, _P, _P, _P, c_int64, _P, _P]),
+    "chfsi_mlp_predict": (c_int32, [_P, _P, _P, c_int64, _P]),
+    "chfsi_set_degree_model": (c_int32, [_P, _P]),
+    "chfsi_degree_log_start": (c_int32, [_P, c_int64]),
+    "chfsi_degree_log_read": (c_int64, [_P, _P, c_int64]),
     "chfsi_batch_create": (c_int32, [POINTER(c_void_p), c_int32, c_int64, c_int32, POINTER(chfsi_opts)]),
     "chfsi_batch_destroy": (None, [_P]),
     "chfsi_batch_last_error": (c_char_p, [_P]),
@@ -384,6 +409,70 @@ def chfsi_zgemm(ctx, opa: str, opb: str, alpha: float, A: torch.Tensor, B: torch
     _check(ctx, load().chfsi_zgemm(ctx, opa.encode(), opb.encode(), M, N, K, alpha, _ptr(Af),
                                    _ld(Af), _ptr(Bf), _ld(Bf), beta, _ptr(C), _ld(C)))
     return C
+
+
+def _f32(x):
+    import numpy as np
+
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+
+
+def chfsi_mlp_init(seed: int = 12063768) -> chfsi_mlp:
+    m = chfsi_mlp()
+    load().chfsi_mlp_init(ctypes.byref(m), seed)
+    return m
+
+
+def chfsi_mlp_train(ctx, model: chfsi_mlp, X, z, epochs: int, batch: int = 256, lr: float = 1e-3,
+                    seed: int = 1) -> float:
+    """Train in place on host data X (n x 4) and targets z (n); returns the last epoch's loss."""
+    X, z = _f32(X), _f32(z)
+    loss = ctypes.c_float()
+    _check(ctx, load().chfsi_mlp_train(ctx, ctypes.byref(model), X.ctypes.data, z.ctypes.data, len(z),
+                                       epochs, batch, lr, seed, ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def chfsi_mlp_gradient(ctx, model: chfsi_mlp, X, z):
+    """(gradient of the mean squared error over all samples [MLP_NPARAM], loss)."""
+    import numpy as np
+
+    X, z = _f32(X), _f32(z)
+    g = np.empty(MLP_NPARAM, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(ctx, load().chfsi_mlp_gradient(ctx, ctypes.byref(model), X.ctypes.data, z.ctypes.data, len(z),
+                                          g.ctypes.data, ctypes.byref(loss)))
+    return g, float(loss.value)
+
+
+def chfsi_mlp_predict(ctx, model: chfsi_mlp, X):
+    import numpy as np
+
+    X = _f32(X)
+    y = np.empty(X.shape[0], dtype=np.float32)
+    _check(ctx, load().chfsi_mlp_predict(ctx, ctypes.byref(model), X.ctypes.data, X.shape[0], y.ctypes.data))
+    return y
+
+
+def chfsi_set_degree_model(ctx, model: chfsi_mlp | None):
+    _check(ctx, load().chfsi_set_degree_model(ctx, ctypes.byref(model) if model is not None else None))
+
+
+def chfsi_degree_log_start(ctx, capacity: int):
+    _check(ctx, load().chfsi_degree_log_start(ctx, capacity))
+
+
+def chfsi_degree_log_read(ctx):
+    """All logged records as an array [count, 12]: problem, loop, g, i, m, theta, r, tau, d, c,
+    e, gap."""
+    import numpy as np
+
+    lib = load()
+    cnt = lib.chfsi_degree_log_read(ctx, None, 0)
+    out = np.empty((max(cnt, 0), DEGREE_LOG_FIELDS), dtype=np.float64)
+    if cnt > 0:
+        lib.chfsi_degree_log_read(ctx, out.ctypes.data, cnt)
+    return out
 
 
 def chfsi_batch_create(workers: int, n_max: int, blk_max: int, **kw):

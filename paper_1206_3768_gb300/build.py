@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libchfsi.so")
-SOURCES = ["gemm.cu", "small.cu", "vec.cu", "engine.cu", "noalloc.cu", "ozgemm.cu", "batch.cu"]
+SOURCES = ["gemm.cu", "small.cu", "vec.cu", "engine.cu", "noalloc.cu", "ozgemm.cu", "batch.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

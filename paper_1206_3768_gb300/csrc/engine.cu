@@ -39,6 +39,12 @@ struct chfsi_ctx {
   size_t ev_used = 0;
   struct Mark { int phase; cudaEvent_t a, b; };
   std::vector<Mark> marks;
+  // learned degree model (FP16 weights on the device) and the degree log
+  __half* mlp_dev = nullptr;
+  bool mlp_on = false;
+  std::vector<double> deglog;
+  int64_t deglog_cap = 0;
+  int64_t problems_solved = 0;
 };
 
 namespace {
@@ -662,9 +668,22 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       if (adaptive) {
         if (!have_r) return set_err(ctx, CHFSI_ECUDA, "internal: residuals missing");
         CK(degrees_kernel_run(theta, resid, m, a, b_up, tau, o.deg_min, o.deg_max, nev - conv,
-                              ws.deg, ws.perm, ws.degs, ctx->stream));
+                              ws.deg, ws.perm, ws.degs, ctx->stream, ctx->mlp_on ? ctx->mlp_dev : nullptr));
         CKS(read_back(ctx, degs.data(), ws.degs, m));
         perm_dev = ws.perm;
+        if (ctx->deglog_cap > 0 && (int)th.size() == m) {
+          // degrees per column (degs holds them in descending order): read them unsorted
+          std::vector<int> dcol(m);
+          CKS(read_back(ctx, dcol.data(), ws.deg, m));
+          const double c = 0.5 * (a + b_up), e = 0.5 * (b_up - a);
+          for (int i = 0; i < m && (int64_t)ctx->deglog.size() / CHFSI_DEGREE_LOG_FIELDS < ctx->deglog_cap; ++i) {
+            const double gap = (i + 1 < m) ? th[i + 1] - th[i] : e;
+            const double rec[CHFSI_DEGREE_LOG_FIELDS] = {(double)ctx->problems_solved, (double)st.loops,
+                                                         (double)(conv + i), (double)i, (double)m, th[i],
+                                                         rr[i], tau, (double)dcol[i], c, e, gap};
+            ctx->deglog.insert(ctx->deglog.end(), rec, rec + CHFSI_DEGREE_LOG_FIELDS);
+          }
+        }
       }
       // ---- a4: filter (split-BF16 tensor-core products in mixed mode)
       int slices = 0;
@@ -816,6 +835,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   ctx->has_warm = (conv == nev);
   ctx->warm_n = n;
   ctx->warm_blk = blk;
+  ctx->problems_solved++;
   CK(cudaEventRecord(t_end, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   float tot = 0.f;
@@ -897,7 +917,7 @@ void workspace_free(Workspace& ws) {
                   ws.Xw, ws.Z, ws.G, ws.V, ws.Rt, ws.jac, ws.lv, ws.lw, ws.lV, ws.lc, ws.theta,
                   ws.theta2, ws.resid, ws.resid2, ws.lamL, ws.residL, ws.gres, ws.dscale,
                   ws.scal, ws.lal, ws.lbe, ws.deg, ws.perm, ws.degs, ws.flag, ws.ilist,
-                  ws.status, ws.status + 1, ws.barrier, ws.splitk};
+                  ws.status, ws.shiftflag, ws.barrier, ws.splitk};
   for (void* p : ptrs)
     if (p) debug_check(cudaFree(p), "cudaFree");
   oz_free(ws.oz);
@@ -965,6 +985,7 @@ void chfsi_destroy(chfsi_ctx* ctx) {
   debug_check(cudaSetDevice(ctx->ws.dev), "cudaSetDevice");
   if (ctx->stream) debug_check(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   for (auto e : ctx->ev_pool) debug_check(cudaEventDestroy(e), "cudaEventDestroy");
+  if (ctx->mlp_dev) debug_check(cudaFree(ctx->mlp_dev), "cudaFree");
   workspace_free(ctx->ws);
   release_stream(ctx);
   delete ctx;
@@ -1191,9 +1212,66 @@ int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* 
   if (m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "m > blk_max");
   cudaSetDevice(ctx->ws.dev);
   CK(degrees_kernel_run(theta, r, m, a, b, tau, dmin, dmax, n_wanted, degrees, ctx->ws.perm,
-                        ctx->ws.degs, ctx->stream));
+                        ctx->ws.degs, ctx->stream, ctx->mlp_on ? ctx->mlp_dev : nullptr));
   CK(cudaStreamSynchronize(ctx->stream));
   return CHFSI_OK;
+}
+
+int chfsi_mlp_train(chfsi_ctx* ctx, chfsi_mlp* model, const float* X, const float* z, int64_t n,
+                    int32_t epochs, int32_t batch, float lr, uint64_t seed, float* loss) {
+  entry_guard("chfsi_mlp_train");
+  if (!ctx || !model || !X || !z || n <= 0 || n > (int64_t)1 << 30 || epochs < 0 || batch < 1 || !(lr > 0.f))
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  cudaSetDevice(ctx->ws.dev);
+  CK(mlp_train(model, X, z, n, epochs, batch, lr, seed, loss, ctx->stream));
+  return CHFSI_OK;
+}
+
+int chfsi_mlp_gradient(chfsi_ctx* ctx, const chfsi_mlp* model, const float* X, const float* z,
+                       int64_t n, float* grad, float* loss) {
+  entry_guard("chfsi_mlp_gradient");
+  if (!ctx || !model || !X || !z || !grad || !loss || n <= 0 || n > (int64_t)1 << 30)
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  cudaSetDevice(ctx->ws.dev);
+  CK(mlp_gradient(model, X, z, n, grad, loss, ctx->stream));
+  return CHFSI_OK;
+}
+
+int chfsi_mlp_predict(chfsi_ctx* ctx, const chfsi_mlp* model, const float* X, int64_t n, float* y) {
+  entry_guard("chfsi_mlp_predict");
+  if (!ctx || !model || !X || !y || n <= 0 || n > (int64_t)1 << 30) return set_err(ctx, CHFSI_EINVAL, "bad args");
+  cudaSetDevice(ctx->ws.dev);
+  CK(mlp_predict(model, X, n, y, ctx->stream));
+  return CHFSI_OK;
+}
+
+int chfsi_set_degree_model(chfsi_ctx* ctx, const chfsi_mlp* model) {
+  entry_guard("chfsi_set_degree_model");
+  if (!ctx) return CHFSI_EINVAL;
+  cudaSetDevice(ctx->ws.dev);
+  if (!model) {
+    ctx->mlp_on = false;
+    return CHFSI_OK;
+  }
+  if (!ctx->mlp_dev) CK(cudaMalloc((void**)&ctx->mlp_dev, sizeof(__half) * (mlp_param_count() + 2 * CHFSI_MLP_IN)));
+  CK(mlp_to_half(model, ctx->mlp_dev, ctx->stream));
+  ctx->mlp_on = true;
+  return CHFSI_OK;
+}
+
+int chfsi_degree_log_start(chfsi_ctx* ctx, int64_t capacity) {
+  if (!ctx || capacity < 0) return CHFSI_EINVAL;
+  ctx->deglog.clear();
+  ctx->deglog_cap = capacity;
+  return CHFSI_OK;
+}
+
+int64_t chfsi_degree_log_read(chfsi_ctx* ctx, double* out, int64_t cap) {
+  if (!ctx) return -1;
+  const int64_t cnt = (int64_t)ctx->deglog.size() / CHFSI_DEGREE_LOG_FIELDS;
+  if (out && cap > 0)
+    std::memcpy(out, ctx->deglog.data(), sizeof(double) * CHFSI_DEGREE_LOG_FIELDS * std::min(cap, cnt));
+  return cnt;
 }
 
 int chfsi_deviation_angles(chfsi_ctx* ctx, int64_t n, int32_t k, const chfsi_z* X_prev, int64_t ldp,

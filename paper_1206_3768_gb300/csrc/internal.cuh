@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <string>
 
+#include <cuda_fp16.h>
+
 #include "chfsi.h"
 
 typedef double2 zd;  // complex double: x = real part, y = imaginary part
@@ -123,9 +125,20 @@ cudaError_t generalized_residuals(const zd* AX, int64_t ldax, const zd* BX, int6
 cudaError_t splitmix_start_vector(zd* v, int n, uint64_t seed, cudaStream_t s);
 cudaError_t splitmix_gaussian_block(zd* Y, int64_t ldy, int n, int m, uint64_t seed,
                                     cudaStream_t s);
+// mlp: FP16 weights of a learned degree model (chfsi_mlp order, then mean and scale), or
+// nullptr for the closed-form rule.
 cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, double a, double b,
                                double tau, int dmin, int dmax, int n_wanted, int* deg,
-                               int* perm_desc, int* deg_sorted, cudaStream_t s);
+                               int* perm_desc, int* deg_sorted, cudaStream_t s,
+                               const __half* mlp = nullptr);
+// learned degree model (mlp.cu)
+int mlp_param_count();
+cudaError_t mlp_to_half(const chfsi_mlp* m, __half* dst_dev, cudaStream_t s);
+cudaError_t mlp_train(chfsi_mlp* m, const float* X, const float* z, int64_t n, int epochs, int batch,
+                      float lr, uint64_t seed, float* loss_out, cudaStream_t s);
+cudaError_t mlp_gradient(const chfsi_mlp* m, const float* X, const float* z, int64_t n, float* grad,
+                         float* loss_out, cudaStream_t s);
+cudaError_t mlp_predict(const chfsi_mlp* m, const float* X, int64_t n, float* y, cudaStream_t s);
 cudaError_t lock_scan(const double* r, int m, double tau, int max_lock, int* nlock,
                       cudaStream_t s);
 cudaError_t fill_nan(double* x, int m, cudaStream_t s);

@@ -235,7 +235,6 @@ __global__ void __launch_bounds__(QR_THREADS)
   }
   if (tid == 0) atomicAdd(flags + 1, 1);
   __syncthreads();
-  const float shifts[4] = {0.f, 1e-5f, 1e-4f, 1e-3f};
   int attempt = 0;
   for (; attempt < 4; ++attempt) {
     for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
@@ -244,7 +243,8 @@ __global__ void __launch_bounds__(QR_THREADS)
       const zd g = G[i + (int64_t)j * ldg];
       const double sc = dscale[i] * dscale[j];
       float2 v = make_float2((float)(g.x * sc), (float)(g.y * sc));
-      if (i == j) v = make_float2(v.x + shifts[attempt], 0.f);
+      const float shift = attempt == 0 ? 0.f : (attempt == 1 ? 1e-5f : (attempt == 2 ? 1e-4f : 1e-3f));
+      if (i == j) v = make_float2(v.x + shift, 0.f);
       A[i + (int64_t)j * m] = v;
     }
     if (tid == 0) fail = -1;

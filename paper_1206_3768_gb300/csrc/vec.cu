@@ -206,9 +206,33 @@ __global__ void gaussian_block_kernel(zd* Y, int64_t ldy, int n, int m, unsigned
 }
 
 // ---------------------------------------------------------------- degrees and locking
+// g(x) of the learned degree model (FP16 weights in the order of chfsi_mlp, then mean and
+// scale), FP32 arithmetic.
+__device__ float degree_mlp(const __half* W, const float* x) {
+  constexpr int IN = CHFSI_MLP_IN, HID = CHFSI_MLP_HID;
+  const __half *w1 = W, *b1 = w1 + HID * IN, *w2 = b1 + HID, *b2 = w2 + HID * HID, *w3 = b2 + HID,
+               *b3 = w3 + HID, *mean = b3 + 1, *scale = mean + IN;
+  float xh[IN], h1[HID];
+#pragma unroll
+  for (int k = 0; k < IN; ++k) xh[k] = (x[k] - __half2float(mean[k])) * __half2float(scale[k]);
+  for (int j = 0; j < HID; ++j) {
+    float acc = __half2float(b1[j]);
+#pragma unroll
+    for (int k = 0; k < IN; ++k) acc += __half2float(w1[j * IN + k]) * xh[k];
+    h1[j] = tanhf(acc);
+  }
+  float y = __half2float(b3[0]);
+  for (int j = 0; j < HID; ++j) {
+    float acc = __half2float(b2[j]);
+    for (int k = 0; k < HID; ++k) acc += __half2float(w2[j * HID + k]) * h1[k];
+    y += __half2float(w3[j]) * tanhf(acc);
+  }
+  return y;
+}
+
 __global__ void degrees_kernel(const double* theta, const double* r, int m, double a, double b,
                                double tau, int dmin, int dmax, int n_wanted, int* deg, int* perm,
-                               int* degs) {
+                               int* degs, const __half* mlp) {
   extern __shared__ int sd[];
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -220,7 +244,16 @@ __global__ void degrees_kernel(const double* theta, const double* r, int m, doub
       const double t = fabs((theta[i] - c) / e);
       if (t > 1.0) {
         const double rho = t + sqrt(t * t - 1.0);
-        const double need = log(ri / tau) / log(rho);
+        const double lrho = log(rho);
+        double need = log(ri / tau) / lrho;
+        if (mlp) {
+          const double gap = (i + 1 < m) ? theta[i + 1] - theta[i] : e;
+          const float x[CHFSI_MLP_IN] = {(float)lrho, (float)log10(ri / tau), (float)i / (float)m,
+                                         (float)log10(fmax(gap / e, 1e-12))};
+          const float g = fminf(3.f, fmaxf(-3.f, degree_mlp(mlp, x)));
+          const double learned = log(ri / tau) / (lrho * exp((double)g));
+          if (isfinite(learned)) need = learned;
+        }
         if (isfinite(need) && need < (double)dmax) d = min(dmax, max(dmin, (int)ceil(need)));
       }
     }
@@ -570,10 +603,10 @@ cudaError_t splitmix_gaussian_block(zd* Y, int64_t ldy, int n, int m, uint64_t s
 }
 cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, double a, double b,
                                double tau, int dmin, int dmax, int n_wanted, int* deg,
-                               int* perm_desc, int* deg_sorted, cudaStream_t s) {
+                               int* perm_desc, int* deg_sorted, cudaStream_t s, const __half* mlp) {
   if (m <= 0) return cudaSuccess;
-  degrees_kernel<<<1, 1024, m * sizeof(int), s>>>(theta, r, m, a, b, tau, dmin, dmax, n_wanted,
-                                                  deg, perm_desc, deg_sorted);
+  degrees_kernel<<<1, 256, m * sizeof(int), s>>>(theta, r, m, a, b, tau, dmin, dmax, n_wanted,
+                                                 deg, perm_desc, deg_sorted, mlp);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -489,6 +489,75 @@ def run_batch(args):
     }), flush=True)
 
 
+def run_degree_model(args):
+    """The learned per-vector degree against the closed-form rule (degree range [4, 40]):
+    the model is trained on degree logs of independent training sequences of the same shape
+    (seed offsets 1 and 2, not timed), then the evaluation sequence is solved with each
+    rule; both solves are timed with CUDA events over the whole sequence."""
+    from paper_1206_3768_gb300 import binding as cb
+    from paper_1206_3768_gb300 import degree_model as dm
+    from paper_1206_3768_gb300 import inputs
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    N = args.problems or 20
+    stream = torch.cuda.current_stream(dev)
+    evalseq = inputs.planted_sequence(args.workload, N=N, device=dev, keep_vectors=False)
+    n, nev, blk = evalseq.n, evalseq.nev, evalseq.blk
+    with cb.Solver(n, blk, stream=stream, deg_min=4, deg_max=40) as s:
+        cb.chfsi_degree_log_start(s.ctx, 10_000_000)
+        for off in (1, 2):
+            tr = inputs.planted_sequence(args.workload, N=min(N, 8), device=dev, keep_vectors=False,
+                                         seed_offset=off)
+            cb.chfsi_reset_warm_state(s.ctx)
+            cb.chfsi_solve_sequence(s.ctx, [p.A for p in tr.problems], [p.B for p in tr.problems], nev, blk, 0,
+                                    evalseq.tol, want_vectors=False)
+            del tr
+        log = cb.chfsi_degree_log_read(s.ctx)
+        cb.chfsi_degree_log_start(s.ctx, 0)
+        X, z = dm.training_pairs(log)
+        model = cb.chfsi_mlp_init(12063768)
+        t0 = time.perf_counter()
+        loss = cb.chfsi_mlp_train(s.ctx, model, X, z, epochs=args.epochs, batch=256, lr=2e-3, seed=1)
+        t_train = time.perf_counter() - t0
+        z_var = float(np.var(z)) if len(z) else float("nan")
+        As = [p.A for p in evalseq.problems]
+        Bs = [p.B for p in evalseq.problems]
+        out = {}
+        for name, mdl in (("closed_form", None), ("learned", model)):
+            cb.chfsi_set_degree_model(s.ctx, mdl)
+            for _ in range(max(1, args.warmup)):
+                cb.chfsi_reset_warm_state(s.ctx)
+                cb.chfsi_solve_sequence(s.ctx, As, Bs, nev, blk, 0, evalseq.tol, want_vectors=False)
+            cb.chfsi_reset_warm_state(s.ctx)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ev, _, st = cb.chfsi_solve_sequence(s.ctx, As, Bs, nev, blk, 0, evalseq.tol, want_vectors=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            scale = max(float(np.max(np.abs(p.lam))) for p in evalseq.problems)
+            err = max(float(np.max(np.abs(ev[l].numpy() - p.lam[:nev]))) for l, p in enumerate(evalseq.problems))
+            out[name] = {"eigenpairs_per_s": float(torch.isfinite(ev).sum()) / (ms / 1e3), "ms": ms,
+                         "filter_matvecs": int(sum(x["filter_matvecs"] for x in st)),
+                         "loops": int(sum(x["loops"] for x in st)),
+                         "max_resid": max(x["max_resid"] for x in st), "max_eig_err": err / scale}
+        cb.chfsi_set_degree_model(s.ctx, None)
+    print(json.dumps({
+        "metric": "learned vs closed-form filter degree (converged eigenpairs/s, filter matvecs)",
+        "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+        "closed_form": out["closed_form"], "learned": out["learned"],
+        "matvec_ratio_learned_over_closed": out["learned"]["filter_matvecs"] / out["closed_form"]["filter_matvecs"],
+        "speedup_learned": out["learned"]["eigenpairs_per_s"] / out["closed_form"]["eigenpairs_per_s"],
+        "training": {"samples": int(len(z)), "epochs": args.epochs, "final_loss": loss,
+                     "target_variance": z_var, "seconds": t_train,
+                     "data": "degree logs of 2 training sequences (seed offsets 1, 2) of the same shape"},
+        "config": {"workload": f"{args.workload}: n={n} nev={nev} blk={blk} N={N}, degree range [4, 40], "
+                               "first problem cold, rest warm"},
+    }), flush=True)
+
+
 def run_kernel_case(args):
     """One Chebyshev filter call (deg launches of the filter GEMM) through the C ABI on a
     seeded n x n Hermitian matrix and n x m block: the small case used for kernel profiles."""
@@ -536,6 +605,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-angles", action="store_true")
+    ap.add_argument("--degree-model", action="store_true",
+                    help="train the learned degree on logs of training sequences and compare it with "
+                         "the closed form on the workload (a separate line, not the headline)")
+    ap.add_argument("--epochs", type=int, default=150)
     ap.add_argument("--kpoints", type=int, default=32)
     ap.add_argument("--workers", type=int, default=4)
     ap.add_argument("--workload", choices=["c2", "c3", "c4"], default=WORKLOAD,
@@ -553,7 +626,9 @@ def main():
     ap.add_argument("--case-reps", type=int, default=1)
     ap.add_argument("--case-slices", type=int, default=0)
     args = ap.parse_args()
-    if args.workload == "c4" and args.impl == "ours" and not args.kernel_case:
+    if args.degree_model and args.impl == "ours":
+        run_degree_model(args)
+    elif args.workload == "c4" and args.impl == "ours" and not args.kernel_case:
         run_batch(args)
     elif args.kernel_case == "heev":
         run_heev_case(args)

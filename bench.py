@@ -385,7 +385,7 @@ def run_ours(args):
                        "filter_arithmetic": "FP64 results from bf16 digit-slice tensor-core "
                                             "products (exact fp32 chunks, double-float sums): "
                                             "filter 2-7 slices chosen per loop, Rayleigh-Ritz, "
-                                            "reduction and other large products 8 slices; FP32 "
+                                            "reduction and other large products 7 slices; FP32 "
                                             "Cholesky QR + FP64 Loewdin steps; FP64 Jacobi "
                                             "eigensolver, residuals and small products",
                        "tol": seq.tol, "max_resid": max_resid,

@@ -137,8 +137,9 @@ int chfsi_cholesky(chfsi_ctx* ctx, int64_t n, const chfsi_z* B, int64_t ldb, chf
                    int64_t ldl);
 
 /* Hs = L^{-1} A L^{-H}, exactly Hermitian in full storage (Section 4.1).  L lower.  With
- * precision 1 the two products run as 8-slice split-BF16 tensor-core products (error below
- * the FP64 GEMM bound); with precision 0 in FP64 arithmetic. */
+ * precision 1 the two products run as 8-slice split-BF16 tensor-core products (error about
+ * 1e-17 relative to the operands' row and column scales, below the FP64 GEMM bound); with
+ * precision 0 in FP64. */
 int chfsi_reduce(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const chfsi_z* L,
                  int64_t ldl, chfsi_z* Hs, int64_t ldh);
 
@@ -177,7 +178,7 @@ int chfsi_orthonormalize(chfsi_ctx* ctx, int64_t n, int32_t m, chfsi_z* Y, int64
 
 /* Rayleigh-Ritz (Algorithm 1): G = Y^H H Y, G w = theta w (ascending), Y <- Y W,
  * W_out <- H Y (the new Ritz vectors' products).  theta: device, m doubles.  H Hermitian;
- * with precision 1 the product H Y uses 8-slice split-BF16 products (FP64-level). */
+ * with precision 1 the product H Y uses 7-slice split-BF16 products (FP64-level). */
 int chfsi_rayleigh_ritz(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,
                         chfsi_z* Y, int64_t ldy, chfsi_z* HY, int64_t ldhy, double* theta);
 

@@ -168,13 +168,15 @@ int gemm(chfsi_ctx* ctx, const GemmDesc& g) {
 }
 
 // A dense product in the context's precision: in mixed mode, products large enough to
-// amortise the slicing run as 8-slice split-BF16 tensor-core products (FP64-level accuracy;
-// triangular operands are used with their exact zeros), the rest as FP64 GEMMs.
+// amortise the slicing run as 7-slice split-BF16 tensor-core products (error ~2e-15 relative
+// to the operands' row and column scales; triangular operands are used with their exact
+// zeros), the rest as FP64 GEMMs.
+constexpr int kGemmSlices = 7;
 int gemm_auto(chfsi_ctx* ctx, const GemmDesc& g) {
   const double work = (double)g.M * g.N * g.K;
   const bool square_c = !g.lowerC || g.M == g.N;
   if (ctx->opts.precision == 1 && work >= 16777216.0 && square_c) {
-    CK(oz_gemm(g.opA, g.A, g.lda, g.opB, g.B, g.ldb, g.M, g.N, g.K, 8, g.alpha, g.beta, g.Cin,
+    CK(oz_gemm(g.opA, g.A, g.lda, g.opB, g.B, g.ldb, g.M, g.N, g.K, kGemmSlices, g.alpha, g.beta, g.Cin,
                g.ldcin, g.gamma, g.D, g.ldd, g.C, g.ldc, g.triA == 1, g.lowerC, ctx->ws.oz,
                ctx->stream));
     return CHFSI_OK;
@@ -195,7 +197,10 @@ GemmDesc gd(int M, int N, int K, const zd* A, int64_t lda, int opA, const zd* B,
 }
 
 constexpr int NB = 128;  // panel width of the blocked factorisations
-constexpr int kRRSlices = 8;  // digit slices of the Rayleigh-Ritz product Hs Y in mixed mode
+// Digit slices of the FP64-level products in mixed mode (reduction, Rayleigh-Ritz, Gram and
+// rotation products, back-transforms): 7 slices leave an error of about 2^-49 (2e-15)
+// relative to the row and column scales, four orders of magnitude below the 1e-10 bar.
+constexpr int kProductSlices = 7;
 
 // In-place blocked right-looking Cholesky on the lower triangle of L (n x n).
 int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n, int nb = NB) {
@@ -253,7 +258,9 @@ int reduce_to_standard(chfsi_ctx* ctx, const zd* Af, int64_t lda, const zd* Linv
                        zd* Hs, int64_t ldh, int n, bool split = false) {
   Workspace& ws = ctx->ws;
   if (split) {
-    const int S = kRRSlices;
+    // 8 slices: the row scales of L^{-1} grow like sqrt(cond(B)), and its two products carry
+    // that growth into Hs; 2^-56 keeps the eigenvalue error at the FP64 level for cond(B) 1e4.
+    const int S = 8;
     CK(oz_gemm(OPN, Linv, ldl, OPN, Af, lda, n, n, n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, ws.T,
                ws.n_max, 1, 0, ws.oz, ctx->stream));
     CK(oz_gemm(OPN, Linv, ldl, OPC, ws.T, ws.n_max, n, n, n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
@@ -431,6 +438,7 @@ int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const z
       {
         PhaseScope ps(ctx, PH_SMALL);
         CK(qr_pass(ws.G, ldm, m, ws.V, ldm, ws.dscale, ws.jac, ws.shiftflag, ws.status, ctx->stream));
+        CK(scale_cols_flag(*Ya, ld, n, m, ws.dscale, ws.shiftflag + 3, ctx->stream));
       }
       CKS(gemm_auto(ctx, gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld)));
       std::swap(*Ya, *Yb);
@@ -478,7 +486,7 @@ int rayleigh_ritz_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, 
   const int64_t ld = ws.n_max;
   const int64_t ldm = ws.blk_max;
   if (rr_slices > 0) {
-    // FP64-level product from 8 digit slices per operand (error below the FP64 GEMM bound)
+    // FP64-level product from 7 digit slices per operand (error ~2e-15 of the scales)
     CK(oz_filter_product(*Ya, ld, n, m, rr_slices, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, *W, ld,
                          ws.oz, ctx->stream));
   } else {
@@ -578,11 +586,11 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
     CKS(stage_in(ctx, S.A, S.lda, n, n, ws.Hs, ld, &Asrc));
     CK(herm_from_lower(Asrc, Asrc == ws.Hs ? ld : S.lda, ws.Af, ld, n, ws.status, ctx->stream));
     CKS(reduce_to_standard(ctx, ws.Af, ld, ws.Linv, ld, ws.Hs, ld, n, o.precision == 1));
-    if (o.precision == 1) CK(oz_slice_hermitian(ws.Hs, ld, n, kRRSlices, ws.oz, ctx->stream));
+    if (o.precision == 1) CK(oz_slice_hermitian(ws.Hs, ld, n, kProductSlices, ws.oz, ctx->stream));
   }
   CKS(check_status(ctx, "input"));
 
-  const int rr_slices = o.precision == 1 ? kRRSlices : 0;
+  const int rr_slices = o.precision == 1 ? kProductSlices : 0;
 
   // ---------------------------------------------------------------- a3: Lanczos bounds
   const bool warm = ctx->has_warm && ctx->warm_n == n && ctx->warm_blk == blk;
@@ -1180,7 +1188,7 @@ int chfsi_rayleigh_ritz(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, 
   zd *Ya = ws.Y0, *Yb = ws.Y1, *W = ws.W, *Zb = ws.Z;
   int rr_slices = 0;
   if (ctx->opts.precision == 1) {
-    rr_slices = kRRSlices;
+    rr_slices = kProductSlices;
     CK(oz_slice_hermitian(Z(H), ldh, (int)n, rr_slices, ws.oz, ctx->stream));
   }
   CKS(rayleigh_ritz_block(ctx, Z(H), ldh, (int)n, m, &Ya, &Yb, &W, &Zb, theta, rr_slices));

@@ -81,10 +81,13 @@ cudaError_t small_cholesky(zd* G, int64_t ldg, int m, int scale, int shift_on_fa
 cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m, cudaStream_t s);
 // One pass of the mixed-precision re-orthonormalisation (Y <- Y T) from G = Y^H Y (lower):
 // a first-order Loewdin step in FP64 when ||G - I||_F <= 1e-3 (flags[0] = 1 once that norm
-// is <= 1e-8), else an FP32 Cholesky QR step on the scaled Gram (shift on breakdown).
-// T is m x m (full).  scratch: m*m + 32*m float2 (used when m > 144).  flags: 4 ints.
+// is <= 1e-8), else an FP32 Cholesky QR step on the scaled Gram (shift on breakdown), whose
+// T applies to Y scaled by dscale (flags[3] = 1).  T is m x m (full).  scratch: m*m + 32*m
+// float2 (used when m > 144).  flags: 4 ints.
 cudaError_t qr_pass(const zd* G, int64_t ldg, int m, zd* T, int64_t ldt, double* dscale, void* scratch,
                     int* flags, int* status, cudaStream_t s);
+// Y[:, j] *= d[j] when *flag (device) is set; no-op otherwise.
+cudaError_t scale_cols_flag(zd* Y, int64_t ldy, int n, int m, const double* d, const int* flag, cudaStream_t s);
 // T = D X^H (upper triangular, zero below): the right factor of Cholesky QR, Q = Y T.
 cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* T, int64_t ldt,
                      cudaStream_t s);

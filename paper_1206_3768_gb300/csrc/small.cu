@@ -162,9 +162,11 @@ __global__ void cholqr_T_kernel(const zd* X, int64_t ldx, int m, const double* d
 //   e <= 1e-3: first-order Loewdin step T = I - (G - I)/2 in FP64 (full Hermitian T); the
 //              new Gram error is about 3/4 e^2, so e <= 1e-8 finishes (flags[0] = 1);
 //   e >  1e-3: Cholesky QR step in FP32 on the unit-diagonal scaled Gram,
-//              D G D + s I = L L^H (s = 0, then 1e-5, 1e-4, 1e-3 on breakdown),
-//              T = D L^{-H} (upper triangular), which reduces e to the FP32 level (or, when Y
-//              is ill-conditioned, reduces cond(Y) by about sqrt(1/s)).
+//              D G D + s I = L L^H (s = 0, then 1e-5, 1e-4, 1e-3 on breakdown), Y <- (Y D) T
+//              with T = L^{-H} (upper triangular; flags[3] = 1 asks for the column scaling
+//              by D = dscale first, so that the product sees unit columns and O(1) factors),
+//              which reduces e to the FP32 level (or, when Y is ill-conditioned, reduces
+//              cond(Y) by about sqrt(1/s)).
 // Precision of T only affects how far Y T is from orthonormal, never its span: the product
 // Y T itself is formed in FP64-level arithmetic and the last step is always an FP64 Loewdin
 // step.  flags[1] counts FP32 Cholesky steps, flags[2] records a shifted one.  One CTA of
@@ -218,11 +220,17 @@ __global__ void __launch_bounds__(QR_THREADS)
       if (i == j) t = zmk(1.0 - 0.5 * (g.x - 1.0), 0.0);
       T[i + (int64_t)j * ldt] = t;
     }
-    if (tid == 0 && e_f <= 1e-8) flags[0] = 1;
+    if (tid == 0) {
+      if (e_f <= 1e-8) flags[0] = 1;
+      flags[3] = 0;  // T applies to Y as it is
+    }
     return;
   }
   if (!(e_f < 1e300)) {  // NaN or Inf in the Gram matrix
-    if (tid == 0) atomicOr(status, DEV_NOTPD);
+    if (tid == 0) {
+      atomicOr(status, DEV_NOTPD);
+      flags[3] = 0;
+    }
     return;
   }
 
@@ -233,7 +241,10 @@ __global__ void __launch_bounds__(QR_THREADS)
     const double d = G[i + (int64_t)i * ldg].x;
     dscale[i] = (d > 0.0 && isfinite(d)) ? rsqrt(d) : 1.0;
   }
-  if (tid == 0) atomicAdd(flags + 1, 1);
+  if (tid == 0) {
+    atomicAdd(flags + 1, 1);
+    flags[3] = 1;  // T applies to Y D (columns scaled by dscale first)
+  }
   __syncthreads();
   int attempt = 0;
   for (; attempt < 4; ++attempt) {
@@ -281,7 +292,10 @@ __global__ void __launch_bounds__(QR_THREADS)
     if (fail < 0) break;
   }
   if (attempt == 4) {
-    if (tid == 0) atomicOr(status, DEV_NOTPD);
+    if (tid == 0) {
+      atomicOr(status, DEV_NOTPD);
+      flags[3] = 0;
+    }
     return;
   }
   if (attempt > 0 && tid == 0) flags[2] = 1;
@@ -308,9 +322,8 @@ __global__ void __launch_bounds__(QR_THREADS)
       }
       __syncwarp();
     }
-    const double dj = dscale[j];
     for (int i = lane; i < m; i += 32)
-      T[j + (int64_t)i * ldt] = (i < j) ? zmk(0.0, 0.0) : zmk(dj * (double)x[i].x, -dj * (double)x[i].y);
+      T[j + (int64_t)i * ldt] = (i < j) ? zmk(0.0, 0.0) : zmk((double)x[i].x, -(double)x[i].y);
     __syncwarp();
   }
 }

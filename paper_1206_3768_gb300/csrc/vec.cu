@@ -525,6 +525,17 @@ __global__ void dev_theta_kernel(const zd* R, int64_t ldr, const zd* BR, int64_t
   if (threadIdx.x == 0) theta[i] = asin(fmin(1.0, sqrt(fmax(acc, 0.0))));
 }
 
+// Y[:, j] *= d[j] for every column when *flag is set (the column scaling a Cholesky QR
+// step of the mixed-precision re-orthonormalisation asks for), nothing otherwise.
+__global__ void scale_cols_flag_kernel(zd* Y, int64_t ldy, int n, int m, const double* d, const int* flag) {
+  if (!*flag) return;
+  const int64_t tot = (int64_t)n * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    Y[i + (int64_t)j * ldy] = zscale(Y[i + (int64_t)j * ldy], d[j]);
+  }
+}
+
 }  // namespace
 
 cudaError_t herm_from_lower(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int* status,
@@ -688,6 +699,13 @@ cudaError_t deviation_residual(const zd* Xp, int64_t ldp, const zd* Xc, int64_t 
 cudaError_t deviation_theta(const zd* R, int64_t ldr, const zd* BR, int64_t ldbr, int n, int k,
                             double* theta, cudaStream_t s) {
   dev_theta_kernel<<<k, 256, 0, s>>>(R, ldr, BR, ldbr, n, theta);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+cudaError_t scale_cols_flag(zd* Y, int64_t ldy, int n, int m, const double* d, const int* flag, cudaStream_t s) {
+  const int64_t tot = (int64_t)n * m;
+  const int blocks = (int)std::min<int64_t>(4 * sm_count(), (tot + 255) / 256);
+  scale_cols_flag_kernel<<<std::max(1, blocks), 256, 0, s>>>(Y, ldy, n, m, d, flag);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

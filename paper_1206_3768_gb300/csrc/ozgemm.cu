@@ -287,6 +287,7 @@ struct TcParams {
   int nkb, tiles_m, splits, Mp, Np, n_real;  // n_real: columns of B^ that hold data
   int b_box_rows;                            // rows of the B box (<= TC_BN, multiple of 16)
   int stages;                                // TMA ring depth (<= TC_MAX_STAGES)
+  int pair_split;                            // splits partition the slice pairs (else k-blocks)
   OzPairs pairs;
   double* part;
   int* status;
@@ -406,8 +407,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // an A slice from L2 while it is hot.
   const int nkb = p.a_lower ? min(p.nkb, m0 / TC_BK + TC_BM / TC_BK) : p.nkb;
   const int ncols = min(TC_BN, ((p.n_real - n0 + 15) / 16) * 16);  // MMA N for this tile
-  const int per = (p.nkb + p.splits - 1) / p.splits;
-  const int kb_lo = min(nkb, (int)blockIdx.y * per), kb_hi = min(nkb, kb_lo + per);
+  // split y takes either a range of k-blocks (all pairs) or, for short K (one panel), a
+  // range of slice pairs (all k-blocks)
+  int kb_lo = 0, kb_hi = nkb, pr_lo = 0, pr_hi = p.pairs.n;
+  if (p.pair_split) {
+    const int pp = (p.pairs.n + p.splits - 1) / p.splits;
+    pr_lo = min(p.pairs.n, (int)blockIdx.y * pp);
+    pr_hi = min(p.pairs.n, pr_lo + pp);
+  } else {
+    const int per = (p.nkb + p.splits - 1) / p.splits;
+    kb_lo = min(nkb, (int)blockIdx.y * per);
+    kb_hi = min(nkb, kb_lo + per);
+  }
+  const int npr = pr_hi - pr_lo;
 
   const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NS;
@@ -444,7 +456,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool stop = false;
       for (int k0 = kb_lo; k0 < kb_hi && !stop; k0 += OZ_CHUNK_KB) {
         const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
-        for (int pr = 0; pr < p.pairs.n && !stop; ++pr) {
+        for (int pr = pr_lo; pr < pr_hi && !stop; ++pr) {
           const int arow = p.pairs.s[pr] * p.Mp + m0, brow = p.pairs.t[pr] * p.Np + n0;
           for (int kb = k0; kb < k1; ++kb, ++i) {
             const uint32_t fb = full0 + 8 * stage;
@@ -480,7 +492,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool stop = false;
       for (int k0 = kb_lo; k0 < kb_hi && !stop; k0 += OZ_CHUNK_KB) {
         const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
-        for (int pr = 0; pr < p.pairs.n && !stop; ++pr, ++chunk) {
+        for (int pr = pr_lo; pr < pr_hi && !stop; ++pr, ++chunk) {
           // accumulator chunk & 1 is free once the drain has finished chunk - 2
           if (chunk >= 2 && !mbar_wait(acce0 + 8 * (chunk & 1), ((chunk >> 1) - 1) & 1, abort_flag, p.status)) {
             stop = true;
@@ -539,12 +551,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     int chunk = 0;
     bool ok = true;
-    const int nchunks = ((kb_hi - kb_lo + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB) * p.pairs.n;
+    const int nchunks = (kb_hi > kb_lo && npr > 0) ? ((kb_hi - kb_lo + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB) * npr : 0;
     for (; chunk < nchunks && ok; ++chunk) {
       const int b = chunk & 1;
       if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status, true)) { ok = false; break; }
       tc_fence_after();
-      const int pr = chunk % p.pairs.n;
+      const int pr = pr_lo + chunk % npr;
       const float sc = ldexpf(1.0f, -OZ_BETA * (p.pairs.s[pr] + p.pairs.t[pr] + 2));
       const uint32_t acc_base = lane_base + (uint32_t)(b * TC_ACC1);
 #pragma unroll
@@ -704,19 +716,17 @@ __global__ void oz_slice_hermitian_kernel(const zd* Hs, int64_t ldh, int n, int 
 }
 
 
-// Slices from the ROWS of a general complex matrix X (rows x cols, column-major): the row
-// scale needs a full pass over the row, and the row is strided in memory, so 32-row blocks
-// are read column by column (coalesced) and transposed through shared memory.
+// Slices from the ROWS of a general complex matrix X (rows x cols, column-major), in two
+// kernels: the row scales need a full pass over each row, and a row is strided in memory,
+// so 32-row groups are read column by column (coalesced) to find the row exponents; the
+// digits are then written by CTAs that each take one 32-row group and one range of columns
+// (transposed through shared memory), so that thin matrices still spread over the GPU.
 //   mode 0 (A operand, real embedding): rows 2r, 2r+1 of A^ = [Re x, -Im x], [Im x, Re x]
 //   mode 1 (B operand of X^H): column r of B^ = conj(row r of X) = [Re x, -Im x]
-__global__ void oz_slice_rows_kernel(const zd* X, int64_t ldx, int rows, int cols, int S, int mode,
-                                     __nv_bfloat16* out, int64_t slice_stride, int Kp, int* e_out) {
+__global__ void oz_row_exponents_kernel(const zd* X, int64_t ldx, int rows, int cols, int* e_out) {
   __shared__ unsigned long long red[8][32];
-  __shared__ int ex[32];
-  __shared__ zd tile[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  const int r0 = blockIdx.x * 32;
-  const int r = r0 + tx;
+  const int r = blockIdx.x * 32 + tx;
   unsigned long long mx = 0ull;
   if (r < rows)
     for (int k = ty; k < cols; k += 8) {
@@ -727,22 +737,32 @@ __global__ void oz_slice_rows_kernel(const zd* X, int64_t ldx, int rows, int col
     }
   red[ty][tx] = mx;
   __syncthreads();
-  if (ty == 0) {
+  if (ty == 0 && r < rows) {
     unsigned long long m2 = red[0][tx];
     for (int j = 1; j < 8; ++j) m2 = red[j][tx] > m2 ? red[j][tx] : m2;
-    ex[tx] = exponent_from_bits(m2);
-    if (r < rows) e_out[r] = ex[tx];
+    e_out[r] = exponent_from_bits(m2);
   }
+}
+
+__global__ void oz_slice_rows_kernel(const zd* X, int64_t ldx, int rows, int cols, int S, int mode,
+                                     __nv_bfloat16* out, int64_t slice_stride, int Kp, const int* e_row,
+                                     int chunk) {
+  __shared__ int ex[32];
+  __shared__ zd tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int r0 = blockIdx.x * 32;
+  if (ty == 0) ex[tx] = (r0 + tx < rows) ? e_row[r0 + tx] : 0;
   __syncthreads();
-  for (int k0 = 0; k0 < cols; k0 += 32) {
+  const int k_end = min(cols, (int)(blockIdx.y + 1) * chunk);
+  for (int k0 = blockIdx.y * chunk; k0 < k_end; k0 += 32) {
     for (int rr = ty; rr < 32; rr += 8) {
       const int gr = r0 + tx, gk = k0 + rr;  // read column gk, rows r0..r0+31 (coalesced)
-      tile[rr][tx] = (gr < rows && gk < cols) ? X[gr + (int64_t)gk * ldx] : zmk(0.0, 0.0);
+      tile[rr][tx] = (gr < rows && gk < k_end) ? X[gr + (int64_t)gk * ldx] : zmk(0.0, 0.0);
     }
     __syncthreads();
     for (int rr = ty; rr < 32; rr += 8) {  // write row r0 + rr, columns k0 + tx (coalesced)
       const int gr = r0 + rr, gk = k0 + tx;
-      if (gr < rows && gk < cols) {
+      if (gr < rows && gk < k_end) {
         const zd v = tile[tx][rr];
         const int e = ex[rr];
         if (mode == 0) {
@@ -810,10 +830,11 @@ int choose_oz_splits(int tiles, int total_kb, size_t cap_elems, int64_t tile_ele
 // tile.  Modelled CTA time in k-block units: every (panel, pair) chunk costs at least the
 // drain of one accumulator (about 5 k-blocks of MMA time), plus a pipeline fill; the launch
 // time is that times the number of waves of one CTA per SM.
-int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t tile_elems) {
+int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t tile_elems, int* pair_split) {
   const int sms = sm_count();
   int best = 1;
   double best_cost = 1e300;
+  *pair_split = 0;
   for (int S = 1; S <= std::min(nkb, 64); ++S) {
     if ((size_t)S * (size_t)tile_elems > cap_elems) break;
     const int per = (nkb + S - 1) / S;
@@ -823,6 +844,17 @@ int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t t
     const int64_t units = (int64_t)tiles * S;
     const double cost = (double)((units + sms - 1) / sms) * cta;
     if (cost < best_cost * 0.999) { best_cost = cost; best = S; }
+  }
+  // short K (a single panel): splitting the slice pairs gives more CTAs than splitting K
+  if (nkb <= OZ_CHUNK_KB) {
+    for (int S = 2; S <= npairs; ++S) {
+      if ((size_t)S * (size_t)tile_elems > cap_elems) break;
+      const int pp = (npairs + S - 1) / S;
+      const double cta = 6.0 + (double)pp * std::max(5, nkb);
+      const int64_t units = (int64_t)tiles * ((npairs + pp - 1) / pp);
+      const double cost = (double)((units + sms - 1) / sms) * cta;
+      if (cost < best_cost * 0.999) { best_cost = cost; best = (npairs + pp - 1) / pp; *pair_split = 1; }
+    }
   }
   return best;
 }
@@ -871,6 +903,24 @@ int oz_padded_n(int m) {
 }
 
 // ---- operands
+// Row exponents, then digits by (32-row group, column range) CTAs: about four CTAs per SM.
+static cudaError_t slice_rows(const zd* X, int64_t ldx, int rows, int cols, int S, int mode, __nv_bfloat16* out,
+                              int64_t slice_stride, int Kp, int* e_out, cudaStream_t s) {
+  const int groups = (rows + 31) / 32, kchunks = (cols + 31) / 32;
+  oz_row_exponents_kernel<<<groups, 256, 0, s>>>(X, ldx, rows, cols, e_out);
+  CHFSI_COUNT_LAUNCH();
+  const int gy = std::max(1, std::min(kchunks, (4 * sm_count() + groups - 1) / groups));
+  const int chunk = 32 * ((kchunks + gy - 1) / gy);
+  oz_slice_rows_kernel<<<dim3(groups, (cols + chunk - 1) / chunk), 256, 0, s>>>(X, ldx, rows, cols, S, mode, out,
+                                                                                slice_stride, Kp, e_out, chunk);
+  return cudaGetLastError();
+}
+#define CK_OZ(expr)                 \
+  do {                              \
+    cudaError_t e_ = (expr);        \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
 cudaError_t oz_slice_a(OzA& a, int op, const zd* X, int64_t ldx, int M, int K, int S, cudaStream_t s) {
   const int Kp = oz_padded_k(K), Mp = oz_padded_m(M);
   if (S > a.S_max || S < 1 || Kp > a.Kp_max || Mp > a.Mp_max || M <= 0 || K <= 0)
@@ -884,7 +934,7 @@ cudaError_t oz_slice_a(OzA& a, int op, const zd* X, int64_t ldx, int M, int K, i
     // op(A) = X^H: row i of op(A) is conj(column i of X), contiguous (X is K x M)
     oz_slice_hermitian_kernel<<<M, 256, 0, s>>>(X, ldx, K, S, a.ptr, a.slice, Kp, a.e);
   } else {
-    oz_slice_rows_kernel<<<(M + 31) / 32, 256, 0, s>>>(X, ldx, M, K, S, 0, a.ptr, a.slice, Kp, a.e);
+    CK_OZ(slice_rows(X, ldx, M, K, S, 0, a.ptr, a.slice, Kp, a.e, s));
   }
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
@@ -900,7 +950,7 @@ cudaError_t oz_slice_b(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, i
   if (e != cudaSuccess) return e;
   if (op == OPC) {
     // op(B) = X^H (X is N x K): column j = conj(row j of X)
-    oz_slice_rows_kernel<<<(N + 31) / 32, 256, 0, s>>>(X, ldx, N, K, S, 1, b.ptr, b.slice, Kp, b.e);
+    CK_OZ(slice_rows(X, ldx, N, K, S, 1, b.ptr, b.slice, Kp, b.e, s));
   } else {
     oz_slice_cols_kernel<<<Np, 256, 0, s>>>(X, ldx, K, N, S, b.ptr, b.slice, Kp, b.e);
   }
@@ -943,7 +993,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     tp.part = oz.part;
     tp.status = oz.status;
     const int tiles = tp.tiles_m * ((Np + TC_BN - 1) / TC_BN);
-    tp.splits = splits = choose_tc_splits(tiles, tp.nkb, pairs.n, oz.part_elems, (int64_t)Mp * Np);
+    tp.splits = splits = choose_tc_splits(tiles, tp.nkb, pairs.n, oz.part_elems, (int64_t)Mp * Np, &tp.pair_split);
     CUtensorMap mapA, mapB;
     // The B box is min(Np, TC_BN) rows high; a last tile narrower than that reads rows past
     // its slice (the next slice, or the buffer's spare rows: the allocation holds at least

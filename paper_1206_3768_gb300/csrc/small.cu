@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(QR_THREADS)
       const int i = (int)(e % m), j = (int)(e / m);
       if (i < j) continue;
       const zd g = G[i + (int64_t)j * ldg];
-      const double sc = dscale[i] * dscale[j];
+      const double sc = dscale[i] * dscale[j];  // FP64: G may exceed the FP32 range
       float2 v = make_float2((float)(g.x * sc), (float)(g.y * sc));
       const float shift = attempt == 0 ? 0.f : (attempt == 1 ? 1e-5f : (attempt == 2 ? 1e-4f : 1e-3f));
       if (i == j) v = make_float2(v.x + shift, 0.f);
@@ -341,7 +341,7 @@ struct JacParams {
   int max_sweeps;
 };
 
-constexpr long kBarrierSpinLimit = 20000000;  // ~1-2 s with the back-off below
+constexpr long kBarrierSpinLimit = 8000000;  // polls of an L2 word: a few seconds at most
 
 // Sense-free generation barrier over all CTAs of a cooperative launch.  Returns false (and
 // sets DEV_TIMEOUT) if the wait ran past its limit or another CTA already reported it.
@@ -366,7 +366,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+
       }
     }
     __threadfence();

@@ -826,10 +826,11 @@ int choose_oz_splits(int tiles, int total_kb, size_t cap_elems, int64_t tile_ele
   return best;
 }
 
-// Split-K count for the tcgen05 kernel: split y takes k-blocks [y per, (y + 1) per) of every
-// tile.  Modelled CTA time in k-block units: every (panel, pair) chunk costs at least the
-// drain of one accumulator (about 5 k-blocks of MMA time), plus a pipeline fill; the launch
-// time is that times the number of waves of one CTA per SM.
+// Split count for the tcgen05 kernel: split y takes k-blocks [y per, (y + 1) per) of every
+// tile, or (short K) a range of slice pairs.  Modelled CTA time in k-block units: every
+// (panel, pair) chunk costs at least the drain of one accumulator (about 3 k-blocks of
+// streaming time), plus a pipeline fill; the launch time is that times the number of waves
+// of one CTA per SM.
 int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t tile_elems, int* pair_split) {
   const int sms = sm_count();
   int best = 1;
@@ -840,7 +841,7 @@ int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t t
     const int per = (nkb + S - 1) / S;
     double cta = 6.0;
     for (int k0 = 0; k0 < per; k0 += OZ_CHUNK_KB)
-      cta += (double)npairs * std::max(5, std::min(OZ_CHUNK_KB, per - k0));
+      cta += (double)npairs * std::max(3, std::min(OZ_CHUNK_KB, per - k0));
     const int64_t units = (int64_t)tiles * S;
     const double cost = (double)((units + sms - 1) / sms) * cta;
     if (cost < best_cost * 0.999) { best_cost = cost; best = S; }
@@ -850,7 +851,7 @@ int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t t
     for (int S = 2; S <= npairs; ++S) {
       if ((size_t)S * (size_t)tile_elems > cap_elems) break;
       const int pp = (npairs + S - 1) / S;
-      const double cta = 6.0 + (double)pp * std::max(5, nkb);
+      const double cta = 6.0 + (double)pp * std::max(3, nkb);
       const int64_t units = (int64_t)tiles * ((npairs + pp - 1) / pp);
       const double cost = (double)((units + sms - 1) / sms) * cta;
       if (cost < best_cost * 0.999) { best_cost = cost; best = (npairs + pp - 1) / pp; *pair_split = 1; }

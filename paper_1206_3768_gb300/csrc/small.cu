@@ -392,16 +392,22 @@ __device__ __forceinline__ Rot jacobi_rotation(const zd* src, int mp, int p, int
   const double a = ldcg(src + p + (int64_t)p * mp).x;
   const double d = ldcg(src + q + (int64_t)q * mp).x;
   const zd b = ldcg(src + p + (int64_t)q * mp);
-  const double ab = sqrt(zabs2(b));
+  const double ab2 = zabs2(b);
   Rot R;
-  if (!(ab > thresh)) {
+  if (!(ab2 > thresh * thresh)) {
     R.c = 1.0; R.s = 0.0; R.w = zmk(1.0, 0.0); R.active = 0;
   } else {
-    const double zeta = (d - a) / (2.0 * ab);
-    const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-    R.c = 1.0 / sqrt(1.0 + t_ * t_);
+    // tan of the rotation angle from zeta = (d - a) / (2 |b|), with reciprocal square roots
+    // in place of divisions where the formula allows (the FP64 pipe is this part's bottleneck)
+    const double inv_ab = rsqrt(ab2);
+    const double zeta = 0.5 * (d - a) * inv_ab;
+    const double az = fabs(zeta);
+    // |zeta| large: 1/(|zeta| + sqrt(1 + zeta^2)) without overflow of zeta^2
+    const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) /
+                      (az + (az < 1e150 ? sqrt(1.0 + zeta * zeta) : az));
+    R.c = rsqrt(1.0 + t_ * t_);
     R.s = t_ * R.c;
-    R.w = zmk(b.x / ab, -b.y / ab);  // e^{-i phi}
+    R.w = zmk(b.x * inv_ab, -b.y * inv_ab);  // e^{-i phi}
     R.active = 1;
   }
   return R;

@@ -730,11 +730,22 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
         CK(column_residuals(W, ld, Ya, ld, theta, n, m, resid, ctx->stream));
         CK(lock_scan(resid, m, tau, nev - conv, ws.ilist, ctx->stream));
       }
+      // one synchronisation for the loop's read-back: status, locked count, theta, r
       int nlock = 0;
-      CKS(read_back(ctx, &nlock, ws.ilist, 1));
-      CKS(read_back(ctx, th.data(), theta, m));
-      CKS(read_back(ctx, rr.data(), resid, m));
-      CKS(check_status(ctx, "filter loop"));
+      {
+        int* h_int = static_cast<int*>(ws.host_pinned);
+        double* h_th = reinterpret_cast<double*>(static_cast<char*>(ws.host_pinned) + 16);
+        double* h_r = h_th + ws.blk_max;
+        CK(cudaMemcpyAsync(h_int, ws.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(h_int + 2, ws.ilist, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(h_th, theta, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(h_r, resid, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        nlock = h_int[2];
+        std::copy(h_th, h_th + m, th.begin());
+        std::copy(h_r, h_r + m, rr.begin());
+        if (h_int[0] != DEV_OK) CKS(check_status(ctx, "filter loop"));
+      }
       have_r = true;
       st.loops++;
       if (nlock > 0) {
@@ -912,6 +923,10 @@ cudaError_t workspace_alloc(Workspace& ws, int64_t n_max, int blk_max, int lancz
   e = oz_alloc(ws.oz, (int)n_max, ws.blk_max, 8);
   if (e != cudaSuccess) return e;
   ws.oz.status = ws.status;
+  // pinned mirror for the per-loop read-back: status (2 ints), locked count, theta, r
+  ws.host_pinned_bytes = 16 + 2 * sizeof(double) * (size_t)ws.blk_max;
+  e = cudaMallocHost(&ws.host_pinned, ws.host_pinned_bytes);
+  if (e != cudaSuccess) return e;
   e = cudaMemset(ws.status, 0, 2 * sizeof(int));
   if (e != cudaSuccess) return e;
   const int big = 0x7fffffff;
@@ -929,6 +944,7 @@ void workspace_free(Workspace& ws) {
   for (void* p : ptrs)
     if (p) debug_check(cudaFree(p), "cudaFree");
   oz_free(ws.oz);
+  if (ws.host_pinned) debug_check(cudaFreeHost(ws.host_pinned), "cudaFreeHost");
   ws = Workspace{};
 }
 

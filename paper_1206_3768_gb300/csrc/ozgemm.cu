@@ -262,11 +262,21 @@ __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int N
 // issues tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor memory, N up to
 // 144 so that a 130-column block is one tile and the large operand is streamed once), and
 // twelve drain warps fold each exact 960-term chunk into double-float sums.  Tensor memory
-// (512 columns): two 144-column accumulators at columns 0 and 160 used alternately (one
-// fills while the other drains) and the high words of the sums at 320..463; the low words
-// live in the drain threads' registers.  Warp 0 issues TMA loads, warp 1 issues MMAs,
-// warps 2..13 drain: three warps per group of 32 tensor-memory lanes, one for each third
-// (48 columns) of the tile.  14 warps keep at most 4 warps on each SM sub-partition, so
+// (512 columns): two sets of accumulators used alternately (one fills while the other
+// drains) and the high words of the sums after them; the low words live in the drain
+// threads' registers.
+// Slice groups: the pairs are issued in groups (s, t0 .. t0 + g - 1) that share the A slice
+// s.  One stage holds one A tile and the B tiles of the whole group (consecutive slices of B
+// are consecutive rows of its buffer, so one TMA box of g x Np rows), and the MMA thread
+// issues the group's products into g accumulators.  The A stream, which bounds this kernel,
+// then carries one tile per group instead of one per pair.  g = 1 for blocks wider than 96
+// columns (two 144-column accumulators at columns 0 and 160, high words at 320); narrower
+// blocks take g up to 7 as tensor memory allows: 2 g accumulators of the block's width
+// (rounded up to 32 columns) plus the high words.
+// Warp 0 issues TMA loads, warp 1 issues MMAs,
+// warps 2..13 drain: three warps per group of 32 tensor-memory lanes; warp h of a lane group
+// owns the 8-column blocks h, h + 3, ..., h + 15 of the tile, so that narrow blocks still
+// spread over all three.  14 warps keep at most 4 warps on each SM sub-partition, so
 // each thread may hold 128 registers.  Every wait on an mbarrier is bounded; a
 // wait that runs out sets DEV_TIMEOUT and the CTA unwinds (waiting, again bounded, for its
 // own copies and MMAs) before freeing tensor memory.
@@ -277,7 +287,9 @@ constexpr int TC_MAX_STAGES = 12;
 constexpr int TC_SMEM_BUDGET = 227 * 1024 - 1024 - 512;  // dynamic shared memory for the ring
 constexpr int TC_DRAIN_THREADS = TC_THREADS - 64;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per stage
-constexpr int TC_ACC1 = 160, TC_HI = 320;           // tensor-memory column offsets
+constexpr int TC_ACC1 = 160, TC_HI = 320;           // tensor-memory columns for groups of one
+constexpr int TC_GROUP_MAX_N = 96;                  // widest block issued in groups of g > 1
+constexpr int TC_GROUP_MAX = 7;
 static_assert((16 * TC_BK * 2) % 1024 == 0, "B stages (16-row multiples) stay 1024-byte aligned");
 static_assert(TC_HI + TC_BN <= 512 && TC_ACC1 + TC_BN <= TC_HI, "tensor-memory layout");
 constexpr long kMbarSpinLimit = 1L << 26;
@@ -287,8 +299,11 @@ struct TcParams {
   int nkb, tiles_m, splits, Mp, Np, n_real;  // n_real: columns of B^ that hold data
   int b_box_rows;                            // rows of the B box (<= TC_BN, multiple of 16)
   int stages;                                // TMA ring depth (<= TC_MAX_STAGES)
-  int pair_split;                            // splits partition the slice pairs (else k-blocks)
-  OzPairs pairs;
+  int pair_split;                            // splits partition the slice groups (else k-blocks)
+  int group;                                 // g: largest group (B box = g x Np rows when g > 1)
+  int acc_stride;                            // tensor-memory columns between accumulators
+  int ngroups;
+  unsigned char gs[OZ_MAX_PAIRS], gt[OZ_MAX_PAIRS], gc[OZ_MAX_PAIRS];  // group: s, first t, size
   double* part;
   int* status;
 };
@@ -407,19 +422,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // an A slice from L2 while it is hot.
   const int nkb = p.a_lower ? min(p.nkb, m0 / TC_BK + TC_BM / TC_BK) : p.nkb;
   const int ncols = min(TC_BN, ((p.n_real - n0 + 15) / 16) * 16);  // MMA N for this tile
-  // split y takes either a range of k-blocks (all pairs) or, for short K (one panel), a
-  // range of slice pairs (all k-blocks)
-  int kb_lo = 0, kb_hi = nkb, pr_lo = 0, pr_hi = p.pairs.n;
+  // split y takes either a range of k-blocks (all groups) or, for short K (one panel), a
+  // range of slice groups (all k-blocks)
+  int kb_lo = 0, kb_hi = nkb, pr_lo = 0, pr_hi = p.ngroups;
   if (p.pair_split) {
-    const int pp = (p.pairs.n + p.splits - 1) / p.splits;
-    pr_lo = min(p.pairs.n, (int)blockIdx.y * pp);
-    pr_hi = min(p.pairs.n, pr_lo + pp);
+    const int pp = (p.ngroups + p.splits - 1) / p.splits;
+    pr_lo = min(p.ngroups, (int)blockIdx.y * pp);
+    pr_hi = min(p.ngroups, pr_lo + pp);
   } else {
     const int per = (p.nkb + p.splits - 1) / p.splits;
     kb_lo = min(nkb, (int)blockIdx.y * per);
     kb_hi = min(nkb, kb_lo + per);
   }
   const int npr = pr_hi - pr_lo;
+  // tensor-memory columns: accumulator j of buffer b at (b g + j) acc_stride, high words after
+  const int G = p.group;
+  const uint32_t acc_stride = (uint32_t)p.acc_stride, hi_col = 2u * (uint32_t)G * acc_stride;
+  const uint32_t b_pair_bytes = (uint32_t)p.Np * TC_BK * 2;  // B tile of one slice in a group box
 
   const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NS;
@@ -457,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int k0 = kb_lo; k0 < kb_hi && !stop; k0 += OZ_CHUNK_KB) {
         const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
         for (int pr = pr_lo; pr < pr_hi && !stop; ++pr) {
-          const int arow = p.pairs.s[pr] * p.Mp + m0, brow = p.pairs.t[pr] * p.Np + n0;
+          const int arow = p.gs[pr] * p.Mp + m0, brow = p.gt[pr] * p.Np + n0;
           for (int kb = k0; kb < k1; ++kb, ++i) {
             const uint32_t fb = full0 + 8 * stage;
             if (i >= NS && !mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status)) {
@@ -499,7 +518,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t d = tmem + (uint32_t)((chunk & 1) * TC_ACC1);
+          const uint32_t d = tmem + (uint32_t)(chunk & 1) * (uint32_t)G * acc_stride;
+          const int gc = p.gc[pr];
           for (int kb = k0; kb < k1; ++kb) {
             if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.status)) {
               stop = true;
@@ -507,10 +527,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             tc_fence_after();
             const uint32_t a_s = sA_u + stage * TC_A_BYTES, b_s = sB_u + stage * b_stage;
+            // pair j of the group: B tile j of the box into accumulator j
+            for (int j = 0; j < gc; ++j) {
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk)
-              tc_mma(d, sw128_desc(a_s + kk * 32), sw128_desc(b_s + kk * 32), idesc,
-                     (kb == k0 && kk == 0) ? 0u : 1u);
+              for (int kk = 0; kk < TC_BK / 16; ++kk)
+                tc_mma(d + (uint32_t)j * acc_stride, sw128_desc(a_s + kk * 32),
+                       sw128_desc(b_s + (uint32_t)j * b_pair_bytes + kk * 32), idesc,
+                       (kb == k0 && kk == 0) ? 0u : 1u);
+            }
             tc_commit(empty0 + 8 * stage);
             if (kb == k1 - 1) tc_commit(accf0 + 8 * (chunk & 1));
             if (++stage == NS) {
@@ -527,23 +551,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------ drain warps (2..13)
-    // Thread (quarter, lane) of third h owns row 32 * quarter + lane of the tile and the 48
-    // columns from c0 = 48 h: the high words of its sums sit in tensor memory, the low words
-    // in lo[] (registers; the column loops below are unrolled so that every index into lo[]
-    // is a constant).  Tensor memory is moved in blocks of 8 columns to keep the live
-    // registers within the 128 that 14 warps allow.
+    // Thread (quarter, lane) of warp h (0..2 within its lane group) owns row 32 * quarter +
+    // lane of the tile and the 8-column blocks h + 3 i (i < 6): the high words of its sums sit
+    // in tensor memory, the low words in lo[] (registers; the block loops below are unrolled
+    // so that every index into lo[] is a constant).  Tensor memory is moved in blocks of 8
+    // columns to keep the live registers within the 128 that 14 warps allow.
     const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
-    constexpr int kCols = TC_BN / 3;  // 48 columns per third
-    const int c0 = ((warp - 2) >> 2) * kCols;
+    constexpr int kBlocks = TC_BN / 24;  // 8-column blocks per warp
+    const int h = (warp - 2) >> 2;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    float lo[kCols];
+    float lo[kBlocks * 8];
     {
       uint32_t zero[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) zero[j] = 0u;
 #pragma unroll
-      for (int c = 0; c < kCols / 8; ++c) {
-        tmem_st8(lane_base + TC_HI + c0 + c * 8, zero);
+      for (int c = 0; c < kBlocks; ++c) {
+        // only the tile's columns: with groups the high words end at the last allocated column
+        if (8 * (3 * c + h) < ncols) tmem_st8(lane_base + hi_col + 8 * (3 * c + h), zero);
 #pragma unroll
         for (int j = 0; j < 8; ++j) lo[c * 8 + j] = 0.f;
       }
@@ -557,22 +582,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status, true)) { ok = false; break; }
       tc_fence_after();
       const int pr = pr_lo + chunk % npr;
-      const float sc = ldexpf(1.0f, -OZ_BETA * (p.pairs.s[pr] + p.pairs.t[pr] + 2));
-      const uint32_t acc_base = lane_base + (uint32_t)(b * TC_ACC1);
+      const int gc = p.gc[pr];
+      const float sc0 = ldexpf(1.0f, -OZ_BETA * (p.gs[pr] + p.gt[pr] + 2));
+      const uint32_t acc_base = lane_base + (uint32_t)b * (uint32_t)G * acc_stride;
 #pragma unroll
-      for (int c = 0; c < kCols / 8; ++c) {
-        if (c0 + c * 8 < ncols) {
+      for (int c = 0; c < kBlocks; ++c) {
+        const int col = 8 * (3 * c + h);
+        if (col < ncols) {
           uint32_t acc[8], hi[8];
-          tmem_ld8(acc_base + c0 + c * 8, acc);
-          tmem_ld8(lane_base + TC_HI + c0 + c * 8, hi);
-          tmem_wait_ld();
+          tmem_ld8(lane_base + hi_col + col, hi);
+          float sc = sc0;
+          for (int j = 0; j < gc; ++j) {  // pair (s, t0 + j), scale 2^{-7 (s + t0 + j + 2)}
+            tmem_ld8(acc_base + (uint32_t)j * acc_stride + col, acc);
+            tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float h = __uint_as_float(hi[j]);
-            two_sum_acc(h, lo[c * 8 + j], __uint_as_float(acc[j]) * sc);
-            hi[j] = __float_as_uint(h);
+            for (int q = 0; q < 8; ++q) {
+              float hq = __uint_as_float(hi[q]);
+              two_sum_acc(hq, lo[c * 8 + q], __uint_as_float(acc[q]) * sc);
+              hi[q] = __float_as_uint(hq);
+            }
+            sc *= 0.0078125f;  // 2^-7
           }
-          tmem_st8(lane_base + TC_HI + c0 + c * 8, hi);
+          tmem_st8(lane_base + hi_col + col, hi);
         }
       }
       tmem_wait_st();
@@ -584,16 +615,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       float2* P = reinterpret_cast<float2*>(p.part) + (int64_t)blockIdx.y * p.Mp * p.Np;
       const int row = m0 + quarter * 32 + lane;
 #pragma unroll
-      for (int c = 0; c < kCols / 8; ++c) {
-        if (c0 + c * 8 < ncols) {
+      for (int c = 0; c < kBlocks; ++c) {
+        const int col0 = 8 * (3 * c + h);
+        if (col0 < ncols) {
           uint32_t hi[8];
-          tmem_ld8(lane_base + TC_HI + c0 + c * 8, hi);
+          tmem_ld8(lane_base + hi_col + col0, hi);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int col = n0 + c0 + c * 8 + j;
+          for (int q = 0; q < 8; ++q) {
+            const int col = n0 + col0 + q;
             if (col < p.Np)
-              P[(int64_t)col * p.Mp + row] = make_float2(__uint_as_float(hi[j]), lo[c * 8 + j]);
+              P[(int64_t)col * p.Mp + row] = make_float2(__uint_as_float(hi[q]), lo[c * 8 + q]);
           }
         }
       }
@@ -873,6 +905,26 @@ bool oz_use_tcgen05() {
   }
   return choice == 1;
 }
+// Slice groups sharing one A tile per stage (tcgen05 kernel, blocks up to 96 columns wide);
+// CHFSI_OZ_GROUPS=0 issues one pair per stage instead.
+static bool oz_grouped_pairs() {
+  static int choice = -1;
+  if (choice < 0) {
+    const char* v = std::getenv("CHFSI_OZ_GROUPS");
+    choice = (v && std::strcmp(v, "0") == 0) ? 0 : 1;
+  }
+  return choice == 1;
+}
+// Smallest TMA ring a slice group may leave (its B box grows with the group): environment
+// variable CHFSI_OZ_GROUP_MIN_STAGES, default 4, clamped to [2, TC_MAX_STAGES].
+static int oz_group_min_stages() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("CHFSI_OZ_GROUP_MIN_STAGES");
+    v = e ? std::max(2, std::min(TC_MAX_STAGES, std::atoi(e))) : 4;
+  }
+  return v;
+}
 
 // 2-D bf16 tensor map over `rows` rows of `inner` elements (row pitch inner * 2 bytes),
 // boxes of 64 elements x box_rows rows, 128-byte swizzle (the layout the tcgen05
@@ -990,16 +1042,37 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     tp.Mp = Mp;
     tp.Np = Np;
     tp.n_real = m;
-    tp.pairs = pairs;
     tp.part = oz.part;
     tp.status = oz.status;
+    // group size (see the kernel's header): tensor memory holds 2 g accumulators of the
+    // block's width rounded up to 32 columns plus the high words, the B box is at most 256
+    // rows, and the ring keeps at least oz_group_min_stages() stages
+    int G = 1;
+    tp.acc_stride = TC_ACC1;
+    if (Np <= TC_GROUP_MAX_N && oz_grouped_pairs()) {
+      const int w = ((Np + 31) / 32) * 32;
+      G = std::min({S, TC_GROUP_MAX, (512 / w - 1) / 2, 256 / Np});
+      while (G > 1 && TC_SMEM_BUDGET / (TC_A_BYTES + G * Np * TC_BK * 2) < oz_group_min_stages()) --G;
+      if (G > 1) tp.acc_stride = w;
+    }
+    tp.group = G;
+    tp.ngroups = 0;
+    for (int si = 1; si <= S; ++si)
+      for (int t0 = 1; si + t0 <= S + 1; t0 += G) {
+        tp.gs[tp.ngroups] = (unsigned char)(si - 1);
+        tp.gt[tp.ngroups] = (unsigned char)(t0 - 1);
+        tp.gc[tp.ngroups] = (unsigned char)std::min(G, S + 2 - si - t0);
+        ++tp.ngroups;
+      }
     const int tiles = tp.tiles_m * ((Np + TC_BN - 1) / TC_BN);
-    tp.splits = splits = choose_tc_splits(tiles, tp.nkb, pairs.n, oz.part_elems, (int64_t)Mp * Np, &tp.pair_split);
+    tp.splits = splits =
+        choose_tc_splits(tiles, tp.nkb, tp.ngroups, oz.part_elems, (int64_t)Mp * Np, &tp.pair_split);
     CUtensorMap mapA, mapB;
-    // The B box is min(Np, TC_BN) rows high; a last tile narrower than that reads rows past
-    // its slice (the next slice, or the buffer's spare rows: the allocation holds at least
-    // TC_BN rows) that the MMA never uses, since its N covers only the tile's own columns.
-    tp.b_box_rows = std::min(Np, TC_BN);
+    // The B box is min(Np, TC_BN) rows high (g Np for groups of g); a last tile or group
+    // narrower than that reads rows past its slices (the next slice, the buffer's spare rows:
+    // the allocation holds at least TC_BN rows, or the fill past the map's last row) that
+    // the MMAs never use, since their N covers only the tile's own columns.
+    tp.b_box_rows = G > 1 ? G * Np : std::min(Np, TC_BN);
     const uint64_t b_rows = std::max<uint64_t>((uint64_t)b.S * Np, (uint64_t)TC_BN);
     if ((int64_t)b_rows * Kp > (int64_t)b.S_max * b.Np_max * b.Kp_max) return cudaErrorInvalidValue;
     if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)a.S * Mp, TC_BM) ||

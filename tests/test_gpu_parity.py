@@ -396,10 +396,13 @@ def test_filter_split_matches_oracle(ctx, n, m, slices, tol):
         assert np.max(np.abs(got[:, j] - ref[:, j])) <= tol * max(scale, 1e-300), (j, degs[j])
 
 
-def test_filter_split_single_product_is_exact_to_fp64_level():
+@pytest.mark.parametrize("m", [1, 16, 40, 64, 96, 112])
+def test_filter_split_single_product_is_exact_to_fp64_level(m):
     """One degree-1 step with 8 slices against the FP64 product on random (not Hermitian-
-    structured beyond symmetry) data: error at the level of FP64 rounding of the result."""
-    n, m = 1100, 64   # K = 2n = 2200 spans three exact 1024-term chunks
+    structured beyond symmetry) data: error at the level of FP64 rounding of the result.
+    The widths cover every slice-group size of the tensor-core kernel (7, 3, 3, 2, 1 pairs
+    per A tile, and the ragged last group of each A slice)."""
+    n = 1100   # K = 2n = 2200 spans three exact 960-term chunks
     rng = _rng(99)
     H = _herm(rng, n, 1.0) * np.exp(rng.uniform(-3, 3, (n, 1)))  # rows on different scales
     H = 0.5 * (H + H.conj().T)

@@ -21,6 +21,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -61,7 +62,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: CHFSI_CLOCKS_CSV (with {rank} replaced by the GPU index), else a temp file
+        tmpl = os.environ.get("CHFSI_CLOCKS_CSV")
+        self.path = (tmpl.replace("{rank}", str(gpu_index)) if tmpl else
+                     os.path.join(tempfile.gettempdir(), f"chfsi_clocks_gpu{gpu_index}.csv"))
 
     def start(self):
         try:
@@ -73,6 +77,8 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            if getattr(self, "f", None) is not None:
+                self.f.close()
 
     def stop(self):
         if self.proc is None:

@@ -4,9 +4,9 @@
  * The library solves sequences of correlated generalized Hermitian eigenproblems
  *     A^(l) x = lambda B^(l) x,   l = 1..N                              (Eq. 1, Section 1)
  * for the nev lowest eigenpairs of each problem, with Chebyshev-filtered subspace
- * iteration with locking (Algorithm 1, Section 3), after reduction to standard form
- * B = L L^H, Hs = L^{-1} A L^{-H}, y = L^H x (Section 4.1), each problem warm-started
- * from the Ritz vectors of the previous one (Section 4.1, stages 1-4).
+ * iteration with locking (Algorithm 1, Section 3.1), after reduction to standard form
+ * B = L L^H, Hs = L^{-1} A L^{-H}, y = L^H x (Section 3.2), each problem warm-started
+ * from the Ritz vectors of the previous one (Section 3.2, stages 1-4).
  *
  * Conventions shared by every entry point
  *   - Complex numbers are interleaved complex128 (chfsi_z), matrices column-major with a
@@ -98,7 +98,7 @@ const char* chfsi_last_error(const chfsi_ctx* ctx);
 int chfsi_reset_warm_state(chfsi_ctx* ctx);
 
 /* ---------------------------------------------------------------- solves */
-/* Solve one problem of the sequence (Algorithm 1 with the reduction of Section 4.1).
+/* Solve one problem of the sequence (Algorithm 1 with the reduction of Section 3.2).
  *   A, B   n x n (lower triangles read), leading dimensions lda, ldb.
  *   V0     optional n x blk start block (ld n) used when the context has no warm state;
  *          NULL = SplitMix64 complex Gaussian block.  Ignored when warm state exists.
@@ -116,7 +116,7 @@ int chfsi_solve_next(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda,
                      int32_t blk, int32_t deg, double tol, double* evals, chfsi_z* evecs,
                      chfsi_stats* st);
 
-/* Solve N problems in order, problem l warm-started from problem l-1 (Section 4.1,
+/* Solve N problems in order, problem l warm-started from problem l-1 (Section 3.2,
  * stages 1-4).  A[l], B[l]: pointers to the l-th matrices (ld = ld).  V0 as above for
  * the first problem.  evals: N x nev (row l at evals + l*nev).  evecs: N pointers to
  * n x nev outputs, or NULL.  st: N entries or NULL.  Starts from the context's warm
@@ -131,12 +131,12 @@ int chfsi_solve_sequence(chfsi_ctx* ctx, int32_t N, int64_t n, const chfsi_z* co
  * assemble their own loop.  All run on the context's stream and synchronise it before
  * returning.  Workspace limits of the context apply (n <= n_max, m <= blk_max). */
 
-/* B = L L^H (Section 4.1).  L receives the lower factor, its strict upper part zeroed.
+/* B = L L^H (Section 3.2).  L receives the lower factor, its strict upper part zeroed.
  * Errors: ENOTPD (message names the failing pivot), EINVAL. */
 int chfsi_cholesky(chfsi_ctx* ctx, int64_t n, const chfsi_z* B, int64_t ldb, chfsi_z* L,
                    int64_t ldl);
 
-/* Hs = L^{-1} A L^{-H}, exactly Hermitian in full storage (Section 4.1).  L lower.  With
+/* Hs = L^{-1} A L^{-H}, exactly Hermitian in full storage (Section 3.2).  L lower.  With
  * precision 1 the two products run as 8-slice split-BF16 tensor-core products (error about
  * 1e-17 relative to the operands' row and column scales, below the FP64 GEMM bound); with
  * precision 0 in FP64. */
@@ -266,7 +266,7 @@ const char* chfsi_batch_last_error(const chfsi_batch* batch);
  * leading dimension ld[s], host or device as in chfsi_solve_next), outputs evals[s]
  * (N x nev[s], host), evecs[s*N + l] (n[s] x nev[s], or evecs == NULL) and st[s*N + l] (or
  * st == NULL).  Every sequence starts cold (each worker resets its warm state) and
- * problem l of a sequence is warm-started from problem l-1 (Section 4.1).  deg, tol as in
+ * problem l of a sequence is warm-started from problem l-1 (Section 3.2).  deg, tol as in
  * chfsi_solve_next.  Returns the first failing sequence's status (message in
  * chfsi_batch_last_error); sequences not yet started are then skipped. */
 int chfsi_batch_solve(chfsi_batch* batch, int32_t K, int32_t N, const int64_t* n, const int32_t* nev,
@@ -276,7 +276,7 @@ int chfsi_batch_solve(chfsi_batch* batch, int32_t K, int32_t N, const int64_t* n
 
 /* ---------------------------------------------------------------- learned degree model */
 /* Not in the paper: a learned form of the adaptive per-vector degree (the degree / block
- * size trade-off of Section 3).  The closed-form rule assumes a degree-d filter reduces the
+ * size trade-off of Section 3.1).  The closed-form rule assumes a degree-d filter reduces the
  * residual of Ritz vector i by rho_i^d, rho_i = exp(acosh|t_i|), t_i = (theta_i - c)/e.  The
  * model predicts a correction g(x) of that rate, rate_i = ln(rho_i) exp(g(x_i)), from
  * x = [acosh|t_i|, log10(r_i/tau), i/m, log10(max(gap_i/e, 1e-12))] (gap_i = theta_{i+1} -

@@ -10,7 +10,7 @@ Two parts:
 
 * The *definition* (``definition_eigenpairs``): the nev lowest eigenpairs of the pencil
   A x = lam B x with B-orthonormal eigenvectors (Eq. 1, Section 1), via LAPACK.
-* The *algorithm* (``chfsi_solve``): reduction to standard form (Section 4.1), a
+* The *algorithm* (``chfsi_solve``): reduction to standard form (Section 3.2), a
   Lanczos upper bound, the Chebyshev filter, re-orthonormalisation, Rayleigh-Ritz and
   contiguous-prefix locking, in the order of Algorithm 1.  Where the paper leaves a step
   unspecified, each function names the reading it implements (readings R1-R14 below).
@@ -33,7 +33,7 @@ Readings of points the paper leaves open (same numbering in the design notes):
       a = theta_1 + (b - theta_1) * blk / n.
   R7  Locking test: standard residual ||Hs y - theta y|| / ||y|| < tau with
       tau = tol * max(|a0|, |b|) / 4 (absolute residuals scaled by the norm estimate, as the
-      footnote of Section 4.2 allows).  Acceptance: the generalized residual
+      footnote of Section 3.3 allows).  Acceptance: the generalized residual
       ||A x - lam B x|| / (||A||_est ||x||) <= tol for every output pair; otherwise tau is
       divided by 10, all pairs are unlocked, and iteration continues (at most 3 times).
   R8  Adaptive degree (not in the paper): d_i = clamp(ceil(ln(r_i / tau) / ln rho_i),
@@ -119,7 +119,7 @@ def definition_eigenpairs(A: np.ndarray, B: np.ndarray, nev: int):
 
 
 # --------------------------------------------------------------------------------------
-# Reduction to standard form (Section 4.1): B = L L^H, Hs = L^{-1} A L^{-H}, y = L^H x.
+# Reduction to standard form (Section 3.2): B = L L^H, Hs = L^{-1} A L^{-H}, y = L^H x.
 # --------------------------------------------------------------------------------------
 def cholesky_lower(B: np.ndarray) -> np.ndarray:
     return np.linalg.cholesky(hermitian_from_lower(B))

@@ -1,7 +1,7 @@
 // ChFSI engine and C ABI: context and workspace, reduction to standard form, Lanczos
 // bound, Chebyshev filter, re-orthonormalisation, Rayleigh-Ritz, locking, and the
 // sequence driver with warm starts (Algorithm 1 of Di Napoli & Berljafa, arXiv:1206.3768,
-// with the reduction of Section 4.1).
+// with the reduction of Section 3.2).
 //
 // All arithmetic runs in the kernels of gemm.cu, small.cu and vec.cu on the context's
 // stream.  The host only sequences launches and reads back, once per filter loop, the

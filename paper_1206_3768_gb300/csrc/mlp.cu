@@ -1,5 +1,5 @@
 // Learned per-vector filter degree (an addition to the paper: the adaptive degree of its
-// Section 3 trade-off between block size and degree, learned from the solver's own logs).
+// Section 3.1 trade-off between block size and degree, learned from the solver's own logs).
 //
 // The closed-form rule assumes that a degree-d filter reduces the residual of Ritz vector i
 // by rho_i^d, rho_i = exp(acosh|t_i|).  The model predicts a correction g(x) to that rate,

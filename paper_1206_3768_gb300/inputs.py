@@ -10,7 +10,7 @@ structure and a *planted* spectrum, so that every problem has a known exact answ
 
 so the pencil A^(l) x = lam B x (Eq. 1, Section 1) has eigenvalues lam_l and
 B-orthonormal eigenvectors X_l = L^{-H} Q_l.  Correlation between neighbouring problems
-(the property of Section 2.2, Eq. 4) is emulated by a small unitary rotation of the
+(the property of Section 2.2, Eq. 9) is emulated by a small unitary rotation of the
 eigenvectors and a small drift of the eigenvalues:
 
     Q_l = Q_{l-1} expm(i eps_l K_l),  K_l = (G + G^H) / (2 sqrt(n)),  eps_l = 1e-2 * 0.5**l

@@ -71,7 +71,7 @@ def test_hermitian_from_lower_uses_lower_triangle_only():
     assert np.allclose(O.hermitian_from_lower(M2), H)
 
 
-# ---------------------------------------------------------------- reduction (Section 4.1)
+# ---------------------------------------------------------------- reduction (Section 3.2)
 def test_reduction_invariants_and_planted_spectrum():
     seq = _small_problem(n=80)
     p = seq.problems[0]

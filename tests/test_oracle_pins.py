@@ -408,3 +408,73 @@ def test_deviation_angles_decrease_along_planted_sequence():
         th, _ = O.deviation_angles(P0.X.numpy()[:, :6], P1.X.numpy()[:, :6], P1.B.numpy())
         means.append(float(np.mean(th)))
     assert means[0] > means[1] > means[2]
+
+
+def test_associate_is_greedy_not_optimal_assignment():
+    """The association takes the largest remaining |M_ij| first (the reading of the
+    one-to-one association of Section 2.2), which differs from the assignment of largest
+    total weight: here greedy takes (0,0) and then (1,1), the optimum (0,1) and (1,0).
+    Ties go to the smallest row, then the smallest column."""
+    M = np.array([[0.9, 0.8], [0.85, 0.1]])
+    assert list(O.associate(M)) == [0, 1]
+    from scipy.optimize import linear_sum_assignment
+
+    r, c = linear_sum_assignment(-M)
+    assert list(c) == [1, 0]  # the optimum differs
+    # complex entries are compared by modulus; ties broken by position
+    T = np.array([[1.0, 1j], [-1.0, 0.5]])
+    assert list(O.associate(T)) == [0, 1]
+    E = np.ones((3, 3))
+    assert list(O.associate(E)) == [0, 1, 2]
+
+
+def test_scalar_products_of_b_orthonormal_vectors():
+    """M = X_prev^H B X_cur is the identity for a B-orthonormal basis against itself and
+    the B-inner products of planted eigenvectors of two neighbouring problems are close to
+    a permutation of phases (Section 2.2, Eq. 9 with a fixed B)."""
+    rng = np.random.default_rng(34)
+    n, k = 50, 7
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    B = np.eye(n) + 0.1 * (G.conj().T @ G) / n
+    X = _bo_basis(rng, n, k, B)
+    assert np.allclose(O.scalar_products(X, X, B), np.eye(k), atol=1e-12)
+    # the order of the arguments matters: M(Y, X) = M(X, Y)^H
+    Y = _bo_basis(rng, n, k, B)
+    assert np.allclose(O.scalar_products(Y, X, B), O.scalar_products(X, Y, B).conj().T, atol=1e-13)
+    seq = inputs.planted_sequence("c1", n=96, N=2, nev=6, blk=8, device="cpu")
+    X0, X1, B1 = seq.problems[0].X.numpy()[:, :6], seq.problems[1].X.numpy()[:, :6], seq.problems[1].B.numpy()
+    M = O.scalar_products(X0, X1, B1)
+    assert np.all(np.abs(np.diag(M)) > 0.9)  # diagonally dominant (eps_1 = 5e-3 rotations)
+
+
+def test_generalized_residuals_closed_form():
+    """Diagonal pencil: exact eigenpairs give zero; a shifted eigenvalue lam_i + d gives
+    |d| ||B e_i|| / (a_norm ||e_i||) = |d| b_i / a_norm; the columns' scale cancels."""
+    n = 6
+    lam = np.array([-3.0, -1.0, 0.5, 2.0, 4.0, 7.0])
+    bdiag = np.array([1.0, 2.0, 0.5, 3.0, 1.5, 1.0])
+    A = np.diag(lam * bdiag).astype(np.complex128)
+    B = np.diag(bdiag).astype(np.complex128)
+    X = np.eye(n, dtype=np.complex128)[:, :4] * np.array([1.0, 2.0, 1j, -3.0])[None, :]
+    r = O.generalized_residuals(A, B, X, lam[:4], a_norm=10.0)
+    assert np.max(r) < 1e-15
+    d = np.array([1e-3, -2e-4, 0.0, 5e-6])
+    r = O.generalized_residuals(A, B, X, lam[:4] + d, a_norm=10.0)
+    # (lam_i + d) is rounded: an absolute error of a few ulps of lam_i b_i / a_norm
+    assert np.allclose(r, np.abs(d) * bdiag[:4] / 10.0, rtol=1e-9, atol=1e-15)
+
+
+def test_matrix_norm_estimate_is_a_lower_bound_exact_at_full_dimension():
+    """max |Ritz value| of Lanczos: never above ||M||_2; equal to it (up to rounding) when
+    the run spans the whole space; the largest modulus may sit at either end."""
+    rng = np.random.default_rng(35)
+    n = 40
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    for lam in (np.linspace(-9.0, 2.0, n), np.linspace(-1.0, 5.0, n)):
+        M = (Q * lam) @ Q.conj().T
+        M = 0.5 * (M + M.conj().T)
+        true = np.max(np.abs(lam))
+        est = O.matrix_norm_estimate(M, seed=7, k=5)
+        assert est <= true * (1 + 1e-12)
+        assert est > 0.5 * true
+        assert abs(O.matrix_norm_estimate(M, seed=7, k=n) - true) < 1e-10 * true

@@ -513,6 +513,41 @@ def test_solve_n9300_mixed_precision_workload():
         assert float(E.abs().max()) < 1e-10
 
 
+def test_solve_n2600_benchmark_workload_full_size():
+    """The benchmark's n = 2600 workload (nev 100, blk 130, adaptive degree 8-25, cond(B) =
+    1e4) at full size in the benchmark's launch configuration, three problems (cold + two
+    warm): eigenvalues against the planted spectrum and, for the first and last problem,
+    against LAPACK on the host; generalized residuals against a lower bound of ||A||_2
+    (power iteration) and B-orthonormality, computed on the GPU."""
+    seq = inputs.planted_sequence("c2", N=3, device="cuda", keep_vectors=False)
+    n, nev, blk = seq.n, seq.nev, seq.blk
+    As = [cb.fortran(torch.tril(p.A)) for p in seq.problems]
+    Bs = [cb.fortran(torch.tril(p.B)) for p in seq.problems]
+    with cb.Solver(n, blk, deg_min=seq.deg_min, deg_max=seq.deg_max) as s:
+        evals, evecs, stats = cb.chfsi_solve_sequence(s.ctx, As, Bs, nev, blk, seq.deg, seq.tol)
+    scale = max(float(np.max(np.abs(p.lam))) for p in seq.problems)
+    for ell, p in enumerate(seq.problems):
+        lam = evals[ell]
+        assert stats[ell]["converged"] == nev
+        assert np.max(np.abs(lam.numpy() - p.lam[:nev])) <= 1e-10 * scale
+        if ell in (0, len(seq.problems) - 1):
+            w_def, _ = O.definition_eigenpairs(np.tril(p.A.cpu().numpy()), np.tril(p.B.cpu().numpy()), nev)
+            assert np.max(np.abs(lam.numpy() - w_def)) <= 1e-10 * scale
+        A, B, X = p.A, p.B, evecs[ell]
+        assert stats[ell]["max_resid"] <= seq.tol
+        v = torch.ones(n, 1, dtype=torch.complex128, device=A.device)
+        for _ in range(30):
+            v = A @ v
+            v = v / torch.linalg.vector_norm(v)
+        a_low = float(torch.linalg.vector_norm(A @ v))  # ||A v|| with ||v|| = 1: <= ||A||_2
+        lam_d = lam.to(A.device).to(torch.complex128)
+        R = A @ X - (B @ X) * lam_d[None, :]
+        res = torch.linalg.vector_norm(R, dim=0) / (a_low * torch.linalg.vector_norm(X, dim=0))
+        assert float(res.max()) <= 1e-10, float(res.max())
+        E = X.mH @ (B @ X) - torch.eye(nev, dtype=torch.complex128, device=A.device)
+        assert float(E.abs().max()) < 1e-10
+
+
 def test_batch_uneven_sequences_match_sequential():
     """Five k-point sequences of uneven size solved by a batch of three workers: every
     eigenvalue equals the one-context sequential solve's and the planted spectrum."""

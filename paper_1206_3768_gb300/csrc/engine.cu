@@ -398,11 +398,10 @@ int slices_for_loop(double hs_norm, double tau, double r_min, double a0, double 
   if (t0 > 1.0) T = std::cosh(dmax * std::acosh(t0));
   if (!std::isfinite(T)) T = 1e300;
   const double target = std::max(tau, r_min / (10.0 * T));
-  static double margin = -1.0;
-  if (margin < 0.0) {
+  static const double margin = [] {
     const char* v = std::getenv("CHFSI_SLICE_MARGIN_BITS");
-    margin = v ? std::atof(v) : 6.0;
-  }
+    return v ? std::atof(v) : 6.0;
+  }();
   const double bits = std::log2(hs_norm / target) + margin;
   const int S = (int)std::ceil(bits / 7.0);
   return std::min(s_max, std::max(2, S));

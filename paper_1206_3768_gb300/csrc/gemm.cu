@@ -177,13 +177,12 @@ __global__ void zgemm_k0(const GemmDesc g) {
 }  // namespace
 
 int sm_count() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0;
+  static const int cached = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
-    if (cached <= 0) cached = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   return cached;
 }
 

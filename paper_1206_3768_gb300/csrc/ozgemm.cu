@@ -897,32 +897,31 @@ int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t t
 // ---------------------------------------------------------------------------- host side
 // Product kernel: tcgen05 (default) or the mma.sync kernel, chosen once per process by the
 // environment variable CHFSI_OZ_KERNEL ("tc" or "mma").
+// The choices below are read once (thread-safe static initialisation: batch workers call
+// the product from several host threads).
 bool oz_use_tcgen05() {
-  static int choice = -1;
-  if (choice < 0) {
+  static const bool tc = [] {
     const char* v = std::getenv("CHFSI_OZ_KERNEL");
-    choice = (v && std::strcmp(v, "mma") == 0) ? 0 : 1;
-  }
-  return choice == 1;
+    return !(v && std::strcmp(v, "mma") == 0);
+  }();
+  return tc;
 }
 // Slice groups sharing one A tile per stage (tcgen05 kernel, blocks up to 96 columns wide);
 // CHFSI_OZ_GROUPS=0 issues one pair per stage instead.
 static bool oz_grouped_pairs() {
-  static int choice = -1;
-  if (choice < 0) {
+  static const bool grouped = [] {
     const char* v = std::getenv("CHFSI_OZ_GROUPS");
-    choice = (v && std::strcmp(v, "0") == 0) ? 0 : 1;
-  }
-  return choice == 1;
+    return !(v && std::strcmp(v, "0") == 0);
+  }();
+  return grouped;
 }
 // Smallest TMA ring a slice group may leave (its B box grows with the group): environment
 // variable CHFSI_OZ_GROUP_MIN_STAGES, default 4, clamped to [2, TC_MAX_STAGES].
 static int oz_group_min_stages() {
-  static int v = -1;
-  if (v < 0) {
+  static const int v = [] {
     const char* e = std::getenv("CHFSI_OZ_GROUP_MIN_STAGES");
-    v = e ? std::max(2, std::min(TC_MAX_STAGES, std::atoi(e))) : 4;
-  }
+    return e ? std::max(2, std::min(TC_MAX_STAGES, std::atoi(e))) : 4;
+  }();
   return v;
 }
 
@@ -1081,13 +1080,10 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     const int b_stage = tp.b_box_rows * TC_BK * 2;
     tp.stages = std::min(TC_MAX_STAGES, TC_SMEM_BUDGET / (TC_A_BYTES + b_stage));
     const size_t smem = 1024 + (size_t)tp.stages * (TC_A_BYTES + b_stage) + 256;
-    static bool tc_attr = false;
-    if (!tc_attr) {
-      e = cudaFuncSetAttribute(oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               1024 + TC_SMEM_BUDGET + 256);
-      if (e != cudaSuccess) return e;
-      tc_attr = true;
-    }
+    // once per process (the library drives one device per process)
+    static const cudaError_t tc_attr = cudaFuncSetAttribute(
+        oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 + TC_SMEM_BUDGET + 256);
+    if (tc_attr != cudaSuccess) return tc_attr;
     if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
     oz_gemm_tc_kernel<<<dim3(tiles, splits), TC_THREADS, smem, s>>>(mapA, mapB, tp);
     CHFSI_COUNT_LAUNCH();
@@ -1112,12 +1108,9 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     p.splits = splits = choose_oz_splits(tiles, p.pairs.n * p.nkb, oz.part_elems, (int64_t)Mp * Np);
     p.part = oz.part;
     const size_t smem = (size_t)OZ_STAGES * (OZ_BM + OZ_BN) * OZ_BK * 2;
-    static bool attr_set = false;
-    if (!attr_set) {
-      e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
+    static const cudaError_t mma_attr =
+        cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (mma_attr != cudaSuccess) return mma_attr;
     if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
     oz_gemm_kernel<<<dim3(tiles, p.splits), OZ_THREADS, smem, s>>>(p);
     CHFSI_COUNT_LAUNCH();

@@ -598,13 +598,10 @@ cudaError_t qr_pass(const zd* G, int64_t ldg, int m, zd* T, int64_t ldt, double*
                     int* flags, int* status, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   const size_t smem = (m <= QR_SMEM_MMAX) ? sizeof(float2) * ((size_t)m * m + 32 * (size_t)m) : 0;
-  static bool attr = false;
-  if (!attr) {
-    const size_t mx = sizeof(float2) * ((size_t)QR_SMEM_MMAX * QR_SMEM_MMAX + 32 * (size_t)QR_SMEM_MMAX);
-    cudaError_t e = cudaFuncSetAttribute(qr_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      qr_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(sizeof(float2) * ((size_t)QR_SMEM_MMAX * QR_SMEM_MMAX + 32 * (size_t)QR_SMEM_MMAX)));
+  if (attr != cudaSuccess) return attr;
   qr_pass_kernel<<<1, QR_THREADS, smem, s>>>(G, ldg, m, T, ldt, dscale, static_cast<float2*>(scratch), flags,
                                              status);
   CHFSI_COUNT_LAUNCH();

@@ -478,3 +478,50 @@ def test_matrix_norm_estimate_is_a_lower_bound_exact_at_full_dimension():
         assert est <= true * (1 + 1e-12)
         assert est > 0.5 * true
         assert abs(O.matrix_norm_estimate(M, seed=7, k=n) - true) < 1e-10 * true
+
+
+# ---------------------------------------------------------------------------- degenerate cases
+def test_repeated_problem_warm_start_converges_in_one_loop():
+    """Problem 2 identical to problem 1: the carried Ritz vectors are its eigenvectors, so one
+    filter loop locks every wanted pair (fixed and adaptive degree)."""
+    p = _small_problem(n=96, nev=6, blk=10).problems[0]
+    A, B = np.tril(p.A.numpy()), np.tril(p.B.numpy())
+    for deg in (10, 0):
+        out = O.chfsi_solve_sequence([A, A], [B, B], 6, 10, 1e-10, deg=deg)
+        assert out[1][2].loops == 1
+        for lam, _, _ in out:
+            assert np.max(np.abs(lam - p.lam[:6])) < 1e-12
+
+
+def test_block_spanning_the_whole_space_is_exact_in_one_loop():
+    """blk = n: the subspace is the whole space, Rayleigh-Ritz is the full eigensolver."""
+    n = 12
+    rng = np.random.default_rng(36)
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    H = 0.5 * (G + G.conj().T)
+    lam, X, _, st = O.chfsi_solve(np.tril(H), np.eye(n, dtype=np.complex128), 5, n, 1e-10, deg=6)
+    assert st.loops == 1
+    assert np.max(np.abs(lam - np.linalg.eigvalsh(H)[:5])) < 1e-12
+
+
+def test_identity_overlap_reduces_to_the_standard_problem():
+    p = _small_problem(n=96, nev=6, blk=10).problems[0]
+    A = np.tril(p.A.numpy())
+    lam, X, _, st = O.chfsi_solve(A, np.eye(96, dtype=np.complex128), 6, 10, 1e-10, deg=10)
+    w, V = sla.eigh(O.hermitian_from_lower(A), subset_by_index=[0, 5])
+    assert np.max(np.abs(lam - w)) < 1e-12 * max(1.0, np.max(np.abs(w)))
+    # eigenvectors up to phase: |<v_i, x_i>| = 1
+    assert np.allclose(np.abs(np.sum(V.conj() * X, axis=0)), 1.0, atol=1e-9)
+
+
+def test_unconverged_run_reports_only_the_locked_prefix():
+    """blk = nev leaves the nev-th wanted value at the edge of the damped interval (a = the
+    largest Ritz value), where the filter does not separate it: within the loop limit the
+    run locks a prefix, reports those values exactly and NaN for the rest."""
+    p = _small_problem(n=96, nev=6, blk=10).problems[0]
+    A, B = np.tril(p.A.numpy()), np.tril(p.B.numpy())
+    lam, X, _, st = O.chfsi_solve(A, B, 8, 8, 1e-10, deg=10, max_loops=20)
+    done = np.isfinite(lam)
+    assert st.loops == 20 and 0 < done.sum() < 8
+    assert np.all(done[: done.sum()])  # a contiguous prefix
+    assert np.max(np.abs(lam[done] - p.lam[: done.sum()])) < 1e-12

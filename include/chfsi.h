@@ -21,6 +21,14 @@
  *     available from chfsi_last_error(ctx).  No entry point aborts the process.
  *   - One context serves one host thread at a time; all work is queued on the
  *     context's CUDA stream and the solve entry points return after it has finished.
+ *
+ * Environment variables (read once per process; none is needed for normal use)
+ *   CHFSI_OZ_KERNEL=mma            digit products on the mma.sync kernel instead of tcgen05
+ *   CHFSI_OZ_GROUPS=0              one slice pair per stage in the tcgen05 kernel (default:
+ *                                  slice groups sharing one A tile, blocks <= 96 columns)
+ *   CHFSI_OZ_GROUP_MIN_STAGES=k    smallest TMA ring a slice group may leave (default 4)
+ *   CHFSI_SLICE_MARGIN_BITS=b      safety margin of the filter's per-loop slice count
+ *                                  (default 6 bits)
  */
 #ifndef CHFSI_H
 #define CHFSI_H
@@ -54,8 +62,12 @@ typedef struct {
   int32_t lanczos_k_warm;   /* Lanczos steps for the spectral upper bound, warm start */
   int32_t lanczos_k_cold;   /* ... cold start */
   int32_t reuse_factor;     /* 1: reuse L when B is bitwise equal to the previous B */
-  int32_t precision;        /* filter products: 0 = FP64, 1 = split-BF16 tensor-core digits
-                               (mixed precision; Rayleigh-Ritz and residuals stay FP64) */
+  int32_t precision;        /* 0 = FP64 throughout; 1 (default) = mixed: the filter products
+                               as split-BF16 tensor-core digit products with an accuracy
+                               chosen per loop, the other large products (reduction,
+                               Rayleigh-Ritz, re-orthonormalisation, back-transform) as
+                               digit products with FP64-level results, the small
+                               eigensolver, residuals and small products in FP64 */
   int32_t slices_max;       /* most digit slices per operand in mixed mode (2..8, default 7) */
   uint64_t seed;            /* SplitMix64 seed of the Lanczos start vector / cold block */
   void* cuda_stream;        /* cudaStream_t to run on (cudaStreamLegacy for the legacy default

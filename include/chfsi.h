@@ -101,7 +101,10 @@ typedef struct {
 void chfsi_default_opts(chfsi_opts* opts);
 
 /* Create a context able to solve problems with n <= n_max and blk <= blk_max; allocates
- * all device workspace (about 6 n_max^2 + 12 n_max blk_max complex entries).
+ * all device workspace: six n_max x n_max complex matrices, bf16 digit-slice buffers (two
+ * of 8 slices of the 2 n_max x 2 n_max real embedding, one of 8 slices of up to n_max
+ * columns), split-K partials and about 12 n_max blk_max complex entries: about 2.0 GB at
+ * n_max = 2600, blk_max = 130.
  * opts may be NULL (defaults).  Errors: EINVAL, ENOMEM, ECUDA. */
 int chfsi_create(chfsi_ctx** out, int64_t n_max, int32_t blk_max, const chfsi_opts* opts);
 void chfsi_destroy(chfsi_ctx* ctx);
@@ -173,7 +176,7 @@ int chfsi_filter(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t
 
 /* The same filter with split-BF16 tensor-core products (mixed-precision filter): every
  * product Hs*Y is computed from `slices` 7-bit digit slices of each FP64 operand (power-of-
- * two scales per row of H and per column of Y), exact in FP32 per 1024-term chunk, combined
+ * two scales per row of H and per column of Y), exact in FP32 per 960-term chunk, combined
  * in double-float; relative error about 2^(-7 slices) of the operands' scales.
  * slices in [1, 8].  H must be Hermitian (full storage). */
 int chfsi_filter_split(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, int64_t ldh,

@@ -46,7 +46,7 @@ typedef enum {
   CHFSI_OK = 0,
   CHFSI_EINVAL = 1,    /* bad sizes (blk < nev, blk > n, n > n_max, ...), NULL, NaN input */
   CHFSI_ENOTPD = 2,    /* B (or a Gram matrix beyond repair) is not positive definite */
-  CHFSI_ENOCONV = 3,   /* max_loops reached: locked prefix returned, the rest NaN */
+  CHFSI_ENOCONV = 3,   /* not converged within max_loops, or residual check failed (see solve) */
   CHFSI_ECUDA = 4,     /* a CUDA runtime call failed */
   CHFSI_ETIMEOUT = 5,  /* a bounded device-side wait expired (kernel returned early) */
   CHFSI_ENOMEM = 6     /* workspace allocation failed */
@@ -124,8 +124,12 @@ int chfsi_reset_warm_state(chfsi_ctx* ctx);
  *   st     optional statistics (host).
  * The Ritz vectors (all blk of them, in x-coordinates) and the bounds are kept in the
  * context as the warm start of the next call.
- * Errors: EINVAL, ENOTPD, ENOCONV (partial: evals of the locked prefix, rest NaN),
- *         ECUDA, ETIMEOUT. */
+ * Errors: EINVAL, ENOTPD, ECUDA, ETIMEOUT, and ENOCONV in two cases: max_loops reached
+ *         with fewer than nev pairs locked (evals of the locked prefix, the rest NaN;
+ *         st->max_resid NaN), or all nev pairs locked but their generalized residual
+ *         st->max_resid still above tol after three tightenings of the locking threshold
+ *         (all nev evals and evecs returned).  In both cases the context's warm state is
+ *         updated from the returned vectors and the context stays usable. */
 int chfsi_solve_next(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda,
                      const chfsi_z* B, int64_t ldb, const chfsi_z* V0, int32_t nev,
                      int32_t blk, int32_t deg, double tol, double* evals, chfsi_z* evecs,
@@ -245,15 +249,27 @@ int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double*
  * until the process exits, so m is limited to CHFSI_HEEV_NOALLOC_MAX.
  *   cuda_stream  cudaStream_t to run on (NULL = the legacy default stream); the call
  *                synchronises it before returning.
- * All calls share the one array: calls that overlap on the GPU (several streams or host
+ * All calls share the one array, which keeps the last call's contents (each call clears
+ * what must start at zero): calls that overlap on the GPU (several streams or host
  * threads at once) race and must be serialised by the caller.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.
+ * current) and keeps it for that device's context; the first call after the context was
+ * reset (cudaDeviceReset) looks it up again.  Make the first call on a device before any
+ * stream capture.  Works on the current device; G, w and V must live on it.
  * Errors: EINVAL (m > CHFSI_HEEV_NOALLOC_MAX, m <= 0, NULL, ld < m), ECUDA, ETIMEOUT,
  *         ENOCONV. */
 #define CHFSI_HEEV_NOALLOC_MAX 128
 int chfsi_heev_noalloc(int32_t m, const chfsi_z* G, int64_t ldg, double* w, chfsi_z* V,
                        int64_t ldv, void* cuda_stream);
+
+/* Bound on the device-side waits of this context's kernels, in polls: the grid barriers of
+ * the Rayleigh-Ritz eigensolver and the mbarrier waits of the split-BF16 product kernel
+ * (not in the paper).  Every such wait is bounded; one that runs out sets a status flag,
+ * the kernel unwinds (letting its own copies and tensor-core operations finish first) and
+ * returns, and the call reports CHFSI_ETIMEOUT with the context still usable.  0 (the
+ * default) means a few seconds of polling, far above any normal wait; a small bound makes
+ * the waits run out, which is how the timeout path is exercised.  Errors: EINVAL. */
+int chfsi_set_wait_limit(chfsi_ctx* ctx, int64_t polls);
 
 /* Complex FP64 GEMM used by every dense step, exposed for testing:
  * C <- alpha op(A) op(B) + beta C, op = 'N' (as stored) or 'C' (conjugate transpose);

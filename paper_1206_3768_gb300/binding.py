@@ -113,6 +113,7 @@ _SIGS = {
     "chfsi_deviation_angles": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P, c_int64, _P, c_int64,
                                          _P, _P]),
     "chfsi_heev_noalloc": (c_int32, [c_int32, _P, c_int64, _P, _P, c_int64, _P]),
+    "chfsi_set_wait_limit": (c_int32, [_P, c_int64]),
     "chfsi_zgemm": (c_int32, [_P, c_char, c_char, c_int32, c_int32, c_int32, c_double, _P, c_int64,
                               _P, c_int64, c_double, _P, c_int64]),
 }
@@ -378,18 +379,30 @@ def chfsi_heev(ctx, G: torch.Tensor):
     return w, V
 
 
+def chfsi_set_wait_limit(ctx, polls: int):
+    _check(ctx, load().chfsi_set_wait_limit(ctx, int(polls)))
+
+
 HEEV_NOALLOC_MAX = 128
 
 
 def chfsi_heev_noalloc(G: torch.Tensor, stream=None):
     """Eigen-decomposition without a context or any device allocation by the library
-    (scratch in a fixed device array; m <= 128).  Output buffers come from the caller."""
+    (scratch in a fixed device array; m <= 128).  The output tensors are allocated here by
+    torch, as a caller of the C entry point would provide them.  The library works on the
+    current device, so the call is made with G's device current and, by default, on that
+    device's current torch stream."""
+    if not (isinstance(G, torch.Tensor) and G.is_cuda and G.dtype == torch.complex128
+            and G.dim() == 2 and G.shape[0] == G.shape[1]):
+        raise ValueError("G must be a square complex128 CUDA tensor")
     m = G.shape[0]
-    Gf = fortran(G)
-    w = torch.empty(m, dtype=torch.float64, device=G.device)
-    V = fortran_empty(m, m, G.device)
-    s = ctypes.c_void_p(_stream_handle(stream))
-    rc = load().chfsi_heev_noalloc(m, _ptr(Gf), _ld(Gf), _ptr(w), _ptr(V), _ld(V), s)
+    with torch.cuda.device(G.device):
+        Gf = fortran(G)
+        w = torch.empty(m, dtype=torch.float64, device=G.device)
+        V = fortran_empty(m, m, G.device)
+        s = ctypes.c_void_p(_stream_handle(stream if stream is not None
+                                           else torch.cuda.current_stream(G.device)))
+        rc = load().chfsi_heev_noalloc(m, _ptr(Gf), _ld(Gf), _ptr(w), _ptr(V), _ld(V), s)
     if rc != CHFSI_OK:
         raise ChfsiError(rc, f"chfsi_heev_noalloc(m={m}) failed")
     return w, V

@@ -497,7 +497,8 @@ int rayleigh_ritz_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, 
   CK(mirror_lower(ws.G, ldm, m, ctx->stream));
   {
     PhaseScope ps(ctx, PH_EIG);
-    CK(jacobi_heev(ws.G, ldm, m, theta, ws.V, ldm, ws.jac, ws.barrier, ws.status, ctx->stream));
+    CK(jacobi_heev(ws.G, ldm, m, theta, ws.V, ldm, ws.jac, ws.barrier, ws.status, ctx->stream,
+                   ws.wait_limit));
   }
   CKS(gemm_auto(ctx, gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld)));
   CKS(gemm_auto(ctx, gd(n, m, m, *W, ld, OPN, ws.V, ldm, OPN, *Zb, ld)));
@@ -800,7 +801,15 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
     std::vector<double> gr(nev);
     CKS(read_back(ctx, gr.data(), ws.gres, nev));
     max_gres = *std::max_element(gr.begin(), gr.end());
-    if (max_gres <= S.tol || accept == 3) break;
+    if (max_gres <= S.tol) break;
+    if (accept == 3) {
+      // every wanted pair is locked, but the generalized residual stays above tol after the
+      // last tightening of the locking threshold: the pairs are returned, flagged
+      status = set_err(ctx, CHFSI_ENOCONV,
+                       "generalized residual %.3e above tol %.3e after %d tightened locking rounds",
+                       max_gres, S.tol, st.accept_rounds);
+      break;
+    }
     // Tighten the locking threshold and iterate again on all blk columns.
     st.accept_rounds++;
     tau /= 10.0;
@@ -1153,6 +1162,7 @@ int chfsi_filter_split(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, i
   std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return degrees[x] > degrees[y]; });
   std::vector<int> ds(m), inv(m);
   for (int r = 0; r < m; ++r) { ds[r] = degrees[idx[r]]; inv[idx[r]] = r; }
+  CKS(reset_status(ctx));
   CK(oz_slice_hermitian(Z(H), ldh, (int)n, slices, ws.oz, ctx->stream));
   CK(cudaMemcpy2DAsync(ws.Y0, ld * sizeof(zd), Y, ldy * sizeof(zd), n * sizeof(zd), m,
                        cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1164,6 +1174,13 @@ int chfsi_filter_split(chfsi_ctx* ctx, int64_t n, int32_t m, const chfsi_z* H, i
   CK(cudaMemcpy2DAsync(Y, ldy * sizeof(zd), Yb, ld * sizeof(zd), n * sizeof(zd), m,
                        cudaMemcpyDeviceToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx, "chfsi_filter_split");
+}
+
+int chfsi_set_wait_limit(chfsi_ctx* ctx, int64_t polls) {
+  if (!ctx || polls < 0) return set_err(ctx, CHFSI_EINVAL, "polls must be >= 0");
+  ctx->ws.wait_limit = polls;
+  ctx->ws.oz.wait_limit = polls;
   return CHFSI_OK;
 }
 
@@ -1333,7 +1350,7 @@ int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double*
   cudaSetDevice(ctx->ws.dev);
   CKS(reset_status(ctx));
   CK(jacobi_heev(Z(G), ldg, m, w, Z(V), ldv, ctx->ws.jac, ctx->ws.barrier, ctx->ws.status,
-                 ctx->stream));
+                 ctx->stream, ctx->ws.wait_limit));
   CK(cudaStreamSynchronize(ctx->stream));
   return check_status(ctx, "chfsi_heev");
 }

@@ -91,9 +91,12 @@ cudaError_t scale_cols_flag(zd* Y, int64_t ldy, int n, int m, const double* d, c
 // T = D X^H (upper triangular, zero below): the right factor of Cholesky QR, Q = Y T.
 cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* T, int64_t ldt,
                      cudaStream_t s);
-// Jacobi eigensolver (cooperative multi-CTA).  G not modified.  work: 2*m'*m' + barrier.
+// Jacobi eigensolver (cooperative multi-CTA).  G not modified.  work: 3*m'*m' (m' = m
+// rounded up to even), barrier: 4 words.  spin_limit: polls of a grid-barrier wait before it
+// gives up (0: the default of a few seconds).
 cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64_t ldv,
-                        zd* work, unsigned* barrier, int* status, cudaStream_t s);
+                        zd* work, unsigned* barrier, int* status, cudaStream_t s,
+                        long long spin_limit = 0);
 
 // Deviation angles (Section 2.2, Fig. 1): B-norms of columns from W = B X; greedy
 // one-to-one association from |M|; the B-orthogonal parts R of the associated current
@@ -182,6 +185,7 @@ struct OzWorkspace {
   double* part = nullptr;           // split-K partial sums
   size_t part_elems = 0;
   int* status = nullptr;            // device status word for bounded-wait timeouts
+  long long wait_limit = 0;         // polls of a first-level mbarrier wait (0: the default)
 };
 bool oz_use_tcgen05();
 int oz_padded_k(int n);
@@ -234,6 +238,7 @@ struct Workspace {
   int *deg = nullptr, *perm = nullptr, *degs = nullptr, *flag = nullptr, *ilist = nullptr;
   int* status = nullptr;  // [0]: DEV_* flags, [1]: first failing pivot
   int* shiftflag = nullptr;  // set when a Cholesky QR pass needed the shifted retry
+  long long wait_limit = 0;  // polls of the eigensolver's grid-barrier waits (0: the default)
   unsigned* barrier = nullptr;
   // split-K partials
   zd* splitk = nullptr;

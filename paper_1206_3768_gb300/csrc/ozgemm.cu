@@ -306,6 +306,7 @@ struct TcParams {
   unsigned char gs[OZ_MAX_PAIRS], gt[OZ_MAX_PAIRS], gc[OZ_MAX_PAIRS];  // group: s, first t, size
   double* part;
   int* status;
+  long long spin_limit;                      // polls before a first-level wait gives up
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -331,10 +332,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // The single-thread producer and MMA roles spin without back-off (their waits sit on the
 // critical path); the drain warps back off after a while.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status, bool backoff = false) {
-  long it = 0;
+                                          int* status, long long limit, bool backoff = false) {
+  long long it = 0;
   while (!mbar_try(bar, parity)) {
-    if (++it > kMbarSpinLimit) {
+    if (++it > limit) {
       *abort_flag = 1;
       atomicOr(status, DEV_TIMEOUT);
       return false;
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int arow = p.gs[pr] * p.Mp + m0, brow = p.gt[pr] * p.Np + n0;
           for (int kb = k0; kb < k1; ++kb, ++i) {
             const uint32_t fb = full0 + 8 * stage;
-            if (i >= NS && !mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status)) {
+            if (i >= NS && !mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status, p.spin_limit)) {
               stop = true;
               break;
             }
@@ -513,7 +514,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
         for (int pr = pr_lo; pr < pr_hi && !stop; ++pr, ++chunk) {
           // accumulator chunk & 1 is free once the drain has finished chunk - 2
-          if (chunk >= 2 && !mbar_wait(acce0 + 8 * (chunk & 1), ((chunk >> 1) - 1) & 1, abort_flag, p.status)) {
+          if (chunk >= 2 && !mbar_wait(acce0 + 8 * (chunk & 1), ((chunk >> 1) - 1) & 1, abort_flag, p.status,
+                                     p.spin_limit)) {
             stop = true;
             break;
           }
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t d = tmem + (uint32_t)(chunk & 1) * (uint32_t)G * acc_stride;
           const int gc = p.gc[pr];
           for (int kb = k0; kb < k1; ++kb) {
-            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.status)) {
+            if (!mbar_wait(full0 + 8 * stage, phase, abort_flag, p.status, p.spin_limit)) {
               stop = true;
               break;
             }
@@ -579,7 +581,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nchunks = (kb_hi > kb_lo && npr > 0) ? ((kb_hi - kb_lo + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB) * npr : 0;
     for (; chunk < nchunks && ok; ++chunk) {
       const int b = chunk & 1;
-      if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status, true)) { ok = false; break; }
+      if (!mbar_wait(accf0 + 8 * b, (chunk >> 1) & 1, abort_flag, p.status, p.spin_limit, true)) { ok = false; break; }
       tc_fence_after();
       const int pr = pr_lo + chunk % npr;
       const int gc = p.gc[pr];
@@ -1043,6 +1045,9 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     tp.n_real = m;
     tp.part = oz.part;
     tp.status = oz.status;
+    // first-level waits: the context's bound (a test hook) or the default; the waits that
+    // let issued copies and MMAs finish after an abort always use the default
+    tp.spin_limit = oz.wait_limit > 0 ? oz.wait_limit : kMbarSpinLimit;
     // group size (see the kernel's header): tensor memory holds 2 g accumulators of the
     // block's width rounded up to 32 columns plus the high words, the B box is at most 256
     // rows, and the ring keeps at least oz_group_min_stages() stages

@@ -339,13 +339,14 @@ struct JacParams {
   unsigned* bar;
   int* status;
   int max_sweeps;
+  long long spin_limit;  // polls of a grid-barrier wait before it gives up
 };
 
 constexpr long kBarrierSpinLimit = 8000000;  // polls of an L2 word: a few seconds at most
 
 // Sense-free generation barrier over all CTAs of a cooperative launch.  Returns false (and
 // sets DEV_TIMEOUT) if the wait ran past its limit or another CTA already reported it.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status, long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -359,9 +360,9 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
-      long it = 0;
+      long long it = 0;
       while (*vgen == gen) {
-        if (++it > kBarrierSpinLimit || (*(volatile int*)status & DEV_TIMEOUT)) {
+        if (++it > limit || (*(volatile int*)status & DEV_TIMEOUT)) {
           atomicOr(status, DEV_TIMEOUT);
           ok = 0;
           break;
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) 
   }
   const double thresh = 1e-15 * sqrt(red[0]) + 1e-300;
   __syncthreads();
-  if (!grid_barrier(P.bar, nb, P.status)) return;
+  if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
 
   int parity = 0;
   int sweep = 0;
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) 
         }
       }
       parity ^= 1;
-      if (!grid_barrier(P.bar, nb, P.status)) return;
+      if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
     }
   }
   __syncthreads();
@@ -619,7 +620,7 @@ cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* 
 }
 
 cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64_t ldv, zd* work,
-                        unsigned* barrier, int* status, cudaStream_t s) {
+                        unsigned* barrier, int* status, cudaStream_t s, long long spin_limit) {
   if (m <= 0) return cudaSuccess;
   const int mp = (m + 1) & ~1;
   JacParams P;
@@ -630,6 +631,7 @@ cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64
   P.bar = barrier;
   P.status = status;
   P.max_sweeps = 40;
+  P.spin_limit = spin_limit > 0 ? spin_limit : kBarrierSpinLimit;
   cudaError_t e = cudaMemsetAsync(barrier, 0, 4 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   const int half = mp / 2;

@@ -47,6 +47,37 @@ def test_noalloc_matches_context_heev_on_two_calls_in_a_row():
             _compare(w, V, w_ref, V_ref, G)
 
 
+def test_noalloc_small_and_odd_sizes_after_a_full_size_call():
+    # the array keeps the previous call's contents: a full-size call first, then sizes whose
+    # padded work copies (odd m adds a row and a column) cover only part of it
+    with cb.Solver(256, cb.HEEV_NOALLOC_MAX) as s:
+        for seed, m in ((4, cb.HEEV_NOALLOC_MAX), (5, 1), (6, cb.HEEV_NOALLOC_MAX - 1), (7, 3)):
+            G = _herm(seed, m)
+            w_ref, V_ref = cb.chfsi_heev(s.ctx, G)
+            w, V = cb.chfsi_heev_noalloc(G)
+            _compare(w, V, w_ref, V_ref, G)
+
+
+def test_noalloc_strided_input_and_side_stream():
+    # G as a column-major view with leading dimension above m, on a non-default stream
+    m = 77
+    G = _herm(8, m)
+    big = cb.fortran_empty(m + 9, m, DEV)
+    big.zero_()
+    view = big[:m, :]
+    view.copy_(G)
+    assert view.stride(0) == 1 and view.stride(1) == m + 9
+    side = torch.cuda.Stream(device=DEV)
+    side.wait_stream(torch.cuda.current_stream())
+    with cb.Solver(256, cb.HEEV_NOALLOC_MAX) as s:
+        w_ref, V_ref = cb.chfsi_heev(s.ctx, G)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            w, V = cb.chfsi_heev_noalloc(view)
+        torch.cuda.current_stream().wait_stream(side)
+        _compare(w, V, w_ref, V_ref, G)
+
+
 def test_noalloc_rejects_sizes_beyond_its_array():
     G = _herm(3, cb.HEEV_NOALLOC_MAX + 1)
     with pytest.raises(cb.ChfsiError) as ei:

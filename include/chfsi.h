@@ -309,25 +309,36 @@ int chfsi_batch_solve(chfsi_batch* batch, int32_t K, int32_t N, const int64_t* n
 /* Not in the paper: a learned form of the adaptive per-vector degree (the degree / block
  * size trade-off of Section 3.1).  The closed-form rule assumes a degree-d filter reduces the
  * residual of Ritz vector i by rho_i^d, rho_i = exp(acosh|t_i|), t_i = (theta_i - c)/e.  The
- * model predicts a correction g(x) of that rate, rate_i = ln(rho_i) exp(g(x_i)), from
- * x = [acosh|t_i|, log10(r_i/tau), i/m, log10(max(gap_i/e, 1e-12))] (gap_i = theta_{i+1} -
- * theta_i, e for the last column), x normalised as (x - mean) * scale, with a perceptron
- * 4 -> 64 -> 64 -> 1 (tanh hidden units, linear output); d_i = clamp(ceil(ln(r_i/tau) /
- * rate_i), deg_min, deg_max), g clamped to [-3, 3], the closed form wherever the result is
- * not finite.  The solver evaluates it with FP16 weights. */
-#define CHFSI_MLP_IN 4
+ * model predicts a correction g(x) of that rate, rate_i = ln(rho_i) exp(g(x_i)), and the
+ * degree is d_i = clamp(ceil(ln(r_i/tau) / rate_i), deg_min, deg_max) (g clamped to [-3, 3];
+ * the closed form wherever the result is not finite or no model is installed), from the
+ * CHFSI_MLP_IN inputs of vector i in loop k of a problem:
+ *   x0..x2  log10(r/tau) of the vector now and after the two previous loops (the residual
+ *           history over the last three loops; a missing loop repeats the later value),
+ *   x3, x4  the degrees it was filtered with in the two previous loops (0 where missing),
+ *   x5      its normalised Ritz-value position t_i = (theta_i - c)/e,
+ *   x6      the position t_0 = (a0 - c)/e of the smallest Ritz value a0 of the block,
+ *   x7      the filter-bound ratio (a - a0)/(b - a0),
+ * normalised as (x - mean) * scale, through a perceptron with three hidden layers of
+ * CHFSI_MLP_HID tanh units and a linear output.  "The same vector" in consecutive loops is the
+ * one with the same global index (locked count + active index; locking removes a prefix).
+ * The solver evaluates it with FP16 weights; an untrained model (zero output layer) gives the
+ * closed form exactly. */
+#define CHFSI_MLP_IN 8
 #define CHFSI_MLP_HID 64
-/* trainable parameters (w1 .. b3): 4545 */
+/* trainable parameters (w1 .. b4): 8961 */
 #define CHFSI_MLP_NPARAM                                                                   \
-  (CHFSI_MLP_HID * CHFSI_MLP_IN + CHFSI_MLP_HID + CHFSI_MLP_HID * CHFSI_MLP_HID +          \
-   2 * CHFSI_MLP_HID + 1)
+  (CHFSI_MLP_HID * CHFSI_MLP_IN + CHFSI_MLP_HID + 2 * (CHFSI_MLP_HID * CHFSI_MLP_HID +     \
+   CHFSI_MLP_HID) + CHFSI_MLP_HID + 1)
 typedef struct {
-  float w1[CHFSI_MLP_HID * CHFSI_MLP_IN]; /* row j: weights of hidden unit j of layer 1 */
+  float w1[CHFSI_MLP_HID * CHFSI_MLP_IN];  /* row j: weights of hidden unit j of layer 1 */
   float b1[CHFSI_MLP_HID];
   float w2[CHFSI_MLP_HID * CHFSI_MLP_HID]; /* row j: weights of hidden unit j of layer 2 */
   float b2[CHFSI_MLP_HID];
-  float w3[CHFSI_MLP_HID];
-  float b3;
+  float w3[CHFSI_MLP_HID * CHFSI_MLP_HID]; /* row j: weights of hidden unit j of layer 3 */
+  float b3[CHFSI_MLP_HID];
+  float w4[CHFSI_MLP_HID];                 /* output weights */
+  float b4;
   float mean[CHFSI_MLP_IN], scale[CHFSI_MLP_IN];
 } chfsi_mlp;
 
@@ -336,23 +347,34 @@ typedef struct {
 void chfsi_mlp_init(chfsi_mlp* model, uint64_t seed);
 /* Training: sets mean/scale from X, then `epochs` epochs of Adam (lr, minibatches of
  * `batch`, order shuffled by SplitMix64(seed)) on L = 1/(2n) sum (g(x_k) - z_k)^2, in place
- * on *model.  X: host, n x 4 (row-major), z: host, n.  *loss: mean loss of the last epoch. */
+ * on *model.  X: host, n x CHFSI_MLP_IN (row-major), z: host, n.  *loss: mean loss of the last
+ * epoch. */
 int chfsi_mlp_train(chfsi_ctx* ctx, chfsi_mlp* model, const float* X, const float* z, int64_t n,
                     int32_t epochs, int32_t batch, float lr, uint64_t seed, float* loss);
-/* dL/dparameters over all n samples (host, CHFSI_MLP_NPARAM floats in the order of chfsi_mlp's fields
- * w1 .. b3) and L, for the given model and its mean/scale. */
+/* One epoch of Adam (beta1 0.9, beta2 0.999, eps 1e-8) over the samples in the caller's order
+ * (order: n indices into X, z), minibatches of `batch`, each on the gradient of its own mean
+ * squared error; model (its mean/scale kept), moments m1, m2 (CHFSI_MLP_NPARAM floats each) and
+ * the step counter updated in place (host); *loss = 1/(2n) sum of the epoch's squared errors. */
+int chfsi_mlp_adam_epoch(chfsi_ctx* ctx, chfsi_mlp* model, float* m1, float* m2, int32_t* step,
+                         const float* X, const float* z, const int32_t* order, int64_t n, int32_t batch,
+                         float lr, float* loss);
+/* dL/dparameters over all n samples (host, CHFSI_MLP_NPARAM floats in the order of chfsi_mlp's
+ * fields w1 .. b4) and L, for the given model and its mean/scale. */
 int chfsi_mlp_gradient(chfsi_ctx* ctx, const chfsi_mlp* model, const float* X, const float* z,
                        int64_t n, float* grad, float* loss);
 /* g(x_k) for n host samples (FP32 weights). */
 int chfsi_mlp_predict(chfsi_ctx* ctx, const chfsi_mlp* model, const float* X, int64_t n, float* y);
-/* Install the model for the context's adaptive degrees (NULL: the closed form). */
+/* Install the model for the context's adaptive degrees (NULL: the closed form).  The step
+ * entry point chfsi_degrees evaluates it without residual history (as in a first loop). */
 int chfsi_set_degree_model(chfsi_ctx* ctx, const chfsi_mlp* model);
 
 /* Degree log: from now on, every adaptive filter loop appends one record of
- * CHFSI_DEGREE_LOG_FIELDS doubles per active column, [problem, loop, g, i, m, theta, r,
- * tau, d, c, e, gap] (problem counts solves of the context, g = locked count + i), up to
- * `capacity` records; capacity 0 stops logging and clears it. */
-#define CHFSI_DEGREE_LOG_FIELDS 12
+ * CHFSI_DEGREE_LOG_FIELDS doubles per active column, [problem, loop, g, i, m, theta, r, tau, d,
+ * c, e, r_next, x0 .. x7]: problem counts solves of the context, g = locked count + i, d the
+ * degree the column was filtered with, r_next its residual after the loop's filter and
+ * Rayleigh-Ritz (so that vectors that lock in that loop are logged too), x the model inputs as
+ * the solver computed them; up to `capacity` records; capacity 0 stops logging and clears it. */
+#define CHFSI_DEGREE_LOG_FIELDS 20
 int chfsi_degree_log_start(chfsi_ctx* ctx, int64_t capacity);
 /* Copies up to cap records to out (host) and returns the number of records logged. */
 int64_t chfsi_degree_log_read(chfsi_ctx* ctx, double* out, int64_t cap);

@@ -32,22 +32,33 @@ class ChfsiError(RuntimeError):
         self.code = code
 
 
-MLP_IN, MLP_HID = 4, 64
-MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + 2 * MLP_HID + 1  # 4545
-DEGREE_LOG_FIELDS = 12
+MLP_IN, MLP_HID = 8, 64
+MLP_SIZES = (MLP_IN, MLP_HID, MLP_HID, MLP_HID, 1)
+MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + 2 * (MLP_HID * MLP_HID + MLP_HID) + MLP_HID + 1  # 8961
+DEGREE_LOG_FIELDS = 20
 
 
 class chfsi_mlp(ctypes.Structure):
     _fields_ = [("w1", ctypes.c_float * (MLP_HID * MLP_IN)), ("b1", ctypes.c_float * MLP_HID),
                 ("w2", ctypes.c_float * (MLP_HID * MLP_HID)), ("b2", ctypes.c_float * MLP_HID),
-                ("w3", ctypes.c_float * MLP_HID), ("b3", ctypes.c_float),
+                ("w3", ctypes.c_float * (MLP_HID * MLP_HID)), ("b3", ctypes.c_float * MLP_HID),
+                ("w4", ctypes.c_float * MLP_HID), ("b4", ctypes.c_float),
                 ("mean", ctypes.c_float * MLP_IN), ("scale", ctypes.c_float * MLP_IN)]
 
     def params(self):
-        """The MLP_NPARAM trainable parameters in the order w1, b1, w2, b2, w3, b3 (numpy copy)."""
+        """The MLP_NPARAM trainable parameters in the order w1, b1, .., w4, b4 (numpy copy)."""
         import numpy as np
 
         return np.ctypeslib.as_array((ctypes.c_float * MLP_NPARAM).from_address(ctypes.addressof(self))).copy()
+
+    def set_params(self, p):
+        """Overwrite the trainable parameters from a flat array in the order of params()."""
+        import numpy as np
+
+        a = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        if a.size != MLP_NPARAM:
+            raise ValueError("need MLP_NPARAM parameters")
+        ctypes.memmove(ctypes.addressof(self), a.ctypes.data, 4 * MLP_NPARAM)
 
 
 class chfsi_opts(ctypes.Structure):
@@ -101,6 +112,7 @@ _SIGS = {
     "chfsi_mlp_init": (None, [_P, c_uint64]),
     "chfsi_mlp_train": (c_int32, [_P, _P, _P, _P, c_int64, c_int32, c_int32, ctypes.c_float, c_uint64, _P]),
     "chfsi_mlp_gradient": (c_int32, [_P, _P, _P, _P, c_int64, _P, _P]),
+    "chfsi_mlp_adam_epoch": (c_int32, [_P, _P, _P, _P, _P, _P, _P, _P, c_int64, c_int32, ctypes.c_float, _P]),
     "chfsi_mlp_predict": (c_int32, [_P, _P, _P, c_int64, _P]),
     "chfsi_set_degree_model": (c_int32, [_P, _P]),
     "chfsi_degree_log_start": (c_int32, [_P, c_int64]),
@@ -438,7 +450,8 @@ def chfsi_mlp_init(seed: int = 12063768) -> chfsi_mlp:
 
 def chfsi_mlp_train(ctx, model: chfsi_mlp, X, z, epochs: int, batch: int = 256, lr: float = 1e-3,
                     seed: int = 1) -> float:
-    """Train in place on host data X (n x 4) and targets z (n); returns the last epoch's loss."""
+    """Train in place on host data X (n x MLP_IN) and targets z (n); returns the last epoch's
+    loss."""
     X, z = _f32(X), _f32(z)
     loss = ctypes.c_float()
     _check(ctx, load().chfsi_mlp_train(ctx, ctypes.byref(model), X.ctypes.data, z.ctypes.data, len(z),
@@ -456,6 +469,22 @@ def chfsi_mlp_gradient(ctx, model: chfsi_mlp, X, z):
     _check(ctx, load().chfsi_mlp_gradient(ctx, ctypes.byref(model), X.ctypes.data, z.ctypes.data, len(z),
                                           g.ctypes.data, ctypes.byref(loss)))
     return g, float(loss.value)
+
+
+def chfsi_mlp_adam_epoch(ctx, model: chfsi_mlp, m1, m2, step: int, X, z, order, batch: int, lr: float):
+    """One Adam epoch in the given sample order; model updated in place.  Returns
+    (m1, m2, step, loss) with the updated moments (float32 arrays) and step counter."""
+    import numpy as np
+
+    X, z = _f32(X), _f32(z)
+    m1, m2 = _f32(m1).copy(), _f32(m2).copy()
+    order = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    st = ctypes.c_int32(int(step))
+    loss = ctypes.c_float()
+    _check(ctx, load().chfsi_mlp_adam_epoch(ctx, ctypes.byref(model), m1.ctypes.data, m2.ctypes.data,
+                                            ctypes.byref(st), X.ctypes.data, z.ctypes.data, order.ctypes.data,
+                                            len(z), int(batch), float(lr), ctypes.byref(loss)))
+    return m1, m2, int(st.value), float(loss.value)
 
 
 def chfsi_mlp_predict(ctx, model: chfsi_mlp, X):
@@ -476,8 +505,8 @@ def chfsi_degree_log_start(ctx, capacity: int):
 
 
 def chfsi_degree_log_read(ctx):
-    """All logged records as an array [count, 12]: problem, loop, g, i, m, theta, r, tau, d, c,
-    e, gap."""
+    """All logged records as an array [count, DEGREE_LOG_FIELDS]: problem, loop, g, i, m, theta,
+    r, tau, d, c, e, r_next, x0 .. x7."""
     import numpy as np
 
     lib = load()

@@ -662,6 +662,12 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   int conv = 0;
   int status = CHFSI_OK;
   std::vector<int> degs;
+  std::vector<double> pending_log;  // degree-log records of the current loop
+  if (adaptive) {
+    // the learned degree's per-vector history starts empty for every problem
+    CK(cudaMemsetAsync(ws.hist_r1, 0, 2 * sizeof(double) * ws.blk_max, ctx->stream));
+    CK(cudaMemsetAsync(ws.hist_d1, 0, 2 * sizeof(int) * ws.blk_max, ctx->stream));
+  }
   double max_gres = NAN;
   const double hs_norm = std::max(std::fabs(a0), std::fabs(b_up));
   bool mixed = o.precision == 1;
@@ -673,24 +679,43 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       // ---- a8: degrees
       const int* perm_dev = nullptr;
       degs.assign(m, S.deg);
+      pending_log.clear();
       if (adaptive) {
         if (!have_r) return set_err(ctx, CHFSI_ECUDA, "internal: residuals missing");
+        const bool logging = ctx->deglog_cap > 0 && (int)th.size() == m &&
+                             (int64_t)ctx->deglog.size() / CHFSI_DEGREE_LOG_FIELDS < ctx->deglog_cap;
+        const float* gcorr = nullptr;
+        if (ctx->mlp_on || logging) {
+          CK(degree_features(theta, resid, m, a, b_up, tau, conv, ws.hist_r1, ws.hist_r2, ws.hist_d1,
+                             ws.hist_d2, ws.feat, ctx->stream));
+          if (ctx->mlp_on) {
+            CK(degree_model_eval(ctx->mlp_dev, ws.feat, m, ws.gcorr, ctx->stream));
+            gcorr = ws.gcorr;
+          }
+        }
+        if (logging) {
+          std::vector<float> feat((size_t)m * CHFSI_MLP_IN);
+          CKS(read_back(ctx, feat.data(), ws.feat, feat.size()));
+          const double c = 0.5 * (a + b_up), e = 0.5 * (b_up - a);
+          pending_log.resize((size_t)m * CHFSI_DEGREE_LOG_FIELDS);
+          for (int i = 0; i < m; ++i) {
+            double* rec = pending_log.data() + (size_t)i * CHFSI_DEGREE_LOG_FIELDS;
+            const double head[12] = {(double)ctx->problems_solved, (double)st.loops, (double)(conv + i),
+                                     (double)i, (double)m, th[i], rr[i], tau, 0.0, c, e, NAN};
+            std::copy(head, head + 12, rec);
+            for (int f = 0; f < CHFSI_MLP_IN; ++f) rec[12 + f] = feat[(size_t)i * CHFSI_MLP_IN + f];
+          }
+        }
         CK(degrees_kernel_run(theta, resid, m, a, b_up, tau, o.deg_min, o.deg_max, nev - conv,
-                              ws.deg, ws.perm, ws.degs, ctx->stream, ctx->mlp_on ? ctx->mlp_dev : nullptr));
+                              ws.deg, ws.perm, ws.degs, ctx->stream, gcorr, conv, ws.hist_r1, ws.hist_r2,
+                              ws.hist_d1, ws.hist_d2));
         CKS(read_back(ctx, degs.data(), ws.degs, m));
         perm_dev = ws.perm;
-        if (ctx->deglog_cap > 0 && (int)th.size() == m) {
+        if (logging) {
           // degrees per column (degs holds them in descending order): read them unsorted
           std::vector<int> dcol(m);
           CKS(read_back(ctx, dcol.data(), ws.deg, m));
-          const double c = 0.5 * (a + b_up), e = 0.5 * (b_up - a);
-          for (int i = 0; i < m && (int64_t)ctx->deglog.size() / CHFSI_DEGREE_LOG_FIELDS < ctx->deglog_cap; ++i) {
-            const double gap = (i + 1 < m) ? th[i + 1] - th[i] : e;
-            const double rec[CHFSI_DEGREE_LOG_FIELDS] = {(double)ctx->problems_solved, (double)st.loops,
-                                                         (double)(conv + i), (double)i, (double)m, th[i],
-                                                         rr[i], tau, (double)dcol[i], c, e, gap};
-            ctx->deglog.insert(ctx->deglog.end(), rec, rec + CHFSI_DEGREE_LOG_FIELDS);
-          }
+          for (int i = 0; i < m; ++i) pending_log[(size_t)i * CHFSI_DEGREE_LOG_FIELDS + 8] = dcol[i];
         }
       }
       // ---- a4: filter (split-BF16 tensor-core products in mixed mode)
@@ -748,6 +773,15 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       }
       have_r = true;
       st.loops++;
+      if (!pending_log.empty()) {
+        // the residual each logged column reached after this loop's filter and Rayleigh-Ritz
+        for (int i = 0; i < m; ++i) pending_log[(size_t)i * CHFSI_DEGREE_LOG_FIELDS + 11] = rr[i];
+        const int64_t room = ctx->deglog_cap - (int64_t)ctx->deglog.size() / CHFSI_DEGREE_LOG_FIELDS;
+        const int64_t cnt = std::min<int64_t>(room, m);
+        ctx->deglog.insert(ctx->deglog.end(), pending_log.begin(),
+                           pending_log.begin() + cnt * CHFSI_DEGREE_LOG_FIELDS);
+        pending_log.clear();
+      }
       if (nlock > 0) {
         CK(copy_cols(Ya, ld, ws.YL + (int64_t)conv * ld, ld, n, nlock, ctx->stream));
         CK(cudaMemcpyAsync(ws.lamL + conv, theta, nlock * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -923,6 +957,9 @@ cudaError_t workspace_alloc(Workspace& ws, int64_t n_max, int blk_max, int lancz
   AL(ws.gres, ws.blk_max); AL(ws.dscale, ws.blk_max); AL(ws.scal, 64);
   AL(ws.lal, lanczos_kmax + 1); AL(ws.lbe, lanczos_kmax + 1);
   AL(ws.deg, ws.blk_max); AL(ws.perm, ws.blk_max); AL(ws.degs, ws.blk_max);
+  AL(ws.hist_r1, 2 * ws.blk_max); ws.hist_r2 = ws.hist_r1 + ws.blk_max;
+  AL(ws.hist_d1, 2 * ws.blk_max); ws.hist_d2 = ws.hist_d1 + ws.blk_max;
+  AL(ws.feat, (int64_t)CHFSI_MLP_IN * ws.blk_max); AL(ws.gcorr, ws.blk_max);
   AL(ws.flag, ws.blk_max + 64); AL(ws.ilist, 64);
   AL(ws.status, 2); AL(ws.barrier, 4); AL(ws.shiftflag, 4);
   ws.splitk_elems = (size_t)std::max<int64_t>(8 * nb, 48 * mm);
@@ -947,7 +984,8 @@ void workspace_free(Workspace& ws) {
   void* ptrs[] = {ws.Af, ws.Bf, ws.Lf, ws.Linv, ws.Hs, ws.T, ws.Y0, ws.Y1, ws.F, ws.W, ws.YL,
                   ws.Xw, ws.Z, ws.G, ws.V, ws.Rt, ws.jac, ws.lv, ws.lw, ws.lV, ws.lc, ws.theta,
                   ws.theta2, ws.resid, ws.resid2, ws.lamL, ws.residL, ws.gres, ws.dscale,
-                  ws.scal, ws.lal, ws.lbe, ws.deg, ws.perm, ws.degs, ws.flag, ws.ilist,
+                  ws.scal, ws.lal, ws.lbe, ws.deg, ws.perm, ws.degs, ws.hist_r1, ws.hist_d1,
+                  ws.feat, ws.gcorr, ws.flag, ws.ilist,
                   ws.status, ws.shiftflag, ws.barrier, ws.splitk};
   for (void* p : ptrs)
     if (p) debug_check(cudaFree(p), "cudaFree");
@@ -1251,8 +1289,16 @@ int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* 
     return set_err(ctx, CHFSI_EINVAL, "bad args");
   if (m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "m > blk_max");
   cudaSetDevice(ctx->ws.dev);
+  const float* gcorr = nullptr;
+  if (ctx->mlp_on) {
+    // the model without residual history (as in the first loop of a problem)
+    CK(degree_features(theta, r, m, a, b, tau, 0, nullptr, nullptr, nullptr, nullptr, ctx->ws.feat,
+                       ctx->stream));
+    CK(degree_model_eval(ctx->mlp_dev, ctx->ws.feat, m, ctx->ws.gcorr, ctx->stream));
+    gcorr = ctx->ws.gcorr;
+  }
   CK(degrees_kernel_run(theta, r, m, a, b, tau, dmin, dmax, n_wanted, degrees, ctx->ws.perm,
-                        ctx->ws.degs, ctx->stream, ctx->mlp_on ? ctx->mlp_dev : nullptr));
+                        ctx->ws.degs, ctx->stream, gcorr));
   CK(cudaStreamSynchronize(ctx->stream));
   return CHFSI_OK;
 }
@@ -1282,6 +1328,20 @@ int chfsi_mlp_predict(chfsi_ctx* ctx, const chfsi_mlp* model, const float* X, in
   if (!ctx || !model || !X || !y || n <= 0 || n > (int64_t)1 << 30) return set_err(ctx, CHFSI_EINVAL, "bad args");
   cudaSetDevice(ctx->ws.dev);
   CK(mlp_predict(model, X, n, y, ctx->stream));
+  return CHFSI_OK;
+}
+
+int chfsi_mlp_adam_epoch(chfsi_ctx* ctx, chfsi_mlp* model, float* m1, float* m2, int32_t* step,
+                         const float* X, const float* z, const int32_t* order, int64_t n, int32_t batch,
+                         float lr, float* loss) {
+  entry_guard("chfsi_mlp_adam_epoch");
+  if (!ctx || !model || !m1 || !m2 || !step || !X || !z || !order || !loss || n <= 0 ||
+      n > (int64_t)1 << 30 || batch < 1 || !(lr >= 0.f))
+    return set_err(ctx, CHFSI_EINVAL, "bad args");
+  for (int64_t i = 0; i < n; ++i)
+    if (order[i] < 0 || order[i] >= n) return set_err(ctx, CHFSI_EINVAL, "order out of range");
+  cudaSetDevice(ctx->ws.dev);
+  CK(mlp_adam_epoch(model, m1, m2, step, X, z, order, n, batch, lr, loss, ctx->stream));
   return CHFSI_OK;
 }
 

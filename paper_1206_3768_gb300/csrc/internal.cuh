@@ -131,12 +131,20 @@ cudaError_t generalized_residuals(const zd* AX, int64_t ldax, const zd* BX, int6
 cudaError_t splitmix_start_vector(zd* v, int n, uint64_t seed, cudaStream_t s);
 cudaError_t splitmix_gaussian_block(zd* Y, int64_t ldy, int n, int m, uint64_t seed,
                                     cudaStream_t s);
-// mlp: FP16 weights of a learned degree model (chfsi_mlp order, then mean and scale), or
-// nullptr for the closed-form rule.
+// Per-column degrees (closed-form rule; gcorr: the learned rate correction per column, or
+// nullptr).  With rh1 != nullptr the column's residual and degree are pushed into the
+// per-vector history (rh1/dh1: last loop, rh2/dh2: the loop before; global index g0 + i).
 cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, double a, double b,
                                double tau, int dmin, int dmax, int n_wanted, int* deg,
-                               int* perm_desc, int* deg_sorted, cudaStream_t s,
-                               const __half* mlp = nullptr);
+                               int* perm_desc, int* deg_sorted, cudaStream_t s, const float* gcorr = nullptr,
+                               int g0 = 0, double* rh1 = nullptr, double* rh2 = nullptr,
+                               int* dh1 = nullptr, int* dh2 = nullptr);
+// Model inputs X (m x CHFSI_MLP_IN floats, row per column) from the block and the history
+// (null history: none), and the model's g per column (FP16 weights as laid out by mlp_to_half).
+cudaError_t degree_features(const double* theta, const double* r, int m, double a, double b, double tau,
+                            int g0, const double* rh1, const double* rh2, const int* dh1, const int* dh2,
+                            float* X, cudaStream_t s);
+cudaError_t degree_model_eval(const __half* mlp, const float* X, int m, float* g, cudaStream_t s);
 // learned degree model (mlp.cu)
 int mlp_param_count();
 cudaError_t mlp_to_half(const chfsi_mlp* m, __half* dst_dev, cudaStream_t s);
@@ -145,6 +153,8 @@ cudaError_t mlp_train(chfsi_mlp* m, const float* X, const float* z, int64_t n, i
 cudaError_t mlp_gradient(const chfsi_mlp* m, const float* X, const float* z, int64_t n, float* grad,
                          float* loss_out, cudaStream_t s);
 cudaError_t mlp_predict(const chfsi_mlp* m, const float* X, int64_t n, float* y, cudaStream_t s);
+cudaError_t mlp_adam_epoch(chfsi_mlp* m, float* m1, float* m2, int* step, const float* X, const float* z,
+                           const int* order, int64_t n, int batch, float lr, float* loss_out, cudaStream_t s);
 cudaError_t lock_scan(const double* r, int m, double tau, int max_lock, int* nlock,
                       cudaStream_t s);
 cudaError_t fill_nan(double* x, int m, cudaStream_t s);
@@ -236,6 +246,11 @@ struct Workspace {
   double *lamL = nullptr, *residL = nullptr, *gres = nullptr;
   double *dscale = nullptr, *scal = nullptr, *lal = nullptr, *lbe = nullptr;
   int *deg = nullptr, *perm = nullptr, *degs = nullptr, *flag = nullptr, *ilist = nullptr;
+  // learned degree: per-vector residual/degree history (global column index), model inputs
+  // and outputs of the current loop
+  double *hist_r1 = nullptr, *hist_r2 = nullptr;
+  int *hist_d1 = nullptr, *hist_d2 = nullptr;
+  float *feat = nullptr, *gcorr = nullptr;
   int* status = nullptr;  // [0]: DEV_* flags, [1]: first failing pivot
   int* shiftflag = nullptr;  // set when a Cholesky QR pass needed the shifted retry
   long long wait_limit = 0;  // polls of the eigensolver's grid-barrier waits (0: the default)

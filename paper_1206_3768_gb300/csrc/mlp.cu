@@ -3,13 +3,18 @@
 //
 // The closed-form rule assumes that a degree-d filter reduces the residual of Ritz vector i
 // by rho_i^d, rho_i = exp(acosh|t_i|).  The model predicts a correction g(x) to that rate,
-// rate_i = ln(rho_i) * exp(g(x_i)), from four features of the vector,
-//     x = [acosh|t_i|, log10(r_i / tau), i / m, log10(max(gap_i / e, 1e-12))],
-// with a 4 -> 64 -> 64 -> 1 perceptron (tanh hidden units, linear output).  Training fits
-// g to the logged per-degree reduction rates with Adam on mean squared error; one CTA runs
-// an epoch (minibatches in sub-chunks of 128 samples, every gradient entry owned by one
-// thread and accumulated in shared memory, so the sums over samples have a fixed order).  The solver evaluates the
-// model with FP16 weights; an untrained model (zero output layer) reproduces the closed form.
+// rate_i = ln(rho_i) * exp(g(x_i)), from eight features of the vector and the loop: its log
+// residual over the last three loops, the degrees of the last two, its Ritz-value position
+// relative to the filter interval and the filter bounds (the list is in include/chfsi.h),
+// with an 8 -> 64 -> 64 -> 64 -> 1 perceptron (tanh hidden units, linear output).  The
+// degree is then clamp(ceil(ln(r_i / tau) / rate_i), deg_min, deg_max), the closed form
+// wherever that is not finite; an untrained model (zero output layer, g = 0) gives the
+// closed form exactly.
+//
+// Training fits g to the logged per-degree reduction rates with Adam on mean squared error;
+// one CTA runs an epoch (minibatches in sub-chunks of 64 samples, every gradient entry owned
+// by one thread and accumulated in shared memory, so the sums over samples have a fixed
+// order).  The solver evaluates the model with FP16 weights, one warp per vector.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -23,14 +28,15 @@
 namespace {
 
 constexpr int IN = CHFSI_MLP_IN, HID = CHFSI_MLP_HID;
-constexpr int NPARAM = HID * IN + HID + HID * HID + HID + HID + 1;
+constexpr int NPARAM = HID * IN + HID + 2 * (HID * HID + HID) + HID + 1;
 static_assert(NPARAM == CHFSI_MLP_NPARAM, "parameter count of the C interface");
-constexpr int CHUNK = 128;          // samples per sub-chunk
+constexpr int CHUNK = 64;           // samples per sub-chunk
 constexpr int MLP_THREADS = 512;
 
 // Flattened parameter offsets (the order of the chfsi_mlp struct).
-constexpr int OW1 = 0, OB1 = OW1 + HID * IN, OW2 = OB1 + HID, OB2 = OW2 + HID * HID, OW3 = OB2 + HID,
-              OB3 = OW3 + HID;
+constexpr int OW1 = 0, OB1 = OW1 + HID * IN, OW2 = OB1 + HID, OB2 = OW2 + HID * HID,
+              OW3 = OB2 + HID, OB3 = OW3 + HID * HID, OW4 = OB3 + HID, OB4 = OW4 + HID;
+static_assert(OB4 + 1 == NPARAM, "parameter layout");
 
 // Activations are stored [unit][sample] with rows padded to CHUNK + 1 words, so that both
 // access patterns (lanes along samples in the forward pass, lanes along units in the weight
@@ -42,12 +48,26 @@ struct MlpShared {
   float G[NPARAM];
   float xh[IN][LDC];
   float h1[HID][LDC];
-  float h2[HID][LDC];   // activations, then dL/d(pre-activation) of layer 2
-  float d1[HID][LDC];   // dL/d(pre-activation) of layer 1
+  float h2[HID][LDC];
+  float h3[HID][LDC];   // activations of layer 3, then dL/d(pre-activation) of layers 3 and 1
+  float d[HID][LDC];    // dL/d(pre-activation) of layer 2
   float dy[CHUNK];
 };
 
-// Forward of `cnt` samples (indices idx[0..cnt)) into s.h1, s.h2 and y.
+// One hidden layer: out[j][b] = tanh(b_j + sum_k W[j][k] in[k][b]) for the chunk.
+template <int NIN>
+__device__ void dense_tanh(const float* W, const float* bias, const float (*in)[LDC], float (*out)[LDC]) {
+  for (int e = threadIdx.x; e < HID * CHUNK; e += blockDim.x) {
+    const int j = e / CHUNK, b = e % CHUNK;
+    float a = bias[j];
+#pragma unroll 8
+    for (int k = 0; k < NIN; ++k) a += W[j * NIN + k] * in[k][b];
+    out[j][b] = tanhf(a);
+  }
+  __syncthreads();
+}
+
+// Forward of `cnt` samples (indices idx[0..cnt)) into s.h1 .. s.h3 and y.
 __device__ void mlp_forward_chunk(MlpShared& s, const float* X, const int* idx, int cnt,
                                   const float* mean, const float* scale, float* y) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -56,27 +76,45 @@ __device__ void mlp_forward_chunk(MlpShared& s, const float* X, const int* idx, 
     s.xh[f][b] = (b < cnt) ? (X[(int64_t)idx[b] * IN + f] - mean[f]) * scale[f] : 0.f;
   }
   __syncthreads();
-  for (int e = tid; e < HID * CHUNK; e += nt) {
-    const int j = e / CHUNK, b = e % CHUNK;
-    float a = s.W[OB1 + j];
-#pragma unroll
-    for (int k = 0; k < IN; ++k) a += s.W[OW1 + j * IN + k] * s.xh[k][b];
-    s.h1[j][b] = tanhf(a);
-  }
-  __syncthreads();
-  for (int e = tid; e < HID * CHUNK; e += nt) {
-    const int j = e / CHUNK, b = e % CHUNK;
-    float a = s.W[OB2 + j];
-    for (int k = 0; k < HID; ++k) a += s.W[OW2 + j * HID + k] * s.h1[k][b];
-    s.h2[j][b] = tanhf(a);
-  }
-  __syncthreads();
+  dense_tanh<IN>(s.W + OW1, s.W + OB1, s.xh, s.h1);
+  dense_tanh<HID>(s.W + OW2, s.W + OB2, s.h1, s.h2);
+  dense_tanh<HID>(s.W + OW3, s.W + OB3, s.h2, s.h3);
   for (int b = tid; b < CHUNK; b += nt) {
-    float a = s.W[OB3];
-    for (int k = 0; k < HID; ++k) a += s.W[OW3 + k] * s.h2[k][b];
+    float a = s.W[OB4];
+    for (int k = 0; k < HID; ++k) a += s.W[OW4 + k] * s.h3[k][b];
     y[b] = a;
   }
   __syncthreads();
+}
+
+// G[W] += delta in^T and G[bias] += sum_b delta for a layer with NIN inputs.
+template <int NIN>
+__device__ void layer_grad(float* G, int ow, int ob, const float (*delta)[LDC], const float (*in)[LDC]) {
+  for (int e = threadIdx.x; e < HID * NIN + HID; e += blockDim.x) {
+    float a = 0.f;
+    if (e < HID * NIN) {
+      const int j = e / NIN, k = e % NIN;
+      for (int b = 0; b < CHUNK; ++b) a += delta[j][b] * in[k][b];
+      G[ow + e] += a;
+    } else {
+      const int j = e - HID * NIN;
+      for (int b = 0; b < CHUNK; ++b) a += delta[j][b];
+      G[ob + j] += a;
+    }
+  }
+}
+
+// out[k][b] = (sum_j W[j][k] delta[j][b]) (1 - act[k][b]^2): back through a HID x HID layer
+// and the tanh of the layer below it.  out may not alias delta.
+__device__ void back_delta(const float* W, const float (*delta)[LDC], const float (*act)[LDC],
+                           float (*out)[LDC]) {
+  for (int e = threadIdx.x; e < HID * CHUNK; e += blockDim.x) {
+    const int k = e / CHUNK, b = e % CHUNK;
+    float a = 0.f;
+    for (int j = 0; j < HID; ++j) a += W[j * HID + k] * delta[j][b];
+    const float h = act[k][b];
+    out[k][b] = a * (1.f - h * h);
+  }
 }
 
 // Backward of one sub-chunk: s.dy holds dL/dy per sample (0 beyond the chunk's samples);
@@ -84,61 +122,32 @@ __device__ void mlp_forward_chunk(MlpShared& s, const float* X, const int* idx, 
 __device__ void mlp_backward_chunk(MlpShared& s) {
   const int tid = threadIdx.x, nt = blockDim.x;
   // output layer
-  for (int e = tid; e < NPARAM; e += nt) {
-    if (e >= OW3 && e < OB3) {
-      const int k = e - OW3;
-      float a = 0.f;
-      for (int b = 0; b < CHUNK; ++b) a += s.dy[b] * s.h2[k][b];
-      s.G[e] += a;
-    } else if (e == OB3) {
-      float a = 0.f;
+  for (int e = tid; e < HID + 1; e += nt) {
+    float a = 0.f;
+    if (e < HID)
+      for (int b = 0; b < CHUNK; ++b) a += s.dy[b] * s.h3[e][b];
+    else
       for (int b = 0; b < CHUNK; ++b) a += s.dy[b];
-      s.G[e] += a;
-    }
+    s.G[OW4 + e] += a;   // OB4 == OW4 + HID
   }
   __syncthreads();
-  // h2 <- dA2 = (dy w3) (1 - h2^2)
+  // h3 <- delta3 = dy w4 (1 - h3^2)
   for (int e = tid; e < HID * CHUNK; e += nt) {
     const int j = e / CHUNK, b = e % CHUNK;
-    const float h = s.h2[j][b];
-    s.h2[j][b] = s.dy[b] * s.W[OW3 + j] * (1.f - h * h);
+    const float h = s.h3[j][b];
+    s.h3[j][b] = s.dy[b] * s.W[OW4 + j] * (1.f - h * h);
   }
   __syncthreads();
-  // layer 2 weights and biases; d1 = dA1 = (W2^T dA2) (1 - h1^2)
-  for (int e = tid; e < NPARAM; e += nt) {
-    if (e >= OW2 && e < OB2) {
-      const int j = (e - OW2) / HID, k = (e - OW2) % HID;
-      float a = 0.f;
-      for (int b = 0; b < CHUNK; ++b) a += s.h2[j][b] * s.h1[k][b];
-      s.G[e] += a;
-    } else if (e >= OB2 && e < OW3) {
-      const int j = e - OB2;
-      float a = 0.f;
-      for (int b = 0; b < CHUNK; ++b) a += s.h2[j][b];
-      s.G[e] += a;
-    }
-  }
-  for (int e = tid; e < HID * CHUNK; e += nt) {
-    const int k = e / CHUNK, b = e % CHUNK;
-    float a = 0.f;
-    for (int j = 0; j < HID; ++j) a += s.W[OW2 + j * HID + k] * s.h2[j][b];
-    const float h = s.h1[k][b];
-    s.d1[k][b] = a * (1.f - h * h);
-  }
+  // layer 3 parameters from (delta3, h2); d <- delta2 = (W3^T delta3)(1 - h2^2)
+  layer_grad<HID>(s.G, OW3, OB3, s.h3, s.h2);
+  back_delta(s.W + OW3, s.h3, s.h2, s.d);
   __syncthreads();
-  for (int e = tid; e < NPARAM; e += nt) {
-    if (e >= OW1 && e < OB1) {
-      const int j = (e - OW1) / IN, k = (e - OW1) % IN;
-      float a = 0.f;
-      for (int b = 0; b < CHUNK; ++b) a += s.d1[j][b] * s.xh[k][b];
-      s.G[e] += a;
-    } else if (e >= OB1 && e < OW2) {
-      const int j = e - OB1;
-      float a = 0.f;
-      for (int b = 0; b < CHUNK; ++b) a += s.d1[j][b];
-      s.G[e] += a;
-    }
-  }
+  // layer 2 parameters from (delta2, h1); h3 <- delta1 = (W2^T delta2)(1 - h1^2)
+  layer_grad<HID>(s.G, OW2, OB2, s.d, s.h1);
+  back_delta(s.W + OW2, s.d, s.h1, s.h3);
+  __syncthreads();
+  // layer 1 parameters from (delta1, xh)
+  layer_grad<IN>(s.G, OW1, OB1, s.h3, s.xh);
   __syncthreads();
 }
 
@@ -261,6 +270,7 @@ void chfsi_mlp_init(chfsi_mlp* m, uint64_t seed) {
   const float a1 = std::sqrt(6.0f / (IN + HID)), a2 = std::sqrt(6.0f / (HID + HID));
   for (int e = 0; e < HID * IN; ++e) m->w1[e] = (float)((2.0 * unif() - 1.0) * a1);
   for (int e = 0; e < HID * HID; ++e) m->w2[e] = (float)((2.0 * unif() - 1.0) * a2);
+  for (int e = 0; e < HID * HID; ++e) m->w3[e] = (float)((2.0 * unif() - 1.0) * a2);
   // zero output layer: the untrained model predicts no correction (the closed form)
   for (int f = 0; f < IN; ++f) m->scale[f] = 1.0f;
 }
@@ -324,6 +334,47 @@ cudaError_t mlp_train(chfsi_mlp* m, const float* X, const float* z, int64_t n, i
   return cudaSuccess;
 }
 
+// One epoch of Adam in a caller-given sample order with caller-given moments (host in, host
+// out), for the parity test of the optimiser against the CPU oracle: params, m1, m2 (NPARAM
+// each) and *step are updated in place; the model's mean/scale are used as they are.
+cudaError_t mlp_adam_epoch(chfsi_mlp* m, float* m1, float* m2, int* step, const float* X, const float* z,
+                           const int* order, int64_t n, int batch, float lr, float* loss_out, cudaStream_t s) {
+  if (n <= 0 || batch < 1) return cudaErrorInvalidValue;
+  DevBuf dP, dM1, dM2, dStep, dX, dZ, dIdx, dNorm, dLoss;
+  cudaError_t e;
+  if ((e = dP.alloc(sizeof(float) * NPARAM)) || (e = dM1.alloc(sizeof(float) * NPARAM)) ||
+      (e = dM2.alloc(sizeof(float) * NPARAM)) || (e = dStep.alloc(sizeof(int))) ||
+      (e = dX.alloc(sizeof(float) * n * IN)) || (e = dZ.alloc(sizeof(float) * n)) ||
+      (e = dIdx.alloc(sizeof(int) * n)) || (e = dNorm.alloc(sizeof(float) * 2 * IN)) ||
+      (e = dLoss.alloc(sizeof(float))))
+    return e;
+  float* norm = (float*)dNorm.p;
+  if ((e = cudaMemcpyAsync(dP.p, m, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(dM1.p, m1, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(dM2.p, m2, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(dStep.p, step, sizeof(int), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(dX.p, X, sizeof(float) * n * IN, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(dZ.p, z, sizeof(float) * n, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(dIdx.p, order, sizeof(int) * n, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(norm, m->mean, sizeof(float) * IN, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(norm + IN, m->scale, sizeof(float) * IN, cudaMemcpyHostToDevice, s)))
+    return e;
+  const size_t smem = sizeof(MlpShared);
+  if ((e = cudaFuncSetAttribute(mlp_epoch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return e;
+  mlp_epoch_kernel<<<1, MLP_THREADS, smem, s>>>((float*)dP.p, (float*)dM1.p, (float*)dM2.p, (int*)dStep.p,
+                                                (const float*)dX.p, (const float*)dZ.p, (const int*)dIdx.p,
+                                                (int)n, batch, lr, norm, norm + IN, (float*)dLoss.p, nullptr);
+  CHFSI_COUNT_LAUNCH();
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cudaMemcpyAsync(m, dP.p, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(m1, dM1.p, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(m2, dM2.p, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(step, dStep.p, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(loss_out, dLoss.p, sizeof(float), cudaMemcpyDeviceToHost, s)))
+    return e;
+  return cudaStreamSynchronize(s);
+}
 
 // Gradient of the mean squared error over all n samples (host in, host out), and the loss:
 // one epoch with a single minibatch of all samples and a zero step.

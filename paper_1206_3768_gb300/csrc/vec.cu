@@ -206,33 +206,114 @@ __global__ void gaussian_block_kernel(zd* Y, int64_t ldy, int n, int m, unsigned
 }
 
 // ---------------------------------------------------------------- degrees and locking
-// g(x) of the learned degree model (FP16 weights in the order of chfsi_mlp, then mean and
-// scale), FP32 arithmetic.
-__device__ float degree_mlp(const __half* W, const float* x) {
-  constexpr int IN = CHFSI_MLP_IN, HID = CHFSI_MLP_HID;
-  const __half *w1 = W, *b1 = w1 + HID * IN, *w2 = b1 + HID, *b2 = w2 + HID * HID, *w3 = b2 + HID,
-               *b3 = w3 + HID, *mean = b3 + 1, *scale = mean + IN;
-  float xh[IN], h1[HID];
-#pragma unroll
-  for (int k = 0; k < IN; ++k) xh[k] = (x[k] - __half2float(mean[k])) * __half2float(scale[k]);
-  for (int j = 0; j < HID; ++j) {
-    float acc = __half2float(b1[j]);
-#pragma unroll
-    for (int k = 0; k < IN; ++k) acc += __half2float(w1[j * IN + k]) * xh[k];
-    h1[j] = tanhf(acc);
+// Inputs of the learned degree model for active column i (global index g = g0 + i), in the
+// order of include/chfsi.h: log10 of the residual over tau now and in the last two loops
+// (the current value where a loop is missing), the degrees of the last two loops (0 where
+// missing), the Ritz-value position t_i = (theta_i - c)/e, the position t_0 of the smallest
+// Ritz value a0 = theta_0, and the bound ratio (a - a0)/(b - a0).  History arrays may be
+// null (no history).
+__global__ void degree_features_kernel(const double* theta, const double* r, int m, double a, double b,
+                                       double tau, int g0, const double* rh1, const double* rh2,
+                                       const int* dh1, const int* dh2, float* X) {
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double a0 = theta[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int g = g0 + i;
+    const double r0 = r[i];
+    double r1 = rh1 ? rh1[g] : 0.0;
+    if (!(r1 > 0.0)) r1 = r0;
+    double r2 = rh2 ? rh2[g] : 0.0;
+    if (!(r2 > 0.0)) r2 = r1;
+    float* x = X + (int64_t)i * CHFSI_MLP_IN;
+    x[0] = (float)log10(r0 / tau);
+    x[1] = (float)log10(r1 / tau);
+    x[2] = (float)log10(r2 / tau);
+    x[3] = dh1 ? (float)dh1[g] : 0.f;
+    x[4] = dh2 ? (float)dh2[g] : 0.f;
+    x[5] = (float)((theta[i] - c) / e);
+    x[6] = (float)((a0 - c) / e);
+    x[7] = (float)((a - a0) / (b - a0));
   }
-  float y = __half2float(b3[0]);
-  for (int j = 0; j < HID; ++j) {
-    float acc = __half2float(b2[j]);
-    for (int k = 0; k < HID; ++k) acc += __half2float(w2[j * HID + k]) * h1[k];
-    y += __half2float(w3[j]) * tanhf(acc);
-  }
-  return y;
 }
 
+// g(x) of the learned degree model for every column: one warp per column, FP16 weights (the
+// order of chfsi_mlp, then mean and scale) converted to FP32 in shared memory and stored
+// transposed (input-major) so that the lanes of a warp, which own consecutive units, read
+// consecutive words.  FP32 arithmetic.
+constexpr int DM_WARPS = 8;
+__global__ void __launch_bounds__(32 * DM_WARPS) degree_model_kernel(const __half* W, const float* X, int m,
+                                                                    float* gout) {
+  constexpr int IN = CHFSI_MLP_IN, HID = CHFSI_MLP_HID;
+  extern __shared__ float dm_smem[];
+  float* w1t = dm_smem;                 // [IN][HID]
+  float* b1 = w1t + IN * HID;
+  float* w2t = b1 + HID;                // [HID][HID]
+  float* b2 = w2t + HID * HID;
+  float* w3t = b2 + HID;
+  float* b3 = w3t + HID * HID;
+  float* w4 = b3 + HID;
+  float* act = w4 + HID + 2 * IN + 1;   // per warp: xh[IN], h[HID], h'[HID]
+  const __half *s1 = W, *sb1 = s1 + HID * IN, *s2 = sb1 + HID, *sb2 = s2 + HID * HID, *s3 = sb2 + HID,
+               *sb3 = s3 + HID * HID, *s4 = sb3 + HID, *sb4 = s4 + HID, *smean = sb4 + 1, *sscale = smean + IN;
+  for (int e = threadIdx.x; e < HID * IN; e += blockDim.x) {
+    const int j = e / IN, k = e % IN;
+    w1t[k * HID + j] = __half2float(s1[e]);
+  }
+  for (int e = threadIdx.x; e < HID * HID; e += blockDim.x) {
+    const int j = e / HID, k = e % HID;
+    w2t[k * HID + j] = __half2float(s2[e]);
+    w3t[k * HID + j] = __half2float(s3[e]);
+  }
+  for (int j = threadIdx.x; j < HID; j += blockDim.x) {
+    b1[j] = __half2float(sb1[j]);
+    b2[j] = __half2float(sb2[j]);
+    b3[j] = __half2float(sb3[j]);
+    w4[j] = __half2float(s4[j]);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* xh = act + wid * (IN + 2 * HID);
+  float* h = xh + IN;
+  float* h2 = h + HID;
+  const float bias4 = __half2float(sb4[0]);
+  for (int col = blockIdx.x * DM_WARPS + wid; col < m; col += gridDim.x * DM_WARPS) {
+    if (lane < IN)
+      xh[lane] = (X[(int64_t)col * IN + lane] - __half2float(smean[lane])) * __half2float(sscale[lane]);
+    __syncwarp();
+    for (int j = lane; j < HID; j += 32) {
+      float a = b1[j];
+#pragma unroll
+      for (int k = 0; k < IN; ++k) a += w1t[k * HID + j] * xh[k];
+      h[j] = tanhf(a);
+    }
+    __syncwarp();
+    for (int j = lane; j < HID; j += 32) {
+      float a = b2[j];
+      for (int k = 0; k < HID; ++k) a += w2t[k * HID + j] * h[k];
+      h2[j] = tanhf(a);
+    }
+    __syncwarp();
+    float y = 0.f;
+    for (int j = lane; j < HID; j += 32) {
+      float a = b3[j];
+      for (int k = 0; k < HID; ++k) a += w3t[k * HID + j] * h2[k];
+      y += w4[j] * tanhf(a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (lane == 0) gout[col] = y + bias4;
+    __syncwarp();
+  }
+}
+
+// Per-column degrees: the closed-form rule, with the learned rate correction g (clamped to
+// [-3, 3]) where gcorr is given and the result is finite; columns past the wanted ones take
+// the largest wanted degree; then the stable descending order.  With history arrays the
+// residual and degree of every column are pushed into them (global index g0 + i).
 __global__ void degrees_kernel(const double* theta, const double* r, int m, double a, double b,
                                double tau, int dmin, int dmax, int n_wanted, int* deg, int* perm,
-                               int* degs, const __half* mlp) {
+                               int* degs, const float* gcorr, int g0, double* rh1, double* rh2,
+                               int* dh1, int* dh2) {
   extern __shared__ int sd[];
   const double e = 0.5 * (b - a), c = 0.5 * (b + a);
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -246,11 +327,8 @@ __global__ void degrees_kernel(const double* theta, const double* r, int m, doub
         const double rho = t + sqrt(t * t - 1.0);
         const double lrho = log(rho);
         double need = log(ri / tau) / lrho;
-        if (mlp) {
-          const double gap = (i + 1 < m) ? theta[i + 1] - theta[i] : e;
-          const float x[CHFSI_MLP_IN] = {(float)lrho, (float)log10(ri / tau), (float)i / (float)m,
-                                         (float)log10(fmax(gap / e, 1e-12))};
-          const float g = fminf(3.f, fmaxf(-3.f, degree_mlp(mlp, x)));
+        if (gcorr) {
+          const float g = fminf(3.f, fmaxf(-3.f, gcorr[i]));
           const double learned = log(ri / tau) / (lrho * exp((double)g));
           if (isfinite(learned)) need = learned;
         }
@@ -276,6 +354,13 @@ __global__ void degrees_kernel(const double* theta, const double* r, int m, doub
     deg[i] = di;
     perm[rank] = i;
     degs[rank] = di;
+    if (rh1) {
+      const int g = g0 + i;
+      rh2[g] = rh1[g];
+      dh2[g] = dh1[g];
+      rh1[g] = r[i];
+      dh1[g] = di;
+    }
   }
 }
 
@@ -612,12 +697,34 @@ cudaError_t splitmix_gaussian_block(zd* Y, int64_t ldy, int n, int m, uint64_t s
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
+cudaError_t degree_features(const double* theta, const double* r, int m, double a, double b, double tau,
+                            int g0, const double* rh1, const double* rh2, const int* dh1, const int* dh2,
+                            float* X, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  degree_features_kernel<<<(m + 127) / 128, 128, 0, s>>>(theta, r, m, a, b, tau, g0, rh1, rh2, dh1, dh2, X);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+cudaError_t degree_model_eval(const __half* mlp, const float* X, int m, float* g, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  constexpr int IN = CHFSI_MLP_IN, HID = CHFSI_MLP_HID;
+  const size_t smem = sizeof(float) * ((size_t)HID * IN + 2 * (size_t)HID * HID + 4 * HID + 2 * IN + 1 +
+                                       (size_t)DM_WARPS * (IN + 2 * HID));
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(degree_model_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return attr;
+  const int blocks = std::min((m + DM_WARPS - 1) / DM_WARPS, 2 * sm_count());
+  degree_model_kernel<<<blocks, 32 * DM_WARPS, smem, s>>>(mlp, X, m, g);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
 cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, double a, double b,
                                double tau, int dmin, int dmax, int n_wanted, int* deg,
-                               int* perm_desc, int* deg_sorted, cudaStream_t s, const __half* mlp) {
+                               int* perm_desc, int* deg_sorted, cudaStream_t s, const float* gcorr,
+                               int g0, double* rh1, double* rh2, int* dh1, int* dh2) {
   if (m <= 0) return cudaSuccess;
   degrees_kernel<<<1, 256, m * sizeof(int), s>>>(theta, r, m, a, b, tau, dmin, dmax, n_wanted,
-                                                 deg, perm_desc, deg_sorted, mlp);
+                                                 deg, perm_desc, deg_sorted, gcorr, g0, rh1, rh2, dh1, dh2);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -1,6 +1,10 @@
-"""Learned filter degree: training-data assembly (CPU) and the CUDA perceptron (GPU):
-forward and gradients against a NumPy float64 restatement, training, the untrained model
-reproducing the closed-form rule, and a solve with a trained model."""
+"""Learned filter degree: training-data assembly (CPU) and the CUDA perceptron (GPU).
+
+The CUDA forward pass, gradient and Adam epochs are compared with the oracle in
+oracle/degree_mlp.py (float64 NumPy, pinned by finite differences and hand-worked cases in
+tests/test_degree_mlp_oracle.py); the degrees the solver takes from an installed model are
+compared with the closed-form rule evaluated on the CPU with the oracle's forward pass."""
+import ctypes
 import math
 
 import numpy as np
@@ -8,6 +12,7 @@ import pytest
 import torch
 
 import oracle.chfsi_oracle as O
+from oracle import degree_mlp as D
 from paper_1206_3768_gb300 import degree_model as dm
 from paper_1206_3768_gb300 import inputs
 
@@ -15,107 +20,118 @@ DEV = "cuda"
 
 
 def test_mlp_struct_layout_matches_the_parameter_count():
-    import ctypes
-
     from paper_1206_3768_gb300 import binding as cb
 
-    assert cb.MLP_NPARAM == 4 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+    assert cb.MLP_SIZES == D.LIBRARY_SIZES
+    assert cb.MLP_NPARAM == D.param_count(D.LIBRARY_SIZES) == 8961
     assert ctypes.sizeof(cb.chfsi_mlp) == 4 * (cb.MLP_NPARAM + 2 * cb.MLP_IN)
-    assert cb.chfsi_mlp.b3.offset == 4 * (cb.MLP_NPARAM - 1)
+    assert cb.chfsi_mlp.b4.offset == 4 * (cb.MLP_NPARAM - 1)
+    # the flat order of the oracle is the order of the C structure
+    m = cb.chfsi_mlp_init(3)
+    layers = D.unpack(m.params(), D.LIBRARY_SIZES)
+    assert np.array_equal(layers[0][0].ravel(), np.array(m.w1, np.float64))
+    assert np.array_equal(layers[2][0].ravel(), np.array(m.w3, np.float64))
+    assert np.all(layers[3][0] == 0) and layers[3][1][0] == 0   # untrained: zero output layer
 
 
-def _rec(p, k, g, i, m, th, r, tau, d, c, e, gap):
-    return [p, k, g, i, m, th, r, tau, d, c, e, gap]
+def _rec(p, k, g, i, m, th, r, tau, d, c, e, r_next, x=None):
+    return [p, k, g, i, m, th, r, tau, d, c, e, r_next] + list(x if x is not None else np.arange(8) * 0.5)
 
 
 def test_training_pairs_recover_planted_rate():
-    """A vector whose residual falls by exactly rho^(2d) per loop gives z = ln 2."""
+    """A vector whose residual falls by exactly rho^(2d) in one loop gives z = ln 2, and its
+    logged inputs are passed through unchanged."""
     c, e, tau = 1.0, 0.5, 1e-10
     th = -0.5                        # t = (th - c)/e = -3
     t = 3.0
     lrho = math.log(t + math.sqrt(t * t - 1))
     d, r0 = 7, 1e-2
     r1 = r0 * math.exp(-2 * lrho * d)
-    log = np.array([_rec(0, 3, 5, 2, 10, th, r0, tau, d, c, e, 0.1),
-                    _rec(0, 4, 5, 1, 9, th, r1, tau, d, c, e, 0.1),
-                    _rec(1, 4, 5, 1, 9, th, r1, tau, d, c, e, 0.1)])   # other problem: no pair
+    x = [8.0, 8.5, 9.0, 7, 6, -3.0, -3.2, 0.1]
+    log = np.array([_rec(0, 3, 5, 2, 10, th, r0, tau, d, c, e, r1, x)])
     X, z = dm.training_pairs(log)
-    assert X.shape == (1, 4)
+    assert X.shape == (1, 8)
     assert abs(z[0] - math.log(2.0)) < 1e-6
-    assert abs(X[0, 0] - lrho) < 1e-6 and abs(X[0, 1] - 8.0) < 1e-6
-    assert abs(X[0, 2] - 0.2) < 1e-7 and abs(X[0, 3] - math.log10(0.2)) < 1e-6
+    assert np.allclose(X[0], np.array(x, np.float32))
 
 
-def test_training_pairs_skip_converged_and_inside_interval():
+def test_training_pairs_skip_converged_unfiltered_and_inside_interval():
     c, e, tau = 1.0, 0.5, 1e-10
-    log = np.array([_rec(0, 0, 0, 0, 4, 1.2, 1e-3, tau, 5, c, e, 0.1),   # |t| <= 1
-                    _rec(0, 1, 0, 0, 4, 1.2, 1e-4, tau, 5, c, e, 0.1),
-                    _rec(0, 0, 1, 1, 4, -1.0, 1e-12, tau, 5, c, e, 0.1),  # r <= tau
-                    _rec(0, 1, 1, 1, 4, -1.0, 1e-13, tau, 5, c, e, 0.1)])
+    log = np.array([_rec(0, 0, 0, 0, 4, 1.2, 1e-3, tau, 5, c, e, 1e-4),    # |t| <= 1
+                    _rec(0, 0, 1, 1, 4, -1.0, 1e-12, tau, 5, c, e, 1e-13),  # r <= tau
+                    _rec(0, 0, 2, 2, 4, -1.0, 1e-3, tau, 0, c, e, 1e-3),    # not filtered
+                    _rec(0, 0, 3, 3, 4, -1.0, 1e-3, tau, 5, c, e, 2e-3)])   # residual grew
     X, z = dm.training_pairs(log)
     assert X.shape[0] == 0
 
 
 # ------------------------------------------------------------------------------ GPU
-def _np_model(m):
-    p = m.params().astype(np.float64)
-    H, I = 64, 4
-    w1 = p[:H * I].reshape(H, I); b1 = p[H * I:H * I + H]
-    o = H * I + H
-    w2 = p[o:o + H * H].reshape(H, H); b2 = p[o + H * H:o + H * H + H]
-    o += H * H + H
-    w3 = p[o:o + H]; b3 = p[o + H]
-    mean = np.array(m.mean, np.float64); scale = np.array(m.scale, np.float64)
-    return w1, b1, w2, b2, w3, b3, mean, scale
-
-
-def _np_forward_grad(m, X, z):
-    w1, b1, w2, b2, w3, b3, mean, scale = _np_model(m)
-    xh = (X.astype(np.float64) - mean) * scale
-    h1 = np.tanh(xh @ w1.T + b1)
-    h2 = np.tanh(h1 @ w2.T + b2)
-    y = h2 @ w3 + b3
-    n = len(z)
-    dy = (y - z) / n
-    loss = 0.5 * np.mean((y - z) ** 2)
-    gw3 = h2.T @ dy; gb3 = dy.sum()
-    da2 = np.outer(dy, w3) * (1 - h2 ** 2)
-    gw2 = da2.T @ h1; gb2 = da2.sum(0)
-    da1 = (da2 @ w2) * (1 - h1 ** 2)
-    gw1 = da1.T @ xh; gb1 = da1.sum(0)
-    g = np.concatenate([gw1.ravel(), gb1, gw2.ravel(), gb2, gw3, [gb3]])
-    return y, g, loss
+def _oracle_args(m):
+    return m.params().astype(np.float64), np.array(m.mean, np.float64), np.array(m.scale, np.float64)
 
 
 def _random_model(cb, seed):
     m = cb.chfsi_mlp_init(seed)
     rng = np.random.default_rng(seed)
-    for i in range(64):
-        m.w3[i] = float(rng.normal(0, 0.3))
-        m.b1[i] = float(rng.normal(0, 0.1))
-        m.b2[i] = float(rng.normal(0, 0.1))
-    m.b3 = 0.05
-    for f in range(4):
+    p = m.params()
+    p[-cb.MLP_HID - 1:-1] = rng.normal(0, 0.3, cb.MLP_HID)          # output weights
+    p[-1] = 0.05
+    for o in (cb.MLP_HID * cb.MLP_IN, cb.MLP_HID * cb.MLP_IN + cb.MLP_HID + cb.MLP_HID ** 2):
+        p[o:o + cb.MLP_HID] = rng.normal(0, 0.1, cb.MLP_HID)         # biases of layers 1, 2
+    m.set_params(p)
+    for f in range(cb.MLP_IN):
         m.mean[f] = float(rng.normal(0, 0.5))
         m.scale[f] = float(rng.uniform(0.5, 2.0))
     return m
 
 
 @pytest.mark.gpu
-def test_mlp_forward_and_gradient_match_numpy():
+def test_mlp_forward_and_gradient_match_the_oracle():
     from paper_1206_3768_gb300 import binding as cb
 
     rng = np.random.default_rng(3)
-    X = rng.normal(size=(300, 4)).astype(np.float32)
+    X = rng.normal(size=(300, 8)).astype(np.float32)
     z = rng.normal(size=300).astype(np.float32)
     m = _random_model(cb, 11)
     with cb.Solver(64, 8) as s:
         y = cb.chfsi_mlp_predict(s.ctx, m, X)
         g, loss = cb.chfsi_mlp_gradient(s.ctx, m, X, z)
-    y_ref, g_ref, loss_ref = _np_forward_grad(m, X, z)
+    p, mean, scale = _oracle_args(m)
+    y_ref, _ = D.forward(p, D.LIBRARY_SIZES, mean, scale, X)
+    loss_ref, g_ref = D.loss_and_gradient(p, D.LIBRARY_SIZES, mean, scale, X, z)
+    # FP32 arithmetic over at most 64-term sums: a few ulps of FP32 per layer
     assert np.max(np.abs(y - y_ref)) < 1e-5 * (1 + np.max(np.abs(y_ref)))
     assert abs(loss - loss_ref) < 1e-5 * loss_ref
     assert np.max(np.abs(g - g_ref)) < 1e-4 * np.max(np.abs(g_ref))
+
+
+@pytest.mark.gpu
+def test_adam_epoch_matches_the_oracle():
+    from paper_1206_3768_gb300 import binding as cb
+
+    rng = np.random.default_rng(13)
+    n = 700
+    X = rng.normal(size=(n, 8)).astype(np.float32)
+    z = (0.4 * np.tanh(X[:, 0]) - 0.2 * X[:, 5]).astype(np.float32)
+    m = _random_model(cb, 14)
+    p0, mean, scale = _oracle_args(m)
+    m1 = np.zeros(cb.MLP_NPARAM, np.float32)
+    m2 = np.zeros(cb.MLP_NPARAM, np.float32)
+    step = 0
+    pr, r1, r2, rstep = p0, np.zeros(cb.MLP_NPARAM), np.zeros(cb.MLP_NPARAM), 0
+    with cb.Solver(64, 8) as s:
+        for ep in range(2):
+            order = np.random.default_rng(50 + ep).permutation(n)
+            m1, m2, step, loss = cb.chfsi_mlp_adam_epoch(s.ctx, m, m1, m2, step, X, z, order, 128, 1e-3)
+            pr, r1, r2, rstep, lref = D.adam_epoch(pr, r1, r2, rstep, D.LIBRARY_SIZES, mean, scale, X, z,
+                                                   order, 128, 1e-3)
+            assert step == rstep == 6 * (ep + 1)
+            assert abs(loss - lref) < 1e-4 * lref
+    # a parameter moves by at most lr per step; FP32 gradients differ from the oracle's by
+    # ~1e-5 relative, which changes a step only where the gradient entry is tiny
+    diff = np.abs(m.params() - pr)
+    assert np.max(diff) < 2e-4
+    assert np.median(diff) < 1e-6
 
 
 @pytest.mark.gpu
@@ -123,7 +139,7 @@ def test_mlp_training_fits_a_smooth_target():
     from paper_1206_3768_gb300 import binding as cb
 
     rng = np.random.default_rng(4)
-    X = rng.normal(size=(4000, 4)).astype(np.float32)
+    X = rng.normal(size=(4000, 8)).astype(np.float32)
     z = (0.5 * np.tanh(X[:, 0]) - 0.3 * X[:, 1] + 0.2 * X[:, 2] * X[:, 3]).astype(np.float32)
     m = cb.chfsi_mlp_init(5)
     with cb.Solver(64, 8) as s:
@@ -133,8 +149,27 @@ def test_mlp_training_fits_a_smooth_target():
     assert loss1 < 0.05 * loss0, (loss0, loss1, loss)
 
 
+def _cpu_degrees(theta, r, a, b, tau, dmin, dmax, n_wanted, g):
+    """The closed-form rule with the rate correction exp(g) per column (the learned form),
+    columns past n_wanted taking the largest wanted degree."""
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    d = np.empty(len(theta), dtype=np.int64)
+    for i, (th, ri) in enumerate(zip(theta, r)):
+        if ri <= tau:
+            d[i] = dmin
+            continue
+        t = abs((th - c) / e)
+        if t <= 1:
+            d[i] = dmax
+            continue
+        need = math.log(ri / tau) / (math.log(t + math.sqrt(t * t - 1)) * math.exp(min(3, max(-3, g[i]))))
+        d[i] = dmax if not need < dmax else min(dmax, max(dmin, math.ceil(need)))
+    d[n_wanted:] = max([dmin] + list(d[:n_wanted]))
+    return d
+
+
 @pytest.mark.gpu
-def test_untrained_model_reproduces_the_closed_form_degrees():
+def test_untrained_and_trained_models_give_the_learned_rule_degrees():
     from paper_1206_3768_gb300 import binding as cb
 
     rng = np.random.default_rng(6)
@@ -142,15 +177,67 @@ def test_untrained_model_reproduces_the_closed_form_degrees():
     theta = np.sort(rng.uniform(-1.0, 0.5, m_act))
     r = 10.0 ** rng.uniform(-11, -2, m_act)
     a, b, tau = 0.5, 3.0, 1e-10
+    th_d, r_d = torch.tensor(theta, device=DEV), torch.tensor(r, device=DEV)
+    model = _random_model(cb, 21)
     with cb.Solver(64, 64) as s:
-        d0 = cb.chfsi_degrees(s.ctx, torch.tensor(theta, device=DEV), torch.tensor(r, device=DEV),
-                              a, b, tau, 4, 40, 30)
+        d0 = cb.chfsi_degrees(s.ctx, th_d, r_d, a, b, tau, 4, 40, 30).cpu().numpy()
         cb.chfsi_set_degree_model(s.ctx, cb.chfsi_mlp_init(9))
-        d1 = cb.chfsi_degrees(s.ctx, torch.tensor(theta, device=DEV), torch.tensor(r, device=DEV),
-                              a, b, tau, 4, 40, 30)
+        d1 = cb.chfsi_degrees(s.ctx, th_d, r_d, a, b, tau, 4, 40, 30).cpu().numpy()
+        cb.chfsi_set_degree_model(s.ctx, model)
+        d2 = cb.chfsi_degrees(s.ctx, th_d, r_d, a, b, tau, 4, 40, 30).cpu().numpy()
     ref = O.adaptive_degrees(theta, r, a, b, tau, 4, 40, 30)
-    assert list(d0.cpu().numpy()) == list(ref)
-    assert list(d1.cpu().numpy()) == list(ref)
+    assert list(d0) == list(ref)
+    assert list(d1) == list(ref)          # zero output layer: the closed form exactly
+    # the inputs without history (first loop), the model with its weights rounded to FP16
+    e, c = 0.5 * (b - a), 0.5 * (b + a)
+    lr = np.log10(r / tau)
+    X = np.stack([lr, lr, lr, 0 * lr, 0 * lr, (theta - c) / e, np.full(m_act, (theta[0] - c) / e),
+                  np.full(m_act, (a - theta[0]) / (b - theta[0]))], axis=1).astype(np.float32)
+    p16 = model.params().astype(np.float16).astype(np.float64)
+    mean16 = np.array(model.mean, np.float32).astype(np.float16).astype(np.float64)
+    scale16 = np.array(model.scale, np.float32).astype(np.float16).astype(np.float64)
+    g, _ = D.forward(p16, D.LIBRARY_SIZES, mean16, scale16, X)
+    want = _cpu_degrees(theta, r, a, b, tau, 4, 40, 30, g)
+    # FP32 evaluation on the GPU: a degree may differ by one where ceil() sits on a boundary
+    assert np.max(np.abs(d2.astype(np.int64) - want)) <= 1
+    assert np.mean(d2 == want) >= 0.9
+    assert not np.array_equal(want, ref)  # the random model does change the degrees
+
+
+@pytest.mark.gpu
+def test_degree_log_records_the_solver_inputs_and_the_next_residual():
+    from paper_1206_3768_gb300 import binding as cb
+
+    seq = inputs.planted_sequence("c2", n=520, N=2, nev=20, blk=26, device=DEV, seed_offset=7)
+    with cb.Solver(520, 26, deg_min=4, deg_max=40) as s:
+        cb.chfsi_degree_log_start(s.ctx, 100000)
+        cb.chfsi_reset_warm_state(s.ctx)
+        _, _, st = cb.chfsi_solve_sequence(s.ctx, [p.A for p in seq.problems], [p.B for p in seq.problems],
+                                           20, 26, 0, 1e-10)
+        log = cb.chfsi_degree_log_read(s.ctx)
+    F = dm.FIELDS
+    assert log.shape[1] == len(F) == cb.DEGREE_LOG_FIELDS
+    assert log.shape[0] == sum(x["filtered_vectors"] for x in st)
+    r, tau, d = log[:, F.index("r")], log[:, F.index("tau")], log[:, F.index("d")]
+    x0, x1, x2 = log[:, F.index("x0")], log[:, F.index("x1")], log[:, F.index("x2")]
+    assert np.allclose(x0, np.log10(r / tau), rtol=1e-6, atol=1e-5)
+    assert np.all(np.isfinite(log[:, F.index("r_next")]))
+    assert np.all((d >= 4) & (d <= 40))
+    # history: in a problem's first loop the previous residuals repeat the current one; later
+    # a vector's x1 is the log residual it had one loop earlier (same global index)
+    for p in (0, 1):
+        rows = log[log[:, 0] == p]
+        first = rows[rows[:, 1] == rows[0, 1]]
+        assert np.allclose(first[:, F.index("x1")], first[:, F.index("x0")], atol=1e-5)
+        key = {(int(k), int(g)): row for k, g, row in zip(rows[:, 1], rows[:, 2], rows)}
+        hits = 0
+        for row in rows:
+            prev = key.get((int(row[1]) - 1, int(row[2])))
+            if prev is not None and np.isclose(prev[F.index("tau")], row[F.index("tau")]):
+                assert abs(row[F.index("x1")] - prev[F.index("x0")]) < 1e-4
+                assert row[F.index("x3")] == prev[F.index("d")]
+                hits += 1
+        assert hits > 0
 
 
 @pytest.mark.gpu

@@ -1,17 +1,21 @@
 """Benchmark: converged eigenpairs per second of warm-started ChFSI sequences on GB300.
 
-One step = one full sequence solve (the whole hot path: reduction, Lanczos bound,
-Chebyshev filter, Cholesky QR, Rayleigh-Ritz, locking, back-transform) of the FLAPW-shaped
-workload: n = 2600, nev = 100, blk = 130, adaptive degree in [8, 25], 20 correlated
-problems (first cold, the rest warm-started), cond(B) = 1e4, planted spectrum.  Inputs are
-seeded synthetic matrices resident in HBM (4.3 GB per step, larger than L2).
+The workload is the mixed-precision sequence: n = 9300, nev = 256, blk = 320, filter
+degree 20, 20 correlated problems (generated like the n = 512 case: B = I + 0.1 G^H G/n,
+planted spectrum, eigenvectors rotated between problems), first problem cold, the rest
+warm-started from the previous eigenvectors.  One step is one problem of this sequence,
+taken cyclically (the whole hot path: reduction, Lanczos bound, Chebyshev filter,
+re-orthonormalisation, Rayleigh-Ritz, locking, back-transform); the problem after the last
+one is the first again and starts cold, so K = 20 timed steps solve the whole sequence once
+(one cold and 19 warm problems), whatever the warm-up.  Inputs are seeded synthetic
+matrices resident in HBM (27.7 GB of A and B, larger than L2).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun each rank solves its own independent sequence (different seed): the units
 (eigenpairs) of all ranks are summed and divided by the slowest rank's time ("weak").
-``--impl reference`` times the CPU oracle (NumPy/SciPy FP64) on a bounded sample of the
-same workload; only rank 0 runs it.
+``--impl reference`` times the CPU oracle (NumPy/SciPy FP64) on the same workload, one
+filter loop per step; only rank 0 runs it.
 """
 from __future__ import annotations
 
@@ -34,7 +38,12 @@ import torch  # noqa: E402
 
 METRIC = "converged eigenpairs/s per sequence & filter % tensor peak vs plain FP64 @res≤1e-10"
 UNIT = "eigenpairs/s"
-WORKLOAD = "c2"
+WORKLOAD = "c3"
+WORKLOAD_TEXT = {
+    "c2": "n=2600 nev=100 blk=130 deg adaptive 8-25 cond(B)=1e4",
+    "c3": "n=9300 nev=256 blk=320 deg=20 B=I+0.1G^HG/n",
+    "c5": "n=13400 nev=1000 blk=1200 deg adaptive 4-40 B=I+0.1G^HG/n",
+}
 
 
 def _dist():
@@ -123,56 +132,139 @@ def combine_ranks(ms: float, units: float, device="cpu"):
     return float(t.item()), float(c.item())
 
 
-def load_workload(device, rank: int, name: str = WORKLOAD, N=None):
+def step_schedule(first: int, count: int, N: int):
+    """Problem index and cold flag of the steps first .. first + count - 1 of the cyclic
+    sequence: step s solves problem s mod N, cold when that is the first problem."""
+    return [(s % N, s % N == 0) for s in range(first, first + count)]
+
+
+def segments(first: int, count: int, N: int):
+    """The steps first .. first + count - 1 as runs of consecutive problems
+    [(start problem, length, cold start)], split where the sequence starts over."""
+    out = []
+    s, left = first, count
+    while left > 0:
+        p = s % N
+        ln = min(left, N - p)
+        out.append((p, ln, p == 0))
+        s += ln
+        left -= ln
+    return out
+
+
+def summary(values) -> dict:
+    """Percentiles of a list of non-negative errors (every eigenpair of the timed steps)."""
+    v = np.asarray(values, dtype=np.float64).ravel()
+    if v.size == 0:
+        return {}
+    return {"count": int(v.size), "p50": float(np.percentile(v, 50)), "p90": float(np.percentile(v, 90)),
+            "p99": float(np.percentile(v, 99)), "max": float(v.max())}
+
+
+def load_workload(device, rank: int, name: str = WORKLOAD, N=None, keep_vectors=False):
     from paper_1206_3768_gb300 import inputs
 
-    return inputs.planted_sequence(name, device=device, keep_vectors=False, seed_offset=rank, N=N)
+    return inputs.planted_sequence(name, device=device, keep_vectors=keep_vectors, seed_offset=rank, N=N)
 
 
-def cpu_oracle_sample(seq, problems: int):
-    """Time the oracle on the first `problems` problems of the sequence (host cores)."""
-    import oracle.chfsi_oracle as O
-
-    As = [np.tril(p.A.cpu().numpy()) for p in seq.problems[:problems]]
-    Bs = [np.tril(p.B.cpu().numpy()) for p in seq.problems[:problems]]
-    t0 = time.perf_counter()
-    out = O.chfsi_solve_sequence(As, Bs, seq.nev, seq.blk, seq.tol, deg=seq.deg,
-                                 deg_min=seq.deg_min, deg_max=seq.deg_max)
-    dt = time.perf_counter() - t0
-    pairs = sum(int(np.isfinite(lam).sum()) for lam, _, _ in out)
-    return pairs, dt
+def _workload_text(name, seq, N):
+    return (f"{name}: {WORKLOAD_TEXT.get(name, f'n={seq.n} nev={seq.nev} blk={seq.blk}')} N={N}, "
+            "planted spectrum, first problem cold, rest warm; one step = one problem of the "
+            "cyclic sequence (K = N steps cover it once)")
 
 
 def run_reference(args):
+    """The oracle on the host cores, on the same workload: one step is one filter loop of
+    the oracle's Algorithm 1 (the first loop of a problem also does its reduction, Lanczos
+    bound and start-up), the loops running through the sequence in order (problem 0 cold,
+    each later problem warm-started from the oracle's own previous result); the unit count
+    is the pairs the timed loops locked."""
+    import oracle.chfsi_oracle as O
+
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    seq = load_workload("cpu", 0, N=args.cpu_problems)
     k = max(1, args.steps)
     w = max(0, args.warmup)
-    # Warm-up steps on a one-problem sample, timed steps on the sample of --cpu-problems.
+    n_prob = args.ref_problems
+    dev = "cuda" if torch.cuda.is_available() else "cpu"   # input generation only
+    seq = load_workload(dev, 0, name=args.workload, N=n_prob)
+    As = [np.tril(p.A.cpu().numpy()) for p in seq.problems]
+    Bs = [np.tril(p.B.cpu().numpy()) for p in seq.problems]
+    del seq.problems[:]
+    if dev == "cuda":
+        torch.cuda.empty_cache()
+    cfg = __import__("paper_1206_3768_gb300.inputs", fromlist=["CONFIGS"]).CONFIGS[args.workload]
+
+    def loops():
+        warm = None
+        ell = 0
+        while True:
+            gen = O.chfsi_solve_loops(As[ell], Bs[ell], cfg["nev"], cfg["blk"], cfg["tol"],
+                                      deg=cfg["deg"], deg_min=cfg["deg_min"], deg_max=cfg["deg_max"],
+                                      warm=warm)
+            while True:
+                try:
+                    yield ell, next(gen)
+                except StopIteration as done:
+                    _, _, warm, _ = done.value
+                    break
+            ell += 1
+            if ell == n_prob:
+                raise RuntimeError("reference sample ran past its generated problems")
+
+    it = loops()
     for _ in range(w):
-        cpu_oracle_sample(seq, 1)
-    times, pairs_tot = [], 0
+        next(it)
+    t0 = time.perf_counter()
+    locked, problems = 0, set()
     for _ in range(k):
-        pairs, dt = cpu_oracle_sample(seq, args.cpu_problems)
-        times.append(dt)
-        pairs_tot += pairs
-    total = sum(times)
-    value = pairs_tot / total
+        ell, nl = next(it)
+        locked += nl
+        problems.add(ell)
+    total = time.perf_counter() - t0
+    value = locked / total
     cores = os.cpu_count()
+    sample = (f"{k} filter loops of the oracle after {w} warm-up loops, over problems "
+              f"{sorted(problems)} of the sequence (problem 0 cold), {locked} pairs locked, {total:.1f} s")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": k, "warmup": w, "ms_per_step": 1e3 * total / k, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: n=2600 nev=100 blk=130 deg adaptive 8-25 cond(B)=1e4",
-                   "sample_problems": args.cpu_problems},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"first {args.cpu_problems} problems (1 cold + "
-                                   f"{args.cpu_problems - 1} warm) of the n=2600 sequence"},
+        "config": {"workload": _workload_text(args.workload, None, cfg["N"]).replace(
+                       "one step = one problem of the cyclic sequence (K = N steps cover it once)",
+                       "one step = one filter loop of the oracle"),
+                   "sample_problems": sorted(problems)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_warm_problem(seq, ell: int, budget_s: float):
+    """The oracle on problem ell of the sequence, warm-started from the planted eigenvectors
+    and eigenvalues of problem ell - 1 (exact input data, the state a converged previous solve
+    leaves), loop by loop until it finishes or the time budget is spent.  Returns (pairs
+    locked, seconds, loops, finished, eigenvalues)."""
+    import oracle.chfsi_oracle as O
+
+    prev, cur = seq.problems[ell - 1], seq.problems[ell]
+    A = np.tril(cur.A.cpu().numpy())
+    B = np.tril(cur.B.cpu().numpy())
+    warm = O.WarmState(X=prev.X[:, :seq.blk].cpu().numpy(), lam=np.array(prev.lam[:seq.blk]))
+    t0 = time.perf_counter()
+    gen = O.chfsi_solve_loops(A, B, seq.nev, seq.blk, seq.tol, deg=seq.deg, deg_min=seq.deg_min,
+                              deg_max=seq.deg_max, warm=warm)
+    locked, loops, lam = 0, 0, None
+    while True:
+        try:
+            locked += next(gen)
+            loops += 1
+        except StopIteration as done:
+            lam = done.value[0]
+            return int(np.isfinite(lam).sum()), time.perf_counter() - t0, loops, True, lam
+        if time.perf_counter() - t0 > budget_s:
+            return locked, time.perf_counter() - t0, loops, False, None
 
 
 def run_ours(args):
@@ -186,23 +278,26 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    seq = load_workload(dev, rank, name=args.workload, N=args.problems)
+    want_cpu = rank == 0 and ws == 1 and not args.no_cpu
+    t_gen = time.perf_counter()
+    seq = load_workload(dev, rank, name=args.workload, N=args.problems,
+                        keep_vectors={0} if want_cpu else False)
     n, nev, blk, N = seq.n, seq.nev, seq.blk, len(seq.problems)
-    As = [cb.fortran(torch.tril(p.A)) for p in seq.problems]
-    Bs = [cb.fortran(torch.tril(p.B)) for p in seq.problems]
+    # lower triangles, column-major; B is common to the whole sequence (one copy)
+    B_low = cb.fortran(torch.tril(seq.problems[0].B))
+    As, Bs = [], []
+    for p in seq.problems:
+        As.append(cb.fortran(torch.tril(p.A)))
+        Bs.append(B_low)
+        if not (want_cpu and p is seq.problems[1]):
+            p.A = None
+    lam_planted = [p.lam[:nev].copy() for p in seq.problems]
+    lam_scale = [float(np.max(np.abs(p.lam))) for p in seq.problems]
     torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.current_stream(dev)
-    solver = cb.Solver(n, blk, stream=stream, deg_min=seq.deg_min, deg_max=seq.deg_max)
-    ctx = solver.ctx
-
-    def step(A_list, B_list, want_vectors=True):
-        cb.chfsi_reset_warm_state(ctx)
-        return cb.chfsi_solve_sequence(ctx, A_list, B_list, nev, blk, seq.deg, seq.tol,
-                                       want_vectors=want_vectors)
-
-    for _ in range(args.warmup):
-        step(As, Bs)
-    torch.cuda.synchronize()
+    W, K = args.warmup, args.steps
+    deg = seq.deg
 
     def barrier():
         if ws > 1:
@@ -210,24 +305,40 @@ def run_ours(args):
 
             dist.barrier()
 
+    def run_arm(ctx, want_vectors):
+        """W untimed then K timed steps on ctx; returns (ms, evals by problem, evecs by problem,
+        stats of the timed steps in order)."""
+        for p, cold in step_schedule(0, W, N):
+            if cold:
+                cb.chfsi_reset_warm_state(ctx)
+            cb.chfsi_solve_next(ctx, As[p], Bs[p], nev, blk, deg, seq.tol, want_vectors=False)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        evals, evecs, stats = {}, {}, []
+        e0.record(stream)
+        for p, cold in step_schedule(W, K, N):
+            if cold:
+                cb.chfsi_reset_warm_state(ctx)
+            ev, X, st = cb.chfsi_solve_next(ctx, As[p], Bs[p], nev, blk, deg, seq.tol,
+                                            want_vectors=want_vectors)
+            evals[p], evecs[p] = ev, X
+            st["problem"] = p
+            stats.append(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1), evals, evecs, stats
+
+    solver = cb.Solver(n, blk, stream=stream, deg_min=seq.deg_min, deg_max=seq.deg_max)
+    ctx = solver.ctx
     sampler = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
     sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    all_stats = []
-    converged = 0
-    e0.record(stream)
-    for _ in range(args.steps):
-        evals, evecs, stats = step(As, Bs)
-        all_stats.extend(stats)
-        converged += int(torch.isfinite(evals).sum())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    ms, evals, evecs, all_stats = run_arm(ctx, want_vectors=True)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
+    converged = sum(int(torch.isfinite(e).sum()) for e in [evals[p] for p, _ in step_schedule(W, K, N)])
     ms_max, units = combine_ranks(ms, converged, dev)
     value = units / (ms_max / 1e3)
     max_resid = max(s["max_resid"] for s in all_stats)
@@ -247,8 +358,10 @@ def run_ours(args):
     if os.path.exists(tfile) and products > 0 and os.environ.get("CHFSI_OZ_KERNEL", "tc") != "mma":
         try:
             with open(tfile) as f:
-                ratio = float(json.load(f)["dram_bytes_over_slice_bytes"])
-            traffic = ratio * sum(s["filter_slice_bytes"] for s in all_stats) / products
+                tj = json.load(f)
+            if tj.get("current", True):
+                traffic = float(tj["dram_bytes_over_slice_bytes"]) * sum(
+                    s["filter_slice_bytes"] for s in all_stats) / products
         except (OSError, ValueError, KeyError):
             traffic = None
     if t_flops > 0:
@@ -274,14 +387,38 @@ def run_ours(args):
                     "frac": (achieved / fp64_peak) if achieved else None, "traffic": traffic,
                     "peak_note": f"FP64 = {peak_kind} bf16 sustained x 1.25/2250 (nominal FP64/bf16 "
                                  "ratio); achieved counts 8 flops per complex FMA"}
-    phase = {k: sum(s[k] for s in all_stats) / args.steps for k in
-             ("t_reduce_ms", "t_lanczos_ms", "t_filter_ms", "t_filter_gemm_ms", "t_qr_ms", "t_small_ms",
-              "t_rr_ms", "t_eig_ms", "t_resid_ms", "t_total_ms")}
+    phase_keys = ("t_reduce_ms", "t_lanczos_ms", "t_filter_ms", "t_filter_gemm_ms", "t_qr_ms", "t_small_ms",
+                  "t_rr_ms", "t_eig_ms", "t_resid_ms", "t_total_ms")
+    phase = {k: sum(s[k] for s in all_stats) for k in phase_keys}
+    per_problem = [{"problem": s["problem"], "ms": s["t_total_ms"], "loops": s["loops"],
+                    "filtered_vectors": s["filtered_vectors"]} for s in all_stats]
+    cold_ms = [s["t_total_ms"] for s in all_stats if s["problem"] == 0]
+    warm_ms = [s["t_total_ms"] for s in all_stats if s["problem"] != 0]
 
-    # ---- deviation angles between eigenvectors of adjacent problems (Section 2.2, Fig. 1),
-    # from the last timed step's eigenvectors (outside the timed region)
+    # ---- per-eigenpair accuracy of the timed steps: eigenvalues against the planted ones and
+    # generalized residuals ||A x - lam B x|| / (||A||_2 ||x||) (torch on the GPU, outside
+    # the timed region; ||A||_2 = max |lam| for the planted pencil with ||B|| ~ 1)
+    def pair_errors(evs, vecs):
+        e_pl, res = [], []
+        for p in sorted(evs):
+            lam = evs[p].cpu().numpy()
+            e_pl.append(np.abs(lam - lam_planted[p]) / lam_scale[p])
+            if vecs.get(p) is not None:
+                Af = As[p] + torch.tril(As[p], -1).mH
+                Bf = B_low + torch.tril(B_low, -1).mH
+                X = vecs[p]
+                R = Af @ X - (Bf @ X) * evs[p].to(X.dtype).unsqueeze(0)
+                anorm = torch.linalg.matrix_norm(Af, ord=2) if n <= 3000 else lam_scale[p]
+                res.append((torch.linalg.vector_norm(R, dim=0) / (anorm * torch.linalg.vector_norm(X, dim=0)))
+                           .cpu().numpy())
+                del Af, Bf, R
+        return np.concatenate(e_pl), (np.concatenate(res) if res else np.zeros(0))
+
+    err_mixed, res_mixed = pair_errors(evals, evecs)
+
+    # ---- deviation angles between eigenvectors of adjacent problems (Section 2.2, Fig. 1)
     dev_angles = None
-    if not args.no_angles and evecs is not None and N > 1:
+    if not args.no_angles and N > 1 and all(evecs.get(p) is not None for p in range(N)):
         medians, maxs = [], []
         for ell in range(1, N):
             th, _ = cb.chfsi_deviation_angles(ctx, evecs[ell - 1], evecs[ell], Bs[ell])
@@ -291,118 +428,99 @@ def run_ours(args):
                       "note": "angle between x_i of problem l-1 and its associated x of problem l "
                               "(B-inner product), l = 1..N-1; a max near pi/2 marks an "
                               "eigenvalue crossing the nev boundary (its partner is not computed)"}
+    del evecs
 
-    # ---- a direct solver on the same problem for context (library code, not this path):
-    # torch.linalg Cholesky, triangular solves and the dense Hermitian eigensolver (all
-    # eigenpairs, from which the nev lowest are kept), one cold problem
-    direct = None
-    if not args.no_direct:
-        A0 = seq.problems[0].A
-        B0 = seq.problems[0].B
-        torch.linalg.eigh(torch.eye(64, dtype=torch.complex128, device=dev))  # library warm-up
-        torch.cuda.synchronize()
-        d0 = torch.cuda.Event(enable_timing=True)
-        d1 = torch.cuda.Event(enable_timing=True)
-        d0.record(stream)
-        Lc = torch.linalg.cholesky(B0)
-        T1 = torch.linalg.solve_triangular(Lc, A0, upper=False)
-        Hd = torch.linalg.solve_triangular(Lc, T1.mH, upper=False).mH
-        wd, _ = torch.linalg.eigh(0.5 * (Hd + Hd.mH))
-        d1.record(stream)
-        torch.cuda.synchronize()
-        dms = d0.elapsed_time(d1)
-        err = float((wd[:nev].cpu().numpy() - seq.problems[0].lam[:nev]).__abs__().max())
-        direct = {"value": nev / (dms / 1e3), "unit": UNIT, "ms_per_problem": dms,
-                  "kind": "torch.linalg cholesky + solve_triangular + eigh (cuSOLVER), one cold problem",
-                  "max_abs_eig_err": err}
+    # ---- the plain FP64 form on the same workload, same warm-up and timed steps
+    plain = None
+    if not args.no_plain:
+        with cb.Solver(n, blk, stream=stream, deg_min=seq.deg_min, deg_max=seq.deg_max, precision=0) as s64:
+            pms, ev64, vec64, st64 = run_arm(s64.ctx, want_vectors=True)
+        err64, res64 = pair_errors(ev64, vec64)
+        del vec64
+        diff = np.concatenate([np.abs(evals[p].cpu().numpy() - ev64[p].cpu().numpy()) / lam_scale[p]
+                               for p in sorted(evals)])
+        conv64 = sum(int(torch.isfinite(ev64[p]).sum()) for p, _ in step_schedule(W, K, N))
+        plain = {"value": conv64 / (pms / 1e3), "ms_per_step": pms / K, "steps": K, "warmup": W,
+                 "max_resid": max(s["max_resid"] for s in st64),
+                 "phase_ms": {k: sum(s[k] for s in st64) for k in phase_keys},
+                 "per_eigenpair": {
+                     "eig_diff_mixed_vs_fp64": summary(diff),
+                     "eig_err_mixed_vs_planted": summary(err_mixed),
+                     "eig_err_fp64_vs_planted": summary(err64),
+                     "resid_mixed": summary(res_mixed),
+                     "resid_fp64": summary(res64),
+                     "note": "every eigenpair of the timed steps; eigenvalue errors relative to "
+                             "max|lambda| of the problem; residuals ||Ax - lam Bx|| / (||A|| ||x||)"}}
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies inside the region
+    # ---- end to end through the C ABI with host buffers (pinned): the same warm-up and timed
+    # steps, each problem's A and B copied from the host inside the region (the library
+    # stages them), eigenvalues and eigenvectors copied back
     e2e = None
     if not args.no_e2e:
-        Ah = [a.mT.contiguous().cpu().pin_memory().mT for a in As]
-        Bh = [b.mT.contiguous().cpu().pin_memory().mT for b in Bs]
-        evecs_h = None
-        steps_e2e = max(1, min(args.steps, 2))
-        step_host = lambda: (cb.chfsi_reset_warm_state(ctx),
-                             cb.chfsi_solve_sequence(ctx, Ah, Bh, nev, blk, seq.deg, seq.tol))
-        step_host()
+        B_h = B_low.mT.contiguous().cpu().pin_memory().mT
+        A_h = [a.mT.contiguous().cpu().pin_memory().mT for a in As]
+        B_hl = [B_h] * N
+
+        def host_steps(first, count):
+            conv = 0
+            for p0, ln, cold in segments(first, count, N):
+                if cold:
+                    cb.chfsi_reset_warm_state(ctx)
+                ev, _, _ = cb.chfsi_solve_sequence(ctx, A_h[p0:p0 + ln], B_hl[p0:p0 + ln], nev, blk, deg,
+                                                   seq.tol, want_vectors=True)
+                conv += int(torch.isfinite(ev).sum())
+            return conv
+
+        host_steps(0, W)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        conv_e2e = 0
-        for _ in range(steps_e2e):
-            _, (ev, evecs_h, _) = step_host()
-            conv_e2e += int(torch.isfinite(ev).sum())
+        conv_e2e = host_steps(W, K)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         t_e, c_e = combine_ranks(dt, conv_e2e, dev)
         e2e = {"value": c_e / t_e, "unit": UNIT,
-               "h2d_bytes_per_step": N * 2 * n * n * 16,
-               "d2h_bytes_per_step": N * (nev * 8 + n * nev * 16), "steps": steps_e2e}
-
-    # ---- the plain FP64 form on the same workload (one timed step), for the speed-up
-    plain = None
-    if not args.no_plain:
-        with cb.Solver(n, blk, stream=stream, deg_min=seq.deg_min, deg_max=seq.deg_max,
-                       precision=0) as s64:
-            cb.chfsi_reset_warm_state(s64.ctx)
-            torch.cuda.synchronize()
-            p0 = torch.cuda.Event(enable_timing=True)
-            p1 = torch.cuda.Event(enable_timing=True)
-            p0.record(stream)
-            ev64, _, st64 = cb.chfsi_solve_sequence(s64.ctx, As, Bs, nev, blk, seq.deg, seq.tol,
-                                                    want_vectors=False)
-            p1.record(stream)
-            torch.cuda.synchronize()
-            pms = p0.elapsed_time(p1)
-        # per-eigenpair difference between the mixed-precision and the FP64 eigenvalues, and
-        # both against the planted spectrum, relative to max |lambda|
-        lam_ref = np.stack([p.lam[:nev] for p in seq.problems])
-        scale = float(np.max(np.abs(np.stack([p.lam for p in seq.problems]))))
-        e_mixed, e_fp64 = evals.cpu().numpy(), ev64.cpu().numpy()
-        plain = {"value": float(torch.isfinite(ev64).sum()) / (pms / 1e3), "ms_per_step": pms,
-                 "steps": 1, "max_resid": max(s["max_resid"] for s in st64),
-                 "max_eig_diff_mixed_vs_fp64": float(np.max(np.abs(e_mixed - e_fp64))) / scale,
-                 "max_eig_err_mixed_vs_planted": float(np.max(np.abs(e_mixed - lam_ref))) / scale,
-                 "max_eig_err_fp64_vs_planted": float(np.max(np.abs(e_fp64 - lam_ref))) / scale}
+               "h2d_bytes_per_step": 2 * n * n * 16,
+               "d2h_bytes_per_step": nev * 8 + n * nev * 16, "steps": K, "warmup": W,
+               "note": "host A and B of every problem staged by the library (copies of the next "
+                       "problem overlap the current solve within a chfsi_solve_sequence call)"}
+        del A_h, B_h, B_hl
 
     # ---- CPU baseline (oracle, host cores, bounded sample), rank 0 at N = 1 only
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        pairs, dt = cpu_oracle_sample(seq, args.cpu_problems)
+    if want_cpu and N > 1:
+        pairs, dt, loops, finished, lam_o = cpu_oracle_warm_problem(seq, 1, args.cpu_budget)
         cpu = {"value": pairs / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"first {args.cpu_problems} problems (1 cold + {args.cpu_problems - 1} "
-                         f"warm) of the same n={n} sequence, NumPy/SciPy FP64, {dt:.1f} s"}
+               "sample": f"problem 1 of the same n={n} sequence warm-started from the planted "
+                         f"eigenvectors of problem 0, NumPy/SciPy FP64: {loops} loops, {pairs} pairs "
+                         f"{'converged' if finished else 'locked before the time budget ran out'}, "
+                         f"{dt:.1f} s"}
+        if finished and 1 in evals:
+            cpu["eig_diff_gpu_vs_oracle"] = summary(np.abs(evals[1].cpu().numpy() - lam_o) / lam_scale[1])
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": W, "ms_per_step": ms_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (bf16 digit-slice tensor products)",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: n={n} nev={nev} blk={blk} "
-                                   + (f"deg={seq.deg} fixed" if seq.deg > 0 else
-                                      f"deg adaptive {seq.deg_min}-{seq.deg_max}")
-                                   + f" N={N} "
-                                   + ("cond(B)=1e4" if args.workload == "c2" else "B=I+0.1G^HG/n")
-                                   + ", planted spectrum, first problem cold, rest warm",
-                       "l2": f"inputs larger than L2 (A,B of {N} problems = "
-                             f"{N * 2 * n * n * 16 / 1e9:.1f} GB per step)",
+            "config": {"workload": _workload_text(args.workload, seq, N),
+                       "l2": f"inputs larger than L2 (A of {N} problems + B = "
+                             f"{(N + 1) * n * n * 16 / 1e9:.1f} GB resident)",
                        "filter_arithmetic": "FP64 results from bf16 digit-slice tensor-core "
                                             "products (exact fp32 chunks, double-float sums): "
                                             "filter 2-7 slices chosen per loop, Rayleigh-Ritz, "
-                                            "reduction and other large products 7 slices; FP32 "
+                                            "reduction and other large products 7-8 slices; FP32 "
                                             "Cholesky QR + FP64 Loewdin steps; FP64 Jacobi "
                                             "eigensolver, residuals and small products",
-                       "tol": seq.tol, "max_resid": max_resid,
-                       "loops_per_problem": [s["loops"] for s in all_stats[:N]],
-                       "filtered_vectors_per_problem": [s["filtered_vectors"] for s in all_stats[:N]],
-                       "phase_ms_per_step": phase},
+                       "tol": seq.tol, "max_resid": max_resid, "generation_s": t_gen,
+                       "cold_problem_ms": cold_ms, "warm_problem_ms_mean": (sum(warm_ms) / len(warm_ms)) if warm_ms else None,
+                       "per_problem": per_problem,
+                       "phase_ms_timed_region": phase},
             "roofline": roofline,
             "plain_fp64": plain,
             "speedup_vs_plain_fp64": (value / plain["value"]) if plain else None,
             "cpu_baseline": cpu,
-            "direct_solver": direct,
             "deviation_angles": dev_angles,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -603,10 +721,13 @@ def run_kernel_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-problems", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=150.0,
+                    help="seconds of oracle work for the cpu_baseline sample (one warm problem)")
+    ap.add_argument("--ref-problems", type=int, default=6,
+                    help="problems generated for the reference arm (its loops run through them)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -617,11 +738,11 @@ def main():
     ap.add_argument("--epochs", type=int, default=150)
     ap.add_argument("--kpoints", type=int, default=32)
     ap.add_argument("--workers", type=int, default=4)
-    ap.add_argument("--workload", choices=["c2", "c3", "c4"], default=WORKLOAD,
-                    help="c2: n=2600 adaptive degree (the headline); c3: n=9300, nev=256, blk=320, "
-                         "deg 20 (the mixed-precision workload; use --problems to bound it); c4: "
-                         "--kpoints sequences of uneven size solved by a batch of --workers "
-                         "contexts against one context (a separate line, not the headline)")
+    ap.add_argument("--workload", choices=["c2", "c3", "c4", "c5"], default=WORKLOAD,
+                    help="c3: n=9300, nev=256, blk=320, deg 20 (the headline); c2: n=2600 adaptive "
+                         "degree; c5: n=13400, blk=1200, degrees in [4, 40]; c4: --kpoints "
+                         "sequences of uneven size solved by a batch of --workers contexts against "
+                         "one context (a separate line, not the headline)")
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--problems", type=int, default=None,
                     help="solve only the first N problems of the sequence (profiling runs)")

@@ -354,6 +354,22 @@ def chfsi_solve(A, B, nev: int, blk: int, tol: float = 1e-10, deg: int = 25,
 
     deg > 0 fixes the filter degree; deg == 0 selects the adaptive rule of reading R8.
     """
+    steps = chfsi_solve_loops(A, B, nev, blk, tol, deg, deg_min, deg_max, warm, V0, seed,
+                              lanczos_k_warm, lanczos_k_cold, max_loops)
+    while True:
+        try:
+            next(steps)
+        except StopIteration as done:
+            return done.value
+
+
+def chfsi_solve_loops(A, B, nev: int, blk: int, tol: float = 1e-10, deg: int = 25,
+                      deg_min: int = 8, deg_max: int = 25, warm: WarmState | None = None,
+                      V0: np.ndarray | None = None, seed: int = 12063768,
+                      lanczos_k_warm: int = 10, lanczos_k_cold: int = 40, max_loops: int = 50):
+    """The same computation as chfsi_solve, as a generator that pauses after every filter loop
+    (yielding the number of pairs that loop locked) and returns chfsi_solve's result when it
+    finishes (the value of StopIteration), so that a caller can time the work loop by loop."""
     n = A.shape[0]
     if not (0 < nev <= blk <= n):
         raise ValueError("need 0 < nev <= blk <= n")
@@ -416,6 +432,7 @@ def chfsi_solve(A, B, nev: int, blk: int, tol: float = 1e-10, deg: int = 25,
             nl = lock_count(r, tau, converged, nev)
             st.loops += 1
             st.locked_per_loop.append(nl)
+            yield nl
             if nl:
                 YL = np.concatenate([YL, Y[:, :nl]], axis=1)
                 lamL = np.concatenate([lamL, theta[:nl]])

@@ -45,6 +45,11 @@ struct chfsi_ctx {
   std::vector<double> deglog;
   int64_t deglog_cap = 0;
   int64_t problems_solved = 0;
+  // staging of host inputs in chfsi_solve_sequence: problem l + 1's A and B are copied on
+  // their own stream into the other of two buffer pairs while problem l solves
+  cudaStream_t copy_stream = nullptr;
+  zd* stage[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaEvent_t staged[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -930,6 +935,35 @@ void release_stream(chfsi_ctx* ctx) {
   ctx->stream = nullptr;
 }
 
+// Buffers and stream for staging host inputs ahead of the solve (allocated on first use).
+int prefetch_resources(chfsi_ctx* ctx) {
+  if (ctx->copy_stream) return CHFSI_OK;
+  const size_t bytes = sizeof(zd) * (size_t)ctx->ws.n_max * (size_t)ctx->ws.n_max;
+  for (int k = 0; k < 2; ++k)
+    for (int j = 0; j < 2; ++j) {
+      cudaError_t e = cudaMalloc((void**)&ctx->stage[k][j], bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, e == cudaErrorMemoryAllocation ? CHFSI_ENOMEM : CHFSI_ECUDA,
+                       "staging buffers for host inputs: %s", cudaGetErrorString(e));
+      }
+    }
+  for (int k = 0; k < 2; ++k) CK(cudaEventCreateWithFlags(&ctx->staged[k], cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  return CHFSI_OK;
+}
+
+void release_prefetch(chfsi_ctx* ctx) {
+  if (ctx->copy_stream) debug_check(cudaStreamSynchronize(ctx->copy_stream), "cudaStreamSynchronize");
+  for (int k = 0; k < 2; ++k) {
+    for (int j = 0; j < 2; ++j)
+      if (ctx->stage[k][j]) debug_check(cudaFree(ctx->stage[k][j]), "cudaFree");
+    if (ctx->staged[k]) debug_check(cudaEventDestroy(ctx->staged[k]), "cudaEventDestroy");
+  }
+  if (ctx->copy_stream) debug_check(cudaStreamDestroy(ctx->copy_stream), "cudaStreamDestroy");
+  ctx->copy_stream = nullptr;
+}
+
 }  // namespace
 
 // ====================================================================== workspace
@@ -1056,6 +1090,7 @@ void chfsi_destroy(chfsi_ctx* ctx) {
   if (ctx->stream) debug_check(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   for (auto e : ctx->ev_pool) debug_check(cudaEventDestroy(e), "cudaEventDestroy");
   if (ctx->mlp_dev) debug_check(cudaFree(ctx->mlp_dev), "cudaFree");
+  release_prefetch(ctx);
   workspace_free(ctx->ws);
   release_stream(ctx);
   delete ctx;
@@ -1090,11 +1125,44 @@ int chfsi_solve_sequence(chfsi_ctx* ctx, int32_t N, int64_t n, const chfsi_z* co
                          chfsi_z* const* evecs, chfsi_stats* st) {
   CKS(validate_sizes(ctx, n, nev, blk));
   if (N <= 0 || !A || !B || !evals) return set_err(ctx, CHFSI_EINVAL, "bad sequence arguments");
+  if (ld < n) return set_err(ctx, CHFSI_EINVAL, "ld < n");
+  entry_guard("chfsi_solve_sequence");
+  cudaSetDevice(ctx->ws.dev);
+  bool host_in = false;
+  for (int l = 0; l < N && !host_in; ++l) host_in = !is_device_ptr(A[l]) || !is_device_ptr(B[l]);
+  if (host_in) CKS(prefetch_resources(ctx));
+  const int64_t lds = ctx->ws.n_max;
+  // queue the copies of problem l's host matrices into buffer pair l & 1
+  auto stage = [&](int l) -> int {
+    const int k = l & 1;
+    const chfsi_z* src[2] = {A[l], B[l]};
+    for (int j = 0; j < 2; ++j)
+      if (!is_device_ptr(src[j]))
+        CK(cudaMemcpy2DAsync(ctx->stage[k][j], lds * sizeof(zd), src[j], ld * sizeof(zd), n * sizeof(zd), n,
+                             cudaMemcpyHostToDevice, ctx->copy_stream));
+    CK(cudaEventRecord(ctx->staged[k], ctx->copy_stream));
+    return CHFSI_OK;
+  };
+  if (host_in) CKS(stage(0));
   for (int l = 0; l < N; ++l) {
-    const int rc = chfsi_solve_next(ctx, n, A[l], ld, B[l], ld, l == 0 ? V0 : nullptr, nev, blk,
+    const chfsi_z* Al = A[l];
+    const chfsi_z* Bl = B[l];
+    int64_t lda = ld, ldb = ld;
+    if (host_in) {
+      // buffer pair (l + 1) & 1 was read by problem l - 1, which has finished
+      if (l + 1 < N) CKS(stage(l + 1));
+      const int k = l & 1;
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->staged[k], 0));
+      if (!is_device_ptr(Al)) { Al = reinterpret_cast<const chfsi_z*>(ctx->stage[k][0]); lda = lds; }
+      if (!is_device_ptr(Bl)) { Bl = reinterpret_cast<const chfsi_z*>(ctx->stage[k][1]); ldb = lds; }
+    }
+    const int rc = chfsi_solve_next(ctx, n, Al, lda, Bl, ldb, l == 0 ? V0 : nullptr, nev, blk,
                                     deg, tol, evals + (int64_t)l * nev,
                                     evecs ? evecs[l] : nullptr, st ? st + l : nullptr);
-    if (rc != CHFSI_OK) return rc;
+    if (rc != CHFSI_OK) {
+      if (host_in) debug_check(cudaStreamSynchronize(ctx->copy_stream), "cudaStreamSynchronize");
+      return rc;
+    }
   }
   return CHFSI_OK;
 }

@@ -16,6 +16,15 @@ eigenvectors and a small drift of the eigenvalues:
     Q_l = Q_{l-1} expm(i eps_l K_l),  K_l = (G + G^H) / (2 sqrt(n)),  eps_l = 1e-2 * 0.5**l
     lam_l = sort(lam_{l-1} + 1e-3 * N(0, 1))  (pairs re-sorted together)
 
+For the large workloads (n above DENSE_ROTATION_MAX_N) the dense rotation would cost an
+n x n Hermitian eigendecomposition and three n^3 products per problem in FP64 (about 35 s
+per problem at n = 9300 on one GB300), so there Q_l = Q_{l-1} U_l with U_l a product of
+ROTATION_LAYERS layers of 2 x 2 unitary rotations between randomly paired columns, angles
+N(0, 1) eps_l / sqrt(2 ROTATION_LAYERS) and random phases: exactly unitary, applied in
+O(n^2) per layer, and giving each eigenvector the same first-order deviation angle as the
+dense rotation (about eps_l / sqrt(2)).  A^(l) = M_l diag(lam_l) M_l^H with M_l = L Q_l kept
+up to date by the same rotations, so one n^3 product (lower block triangle only) remains.
+
 All random draws come from numpy's PCG64 seeded by SeedSequence(12063768 + config_id);
 the dense linear algebra of the construction runs in torch on any device, so the CPU
 and GPU builds of one sequence see the same random numbers.  Nothing here is part of
@@ -47,7 +56,15 @@ CONFIGS = {
     # one k-point of the batched workload (kpoint_sequences draws n per k-point), like c1.
     "c4": dict(config_id=4, n=4500, nev=180, blk=234, deg=20, deg_min=20, deg_max=20, N=10,
                spectrum="uniform_cluster", overlap="mild", tol=1e-10),
+    # n=13400 learned-degree workload: degrees in [4, 40], generated like c1.
+    "c5": dict(config_id=5, n=13400, nev=1000, blk=1200, deg=0, deg_min=4, deg_max=40, N=20,
+               spectrum="uniform_cluster", overlap="mild", tol=1e-10),
 }
+
+# Largest n built with the dense correlation rotation expm(i eps K); larger problems use the
+# layered pairwise rotations described in the module docstring.
+DENSE_ROTATION_MAX_N = 3000
+ROTATION_LAYERS = 8
 
 
 def _preload_cuda_linalg():
@@ -156,21 +173,73 @@ def _overlap(rng, n: int, kind: str, kappa: float, device) -> torch.Tensor:
     raise ValueError(f"unknown overlap kind {kind!r}")
 
 
+def _rotation_layers(rng, n: int, eps: float):
+    """Random pairings and 2 x 2 unitary rotations [[c, -conj(w) s], [w s, c]] (c = cos phi,
+    s = sin phi, w = exp(i psi)) of ROTATION_LAYERS layers, drawn from rng."""
+    layers = []
+    sig = eps / math.sqrt(2.0 * ROTATION_LAYERS)
+    for _ in range(ROTATION_LAYERS):
+        perm = rng.permutation(n)
+        half = n // 2
+        ia, ib = perm[:half], perm[half:2 * half]
+        phi = sig * rng.standard_normal(half)
+        psi = rng.uniform(0.0, 2.0 * math.pi, half)
+        layers.append((ia, ib, np.cos(phi), np.sin(phi) * np.exp(1j * psi)))
+    return layers
+
+
+def _apply_layers(M: torch.Tensor, layers) -> torch.Tensor:
+    """M <- M U for the rotation layers (columns a, b of each pair mixed: new a = c a + ws b,
+    new b = -conj(ws) a + c b), applied in place."""
+    dev = M.device
+    for ia, ib, c, ws in layers:
+        ta = torch.from_numpy(ia).to(dev)
+        tb = torch.from_numpy(ib).to(dev)
+        tc = torch.from_numpy(c).to(dev).to(M.dtype)
+        tw = torch.from_numpy(ws).to(dev)
+        Ma, Mb = M[:, ta], M[:, tb]
+        M[:, ta] = Ma * tc + Mb * tw
+        M[:, tb] = Mb * tc - Ma * tw.conj()
+    return M
+
+
+def _herm_product(M: torch.Tensor, lam: np.ndarray, blocks: int = 8) -> torch.Tensor:
+    """M diag(lam) M^H from the products of its lower block triangle (about half the flops
+    of the full product), completed to full Hermitian storage."""
+    n = M.shape[0]
+    lam_t = torch.from_numpy(lam).to(M.device).to(M.dtype)
+    ML = M * lam_t.unsqueeze(0)
+    A = torch.zeros((n, n), dtype=M.dtype, device=M.device)
+    edges = [round(n * k / blocks) for k in range(blocks + 1)]
+    for k in range(blocks):
+        r0, r1 = edges[k], edges[k + 1]
+        A[r0:r1, :r1] = ML[r0:r1] @ M[:r1].conj().T
+    A = torch.tril(A) + torch.tril(A, -1).conj().T
+    A.diagonal().imag.zero_()
+    return A
+
+
 def planted_sequence(name: str = "c1", *, n: int | None = None, N: int | None = None,
                      nev: int | None = None, blk: int | None = None,
                      spectrum: str | None = None, device="cpu",
-                     keep_vectors: bool = True, seed_offset: int = 0) -> Sequence:
+                     keep_vectors: bool = True, seed_offset: int = 0,
+                     rotation: str | None = None) -> Sequence:
     """Build a seeded correlated sequence for one of the configurations in CONFIGS.
 
     ``n``, ``N``, ``nev``, ``blk`` and ``spectrum`` override the configuration's values
-    (used for small test cases with the same structure).
+    (used for small test cases with the same structure).  ``rotation`` ("dense" or "layers")
+    overrides the choice by size (dense up to DENSE_ROTATION_MAX_N).  ``keep_vectors``: True
+    (planted eigenvectors of every problem), False, or a collection of problem indices.
     """
+    want_x = (lambda ell: True) if keep_vectors is True else (
+        (lambda ell: False) if not keep_vectors else (lambda ell, s=frozenset(keep_vectors): ell in s))
     cfg = dict(CONFIGS[name])
     n = int(n or cfg["n"])
     N = int(N or cfg["N"])
     nev = int(nev or cfg["nev"])
     blk = int(blk or cfg["blk"])
     spectrum = spectrum or cfg["spectrum"]
+    rotation = rotation or ("dense" if n <= DENSE_ROTATION_MAX_N else "layers")
     cid = cfg["config_id"] + 1000 * seed_offset
     rng = _rng(cid)
     dev = torch.device(device)
@@ -183,24 +252,41 @@ def planted_sequence(name: str = "c1", *, n: int | None = None, N: int | None = 
     lam = planted_spectrum(rng, n, spectrum, nev)
     seq = Sequence(n=n, nev=nev, blk=blk, deg=cfg["deg"], deg_min=cfg["deg_min"],
                    deg_max=cfg["deg_max"], tol=cfg["tol"], name=name)
+    M = Lg @ Q if rotation == "layers" else None
+    if M is not None and not keep_vectors:
+        del Q
+        Q = None
     for ell in range(N):
         if ell > 0:
             eps = 1e-2 * 0.5 ** ell
-            Gk = torch.from_numpy(complex_gaussian(rng, (n, n))).to(dev)
-            K = (Gk + Gk.conj().T) / (2.0 * math.sqrt(n))
-            kap, V = torch.linalg.eigh(K)
-            U = (V * torch.exp(1j * eps * kap).unsqueeze(0)) @ V.conj().T
-            Q = Q @ U
+            if rotation == "layers":
+                layers = _rotation_layers(rng, n, eps)
+                M = _apply_layers(M, layers)
+                if Q is not None:
+                    Q = _apply_layers(Q, layers)
+            else:
+                Gk = torch.from_numpy(complex_gaussian(rng, (n, n))).to(dev)
+                K = (Gk + Gk.conj().T) / (2.0 * math.sqrt(n))
+                kap, V = torch.linalg.eigh(K)
+                U = (V * torch.exp(1j * eps * kap).unsqueeze(0)) @ V.conj().T
+                Q = Q @ U
             lam = lam + 1e-3 * rng.standard_normal(n)
             order = np.argsort(lam, kind="stable")
             lam = _enforce_gap(lam[order], nev)
-            Q = Q[:, torch.from_numpy(order).to(dev)]
-        LQ = Lg @ Q
-        lam_t = torch.from_numpy(lam).to(dev).to(torch.complex128)
-        A = (LQ * lam_t.unsqueeze(0)) @ LQ.conj().T
-        A = 0.5 * (A + A.conj().T)
+            idx = torch.from_numpy(order).to(dev)
+            if M is not None:
+                M = M[:, idx]
+            if Q is not None:
+                Q = Q[:, idx]
+        if rotation == "layers":
+            A = _herm_product(M, lam)
+        else:
+            LQ = Lg @ Q
+            lam_t = torch.from_numpy(lam).to(dev).to(torch.complex128)
+            A = (LQ * lam_t.unsqueeze(0)) @ LQ.conj().T
+            A = 0.5 * (A + A.conj().T)
         X = None
-        if keep_vectors:
+        if want_x(ell):
             X = torch.linalg.solve_triangular(Lg.conj().T, Q, upper=True)
         seq.problems.append(Problem(A=A, B=B, lam=lam.copy(), X=X))
     return seq

@@ -337,6 +337,22 @@ def test_host_pointers_give_the_device_result(ctx):
     assert torch.equal(X_d.cpu(), X_h)
 
 
+def test_host_sequence_is_staged_ahead_and_gives_the_device_result(ctx):
+    """chfsi_solve_sequence with host matrices copies problem l + 1 while problem l solves
+    (two staging buffer pairs on a copy stream): the results equal the device-input solve."""
+    seq = inputs.planted_sequence("c1", n=256, N=3, nev=10, blk=16)
+    As = [torch.tril(p.A) for p in seq.problems]
+    Bs = [torch.tril(p.B) for p in seq.problems]
+    cb.chfsi_reset_warm_state(ctx)
+    ev_d, X_d, _ = cb.chfsi_solve_sequence(ctx, [a.to(DEV) for a in As], [b.to(DEV) for b in Bs], 10, 16, 10)
+    cb.chfsi_reset_warm_state(ctx)
+    pinned = [a.mT.contiguous().pin_memory().mT for a in As]
+    ev_h, X_h, _ = cb.chfsi_solve_sequence(ctx, pinned, Bs, 10, 16, 10)
+    assert torch.equal(ev_d, ev_h)
+    for xd, xh in zip(X_d, X_h):
+        assert torch.equal(xd.cpu(), xh)
+
+
 def test_cold_start_with_caller_block(ctx):
     seq = inputs.planted_sequence("c1", n=300, N=1, nev=12, blk=20)
     p = seq.problems[0]

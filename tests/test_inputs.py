@@ -71,3 +71,27 @@ def test_kpoint_sizes_follow_the_rules():
         assert s.nev == math.ceil(0.04 * s.n) and s.blk == math.ceil(1.3 * s.nev)
         assert len(s.problems) == 2 and s.problems[0].A.shape == (s.n, s.n)
     assert len({float(s.problems[0].A[0, 0].real) for s in seqs}) == 4  # independent k-points
+
+
+def test_layered_rotations_keep_the_pencil_planted_and_the_deviation_scale():
+    """The layered pairwise rotations used for large n: exactly unitary (planted eigenpairs and
+    B-orthonormality at rounding level), Hermitian A from the lower block triangle, and a
+    median deviation angle between neighbouring eigenvectors of eps_l / sqrt(2), as with the
+    dense rotation expm(i eps K)."""
+    for rot in ("layers", "dense"):
+        s = inputs.planted_sequence("c1", n=300, N=4, nev=10, blk=16, keep_vectors=True, rotation=rot)
+        B = s.problems[0].B.numpy()
+        for ell, p in enumerate(s.problems):
+            A, X = p.A.numpy(), p.X.numpy()
+            assert np.array_equal(A, A.conj().T)
+            assert np.max(np.abs(A @ X - (B @ X) * p.lam[None, :])) < 1e-11 * np.max(np.abs(p.lam))
+            assert np.allclose(X.conj().T @ B @ X, np.eye(300), atol=1e-10)
+            if ell:
+                M = np.abs(s.problems[ell - 1].X.numpy().conj().T @ B @ X)
+                top = np.sort(M, axis=1)[:, -1]
+                ang = np.median(np.sqrt(np.maximum(0.0, 1.0 - top ** 2)))
+                eps = 1e-2 * 0.5 ** ell
+                assert 0.8 < ang / (eps / math.sqrt(2)) < 1.2, (rot, ell, ang)
+    big = inputs.planted_sequence("c1", n=inputs.DENSE_ROTATION_MAX_N + 1, N=1, nev=4, blk=6,
+                                  keep_vectors=False)
+    assert big.problems[0].A.shape[0] == inputs.DENSE_ROTATION_MAX_N + 1  # the layered path runs

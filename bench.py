@@ -168,7 +168,8 @@ def load_workload(device, rank: int, name: str = WORKLOAD, N=None, keep_vectors=
 
 
 def _workload_text(name, seq, N):
-    return (f"{name}: {WORKLOAD_TEXT.get(name, f'n={seq.n} nev={seq.nev} blk={seq.blk}')} N={N}, "
+    text = WORKLOAD_TEXT[name] if name in WORKLOAD_TEXT else f"n={seq.n} nev={seq.nev} blk={seq.blk}"
+    return (f"{name}: {text} N={N}, "
             "planted spectrum, first problem cold, rest warm; one step = one problem of the "
             "cyclic sequence (K = N steps cover it once)")
 

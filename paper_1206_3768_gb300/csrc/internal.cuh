@@ -115,6 +115,8 @@ cudaError_t herm_from_lower(const zd* src, int64_t lds, zd* dst, int64_t ldd, in
                             int* status, cudaStream_t s);
 cudaError_t mirror_lower(zd* H, int64_t ldh, int n, cudaStream_t s);
 cudaError_t zero_upper(zd* L, int64_t ldl, int n, cudaStream_t s);
+// out2 = [max_i |L_ii|^2, min_i |L_ii|^2] (device): their ratio bounds cond(L L^H) from below.
+cudaError_t diag_ratio(const zd* L, int64_t ldl, int n, double* out2, cudaStream_t s);
 cudaError_t copy_cols(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m,
                       cudaStream_t s);
 cudaError_t compare_equal(const zd* a, int64_t lda, const zd* b, int64_t ldb, int n, int m,

@@ -258,29 +258,33 @@ __global__ void oz_epilogue_kernel(const double* part, int splits, int Mp, int N
 
 // ============================================================================ tcgen05 path
 // The same digit products on the 5th-generation tensor cores: TMA (128-byte swizzle) stages
-// a 128 x 64 bf16 tile of A and an (up to) 144 x 64 tile of B in shared memory, one elected thread
-// issues tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor memory, N up to
-// 144 so that a 130-column block is one tile and the large operand is streamed once), and
-// twelve drain warps fold each exact 960-term chunk into double-float sums.  Tensor memory
-// (512 columns): two sets of accumulators used alternately (one fills while the other
-// drains) and the high words of the sums after them; the low words live in the drain
-// threads' registers.
+// a 128 x 64 bf16 tile of A and an (up to) 160 x 64 tile of B in shared memory, one elected
+// thread issues tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulator in tensor memory, N up
+// to 160 so that a 130-column block is one tile and a 320-column block two), and sixteen
+// drain warps fold each exact 960-term chunk into double-float sums.  Tensor memory (512
+// columns): two sets of accumulators used alternately (one fills while the other drains) and
+// the high words of the sums after them; the low words live in the drain threads' registers.
 // Slice groups: the pairs are issued in groups (s, t0 .. t0 + g - 1) that share the A slice
 // s.  One stage holds one A tile and the B tiles of the whole group (consecutive slices of B
 // are consecutive rows of its buffer, so one TMA box of g x Np rows), and the MMA thread
-// issues the group's products into g accumulators.  The A stream, which bounds this kernel,
-// then carries one tile per group instead of one per pair.  g = 1 for blocks wider than 96
-// columns (two 144-column accumulators at columns 0 and 160, high words at 320); narrower
-// blocks take g up to 7 as tensor memory allows: 2 g accumulators of the block's width
-// (rounded up to 32 columns) plus the high words.
-// Warp 0 issues TMA loads, warp 1 issues MMAs,
-// warps 2..13 drain: three warps per group of 32 tensor-memory lanes; warp h of a lane group
-// owns the 8-column blocks h, h + 3, ..., h + 15 of the tile, so that narrow blocks still
-// spread over all three.  14 warps keep at most 4 warps on each SM sub-partition, so
-// each thread may hold 128 registers.  Every wait on an mbarrier is bounded; a
-// wait that runs out sets DEV_TIMEOUT and the CTA unwinds (waiting, again bounded, for its
-// own copies and MMAs) before freeing tensor memory.
-constexpr int TC_BM = 128, TC_BN = 144, TC_BK = 64, TC_THREADS = 448;
+// issues the group's products into g accumulators.  The A stream then carries one tile per
+// group instead of one per pair.  g = 1 for blocks wider than 96 columns (two 160-column
+// accumulators at columns 0 and 160, high words at 320); narrower blocks take g up to 7 as
+// tensor memory allows: 2 g accumulators of the block's width (rounded up to 32 columns)
+// plus the high words.
+// Clusters: the CTAs of consecutive row tiles (2 or 4) form a cluster and share every B
+// tile: each CTA loads its share of the B box and multicasts it to the cluster, and the MMAs
+// of every CTA release a stage to all of them (the empty barriers count one arrival per
+// CTA), which divides the B stream from L2 by the cluster size.
+// Warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..17 drain: four warps per group of 32
+// tensor-memory lanes; warp h of a lane group owns the 8-column blocks h, h + 4, ... of the
+// tile, so that narrow blocks still spread over all four.  18 warps allow 112 registers per
+// thread.  Every wait on an mbarrier is bounded; a wait that runs out sets DEV_TIMEOUT and the
+// CTA unwinds (waiting, again bounded, for its own copies and MMAs) before freeing tensor
+// memory.
+constexpr int TC_BM = 128, TC_BN = 160, TC_BK = 64;
+constexpr int TC_DWQ = 3;                                  // drain warps per 32-lane quarter
+constexpr int TC_THREADS = 64 + 32 * 4 * TC_DWQ;           // producer, MMA issuer, drain warps
 // The ring holds as many stages as fit: 6 for a 144-row B box, up to TC_MAX_STAGES for narrow
 // blocks, whose smaller B boxes leave room for more of the (dominant) A stream in flight.
 constexpr int TC_MAX_STAGES = 12;
@@ -288,10 +292,12 @@ constexpr int TC_SMEM_BUDGET = 227 * 1024 - 1024 - 512;  // dynamic shared memor
 constexpr int TC_DRAIN_THREADS = TC_THREADS - 64;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per stage
 constexpr int TC_ACC1 = 160, TC_HI = 320;           // tensor-memory columns for groups of one
+constexpr int TC_LO = 480;                         // low words of tile columns 128..159
 constexpr int TC_GROUP_MAX_N = 96;                  // widest block issued in groups of g > 1
 constexpr int TC_GROUP_MAX = 7;
 static_assert((16 * TC_BK * 2) % 1024 == 0, "B stages (16-row multiples) stay 1024-byte aligned");
-static_assert(TC_HI + TC_BN <= 512 && TC_ACC1 + TC_BN <= TC_HI, "tensor-memory layout");
+static_assert(TC_HI + TC_BN <= TC_LO && TC_LO + (TC_BN - 128) <= 512 && TC_ACC1 + TC_BN <= TC_HI,
+              "tensor-memory layout");
 constexpr long kMbarSpinLimit = 1L << 26;
 
 struct TcParams {
@@ -307,6 +313,8 @@ struct TcParams {
   double* part;
   int* status;
   long long spin_limit;                      // polls before a first-level wait gives up
+  int cl;                                    // CTAs per cluster along M sharing the B tiles (1, 2, 4)
+  int tiles_m_pad;                           // tiles_m rounded up to a multiple of cl
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -353,6 +361,25 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+// The same copy delivered to every CTA of the cluster in `mask`, at the same shared-memory
+// offsets (destination and mbarrier) as this CTA's.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                               uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3}], [%4], %5;\n"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -381,6 +408,12 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                ::"r"(bar) : "memory");
 }
+// Arrive (once the issued MMAs complete) on the mbarrier at this offset in every CTA of mask.
+__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n"
+      ::"r"(bar), "h"(mask) : "memory");
+}
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 }
@@ -396,6 +429,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
                ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n"
+               ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
@@ -414,14 +456,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tm = blockIdx.x % p.tiles_m, tn = blockIdx.x / p.tiles_m;
+  const int tm = blockIdx.x % p.tiles_m_pad, tn = blockIdx.x / p.tiles_m_pad;
   const int m0 = tm * TC_BM, n0 = tn * TC_BN;
-  if (p.c_lower && n0 > (m0 + TC_BM - 1) / 2) return;  // tile above the diagonal: not needed
+  // Clusters of p.cl CTAs on consecutive row tiles share every B tile: each CTA loads 1/cl of
+  // the B box and multicasts it to the whole cluster, so all CTAs of a cluster must walk the
+  // same stages.  Their work is therefore decided by the cluster's last row tile (the widest
+  // k-range of a lower-triangular A, the last tile to reach the diagonal); the extra work is
+  // exact (zero blocks of A) or unused (tiles above the diagonal, rows past Mp).
+  const int crank = p.cl > 1 ? (int)cluster_ctarank() : 0;
+  const int m0_last = (tm - crank + p.cl - 1) * TC_BM;
+  const uint16_t cmask = (uint16_t)((1u << p.cl) - 1u);
+  if (p.c_lower && n0 > (m0_last + TC_BM - 1) / 2) return;  // above the diagonal: not needed
   // k-blocks of this CTA: split y takes [y per, (y + 1) per) of the tile's nonzero k-blocks.
   // The work is ordered panel-major: for each panel of at most OZ_CHUNK_KB k-blocks, every
   // slice pair in turn (one exact chunk each), so consecutive chunks reuse the same panel of
   // an A slice from L2 while it is hot.
-  const int nkb = p.a_lower ? min(p.nkb, m0 / TC_BK + TC_BM / TC_BK) : p.nkb;
+  const int nkb = p.a_lower ? min(p.nkb, m0_last / TC_BK + TC_BM / TC_BK) : p.nkb;
   const int ncols = min(TC_BN, ((p.n_real - n0 + 15) / 16) * 16);  // MMA N for this tile
   // split y takes either a range of k-blocks (all groups) or, for short K (one panel), a
   // range of slice groups (all k-blocks)
@@ -440,6 +490,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int G = p.group;
   const uint32_t acc_stride = (uint32_t)p.acc_stride, hi_col = 2u * (uint32_t)G * acc_stride;
   const uint32_t b_pair_bytes = (uint32_t)p.Np * TC_BK * 2;  // B tile of one slice in a group box
+  const int b_share = p.b_box_rows / p.cl;                   // B rows each CTA of a cluster loads
 
   const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
   const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NS;
@@ -448,7 +499,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (tid == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(full0 + 8 * i, 1);
-      mbar_init(empty0 + 8 * i, 1);
+      mbar_init(empty0 + 8 * i, p.cl);  // released by the MMAs of every CTA of the cluster
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
@@ -464,6 +515,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   __syncthreads();
+  // every CTA of the cluster has initialised its barriers before any copy or commit reaches them
+  if (p.cl > 1) cluster_sync_all();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -486,7 +539,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             mbar_expect_tx(fb, TC_A_BYTES + b_stage);
             tma_load_2d(sA_u + stage * TC_A_BYTES, &tmA, kb * TC_BK, arow, fb);
-            tma_load_2d(sB_u + stage * b_stage, &tmB, kb * TC_BK, brow, fb);
+            if (p.cl > 1)  // this CTA's share of the B box, to every CTA of the cluster
+              tma_load_2d_mc(sB_u + stage * b_stage + (uint32_t)(crank * b_share) * (TC_BK * 2), &tmB,
+                             kb * TC_BK, brow + crank * b_share, fb, cmask);
+            else
+              tma_load_2d(sB_u + stage * b_stage, &tmB, kb * TC_BK, brow, fb);
             if (++stage == NS) {
               stage = 0;
               phase ^= 1;
@@ -500,6 +557,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int j = max(0, i - NS); j < i; ++j) {
           long it = 0;
           while (!mbar_try(full0 + 8 * (j % NS), (j / NS) & 1) && ++it < kMbarSpinLimit) {}
+        }
+      } else if (p.cl > 1) {
+        // the B shares this CTA sent to the cluster: every CTA has consumed them (so they have
+        // landed) before this CTA may exit
+        for (int j = max(0, i - NS); j < i; ++j) {
+          long it = 0;
+          while (!mbar_try(empty0 + 8 * (j % NS), (j / NS) & 1) && ++it < kMbarSpinLimit) {}
         }
       }
     }
@@ -537,7 +601,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                        sw128_desc(b_s + (uint32_t)j * b_pair_bytes + kk * 32), idesc,
                        (kb == k0 && kk == 0) ? 0u : 1u);
             }
-            tc_commit(empty0 + 8 * stage);
+            if (p.cl > 1) tc_commit_mc(empty0 + 8 * stage, cmask);
+            else tc_commit(empty0 + 8 * stage);
             if (kb == k1 - 1) tc_commit(accf0 + 8 * (chunk & 1));
             if (++stage == NS) {
               stage = 0;
@@ -554,14 +619,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else {
     // ------------------------------------------------------------ drain warps (2..13)
     // Thread (quarter, lane) of warp h (0..2 within its lane group) owns row 32 * quarter +
-    // lane of the tile and the 8-column blocks h + 3 i (i < 6): the high words of its sums sit
-    // in tensor memory, the low words in lo[] (registers; the block loops below are unrolled
-    // so that every index into lo[] is a constant).  Tensor memory is moved in blocks of 8
-    // columns to keep the live registers within the 128 that 14 warps allow.
+    // lane of the tile and the 8-column blocks h + 3 i: the high words of its sums sit in
+    // tensor memory, the low words of columns 0..127 in lo[] (registers; the block loops below
+    // are unrolled so that every index into lo[] is a constant) and those of columns 128..159
+    // in the last 32 tensor-memory columns (blocks 16..19 are only used with groups of one,
+    // whose high words end at column 480).  Tensor memory is moved in blocks of 8 columns to
+    // keep the live registers within the 128 that 14 warps allow.
     const int quarter = warp & 3;  // tensor-memory lanes 32*quarter .. +31
-    constexpr int kBlocks = TC_BN / 24;  // 8-column blocks per warp
+    constexpr int kRegCols = 128;                                       // columns with lo[] in registers
+    constexpr int kBlocks = (kRegCols / 8 + TC_DWQ - 1) / TC_DWQ;       // register blocks per warp
+    constexpr int kTmBlocks = ((TC_BN - kRegCols) / 8 + TC_DWQ - 1) / TC_DWQ;  // tensor-memory blocks
     const int h = (warp - 2) >> 2;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int reg_cols = min(ncols, kRegCols);
     float lo[kBlocks * 8];
     {
       uint32_t zero[8];
@@ -570,9 +640,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int c = 0; c < kBlocks; ++c) {
         // only the tile's columns: with groups the high words end at the last allocated column
-        if (8 * (3 * c + h) < ncols) tmem_st8(lane_base + hi_col + 8 * (3 * c + h), zero);
+        const int col = 8 * (TC_DWQ * c + h);
+        if (col < reg_cols) tmem_st8(lane_base + hi_col + col, zero);
 #pragma unroll
         for (int j = 0; j < 8; ++j) lo[c * 8 + j] = 0.f;
+      }
+#pragma unroll
+      for (int t = 0; t < kTmBlocks; ++t) {
+        const int col = kRegCols + 8 * (TC_DWQ * t + h);
+        if (col < ncols) {
+          tmem_st8(lane_base + hi_col + col, zero);
+          tmem_st8(lane_base + TC_LO + (col - kRegCols), zero);
+        }
       }
       tmem_wait_st();
     }
@@ -589,8 +668,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t acc_base = lane_base + (uint32_t)b * (uint32_t)G * acc_stride;
 #pragma unroll
       for (int c = 0; c < kBlocks; ++c) {
-        const int col = 8 * (3 * c + h);
-        if (col < ncols) {
+        const int col = 8 * (TC_DWQ * c + h);
+        if (col < reg_cols) {
           uint32_t acc[8], hi[8];
           tmem_ld8(lane_base + hi_col + col, hi);
           float sc = sc0;
@@ -608,18 +687,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tmem_st8(lane_base + hi_col + col, hi);
         }
       }
+#pragma unroll
+      for (int t = 0; t < kTmBlocks; ++t) {  // groups of one: a single pair per chunk
+        const int col = kRegCols + 8 * (TC_DWQ * t + h);
+        if (col < ncols) {
+#pragma unroll
+          for (int half = 0; half < 8; half += 4) {  // four columns at a time (registers)
+            uint32_t acc[4], hi[4], lw[4];
+            tmem_ld4(lane_base + hi_col + col + half, hi);
+            tmem_ld4(lane_base + TC_LO + (col - kRegCols) + half, lw);
+            tmem_ld4(acc_base + col + half, acc);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              float hq = __uint_as_float(hi[q]), lq = __uint_as_float(lw[q]);
+              two_sum_acc(hq, lq, __uint_as_float(acc[q]) * sc0);
+              hi[q] = __float_as_uint(hq);
+              lw[q] = __float_as_uint(lq);
+            }
+            tmem_st4(lane_base + hi_col + col + half, hi);
+            tmem_st4(lane_base + TC_LO + (col - kRegCols) + half, lw);
+          }
+        }
+      }
       tmem_wait_st();
       tc_fence_before();
       mbar_arrive(acce0 + 8 * b);
     }
-    if (ok && !*abort_flag) {
+    if (ok && !*abort_flag && m0 < p.Mp) {
       // partial sums of this split as (hi, lo) pairs: P[split][col * Mp + row]
       float2* P = reinterpret_cast<float2*>(p.part) + (int64_t)blockIdx.y * p.Mp * p.Np;
       const int row = m0 + quarter * 32 + lane;
 #pragma unroll
       for (int c = 0; c < kBlocks; ++c) {
-        const int col0 = 8 * (3 * c + h);
-        if (col0 < ncols) {
+        const int col0 = 8 * (TC_DWQ * c + h);
+        if (col0 < reg_cols) {
           uint32_t hi[8];
           tmem_ld8(lane_base + hi_col + col0, hi);
           tmem_wait_ld();
@@ -631,12 +733,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
+#pragma unroll
+      for (int t = 0; t < kTmBlocks; ++t) {
+        const int col0 = kRegCols + 8 * (TC_DWQ * t + h);
+        if (col0 < ncols) {
+          uint32_t hi[8], lw[8];
+          tmem_ld8(lane_base + hi_col + col0, hi);
+          tmem_ld8(lane_base + TC_LO + (col0 - kRegCols), lw);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int col = n0 + col0 + q;
+            if (col < p.Np)
+              P[(int64_t)col * p.Mp + row] = make_float2(__uint_as_float(hi[q]), __uint_as_float(lw[q]));
+          }
+        }
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+  // no CTA leaves while a CTA of its cluster may still address its shared memory
+  if (p.cl > 1) cluster_sync_all();
 }
 
 // Digit extraction with integer operations only (the FP64 pipe of this part is 1/64 of the
@@ -917,6 +1037,16 @@ static bool oz_grouped_pairs() {
   }();
   return grouped;
 }
+// Largest cluster of CTAs sharing the B tiles of the tcgen05 kernel by multicast: environment
+// variable CHFSI_OZ_CLUSTER (1, 2 or 4; default 4).
+static int oz_cluster_max() {
+  static const int v = [] {
+    const char* e = std::getenv("CHFSI_OZ_CLUSTER");
+    const int c = e ? std::atoi(e) : 4;
+    return c >= 4 ? 4 : (c >= 2 ? 2 : 1);
+  }();
+  return v;
+}
 // Smallest TMA ring a slice group may leave (its B box grows with the group): environment
 // variable CHFSI_OZ_GROUP_MIN_STAGES, default 4, clamped to [2, TC_MAX_STAGES].
 static int oz_group_min_stages() {
@@ -953,7 +1083,8 @@ static bool encode_bf16_map(CUtensorMap* map, const void* ptr, int inner, uint64
 int oz_padded_k(int n) { return ((2 * n + OZ_BK - 1) / OZ_BK) * OZ_BK; }
 int oz_padded_m(int n) { return ((2 * n + OZ_BM - 1) / OZ_BM) * OZ_BM; }
 int oz_padded_n(int m) {
-  return oz_use_tcgen05() ? ((m + 15) / 16) * 16 : ((m + OZ_BN - 1) / OZ_BN) * OZ_BN;
+  // tcgen05: multiples of 32 columns, so that a B box splits into four 8-row-aligned shares
+  return oz_use_tcgen05() ? ((m + 31) / 32) * 32 : ((m + OZ_BN - 1) / OZ_BN) * OZ_BN;
 }
 
 // ---- operands
@@ -1068,19 +1199,31 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
         tp.gc[tp.ngroups] = (unsigned char)std::min(G, S + 2 - si - t0);
         ++tp.ngroups;
       }
-    const int tiles = tp.tiles_m * ((Np + TC_BN - 1) / TC_BN);
-    tp.splits = splits =
-        choose_tc_splits(tiles, tp.nkb, tp.ngroups, oz.part_elems, (int64_t)Mp * Np, &tp.pair_split);
     CUtensorMap mapA, mapB;
     // The B box is min(Np, TC_BN) rows high (g Np for groups of g); a last tile or group
     // narrower than that reads rows past its slices (the next slice, the buffer's spare rows:
     // the allocation holds at least TC_BN rows, or the fill past the map's last row) that
     // the MMAs never use, since their N covers only the tile's own columns.
     tp.b_box_rows = G > 1 ? G * Np : std::min(Np, TC_BN);
+    // Cluster of cl CTAs on consecutive row tiles sharing each B box (each loads b_box_rows /
+    // cl rows, a multiple of 8 so that every share starts on a 1024-byte swizzle atom); the
+    // single-CTA launch when the context shortens its waits (the timeout test exercises that
+    // launch's unwinding) or the grid has too few row tiles.
+    tp.cl = 1;
+    if (oz.wait_limit == 0 && oz_cluster_max() > 1)
+      for (int c = oz_cluster_max(); c >= 2; c /= 2)
+        if (tp.tiles_m >= 2 * c && tp.b_box_rows % (8 * c) == 0) {
+          tp.cl = c;
+          break;
+        }
+    tp.tiles_m_pad = ((tp.tiles_m + tp.cl - 1) / tp.cl) * tp.cl;
+    const int tiles = tp.tiles_m_pad * ((Np + TC_BN - 1) / TC_BN);
+    tp.splits = splits =
+        choose_tc_splits(tiles, tp.nkb, tp.ngroups, oz.part_elems, (int64_t)Mp * Np, &tp.pair_split);
     const uint64_t b_rows = std::max<uint64_t>((uint64_t)b.S * Np, (uint64_t)TC_BN);
     if ((int64_t)b_rows * Kp > (int64_t)b.S_max * b.Np_max * b.Kp_max) return cudaErrorInvalidValue;
     if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)a.S * Mp, TC_BM) ||
-        !encode_bf16_map(&mapB, b.ptr, Kp, b_rows, tp.b_box_rows))
+        !encode_bf16_map(&mapB, b.ptr, Kp, b_rows, tp.b_box_rows / tp.cl))
       return cudaErrorInvalidValue;
     const int b_stage = tp.b_box_rows * TC_BK * 2;
     tp.stages = std::min(TC_MAX_STAGES, TC_SMEM_BUDGET / (TC_A_BYTES + b_stage));
@@ -1090,7 +1233,24 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
         oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 + TC_SMEM_BUDGET + 256);
     if (tc_attr != cudaSuccess) return tc_attr;
     if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
-    oz_gemm_tc_kernel<<<dim3(tiles, splits), TC_THREADS, smem, s>>>(mapA, mapB, tp);
+    if (tp.cl > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(tiles, splits);
+      cfg.blockDim = dim3(TC_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = tp.cl;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, oz_gemm_tc_kernel, mapA, mapB, tp);
+      if (e != cudaSuccess) return e;
+    } else {
+      oz_gemm_tc_kernel<<<dim3(tiles, splits), TC_THREADS, smem, s>>>(mapA, mapB, tp);
+    }
     CHFSI_COUNT_LAUNCH();
     if (ev_gemm_end) cudaEventRecord(ev_gemm_end, s);
     e = cudaGetLastError();

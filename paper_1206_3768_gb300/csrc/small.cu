@@ -340,6 +340,7 @@ struct JacParams {
   int* status;
   int max_sweeps;
   long long spin_limit;  // polls of a grid-barrier wait before it gives up
+  int pairs_per_cta;     // rotation pairs (and 2x as many rows of V) per CTA
 };
 
 constexpr long kBarrierSpinLimit = 8000000;  // polls of an L2 word: a few seconds at most
@@ -388,6 +389,7 @@ __device__ __forceinline__ zd ldcg(const zd* p) { return __ldcg(p); }
 struct Rot { double c, s; zd w; int active; };
 
 constexpr int JAC_THREADS = 256;
+constexpr int kJacSmemMax = 200 * 1024;  // dynamic shared memory a Jacobi CTA may use
 
 __device__ __forceinline__ Rot jacobi_rotation(const zd* src, int mp, int p, int q, double thresh) {
   const double a = ldcg(src + p + (int64_t)p * mp).x;
@@ -414,23 +416,29 @@ __device__ __forceinline__ Rot jacobi_rotation(const zd* src, int mp, int p, int
   return R;
 }
 
-// One CTA per rotation pair.  Per round: thread e (< mp) owns output row (e & 1 ? q : p) of
-// this CTA's pair and column pair t = e >> 1; it loads its four source entries before the
-// rotations are computed (so the L2 latency overlaps them), then writes two entries.  The
-// CTA's two rows of V stay in shared memory for the whole run.
+// CTA c takes the rotation pairs (slots) c*ppc .. c*ppc + ppc - 1 of every round (ppc =
+// P.pairs_per_cta; one pair per CTA while the grid fits, more for large blocks).  Per round,
+// work item e = (k, row, t) of the CTA is output row (row ? q : p) of its k-th pair at column
+// pair t; the item's four source entries are loaded before the round's rotations are
+// computed (so the L2 latency overlaps them) when it is the thread's first item.  The CTA's
+// 2 ppc rows of V (rows 2 slot, 2 slot + 1 of its slots) stay in shared memory for the whole
+// run and take the right rotations of every pair of the round.
 __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) {
   extern __shared__ unsigned char smem_raw[];
-  const int mp = P.mp, half = mp / 2;
+  const int mp = P.mp, half = mp / 2, ppc = P.pairs_per_cta;
   Rot* rot = reinterpret_cast<Rot*>(smem_raw);
-  zd* vrow = reinterpret_cast<zd*>(smem_raw + sizeof(Rot) * (size_t)half);  // 2 x mp
+  zd* vrow = reinterpret_cast<zd*>(smem_raw + sizeof(Rot) * (size_t)half);  // 2 ppc x mp
   __shared__ double red[JAC_THREADS];
   const int tid = threadIdx.x, nt = blockDim.x;
   const unsigned nb = gridDim.x;
   const int cta = blockIdx.x;
+  const int slot0 = cta * ppc;
+  const int nslot = max(0, min(ppc, half - slot0));  // pairs this CTA owns
+  const int items = nslot * mp;                       // work items per round
 
-  // ---- set-up: rows 2cta, 2cta+1 of Ga (padded copy of G) and of V (identity)
-  for (int rr = 0; rr < 2; ++rr) {
-    const int i = 2 * cta + rr;
+  // ---- set-up: rows 2 slot, 2 slot + 1 of Ga (padded copy of G) and of V (identity)
+  for (int rr = 0; rr < 2 * nslot; ++rr) {
+    const int i = 2 * slot0 + rr;
     for (int j = tid; j < mp; j += nt) {
       zd v = zmk(0.0, 0.0);
       if (i < P.m && j < P.m) v = P.G[i + (int64_t)j * P.ldg];
@@ -478,36 +486,42 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) 
     for (int round = 0; round < mp - 1; ++round) {
       const zd* src = parity ? P.Gb : P.Ga;
       zd* dst = parity ? P.Ga : P.Gb;
-      int p, q;
-      pair_of(round, cta, mp, p, q);
-      // this thread's first item: source entries of rows p, q at its column pair
+      // this thread's first item: source entries of its rows at its column pair
       zd m00, m01, m10, m11;
-      if (tid < mp) {
-        int r, s;
-        pair_of(round, tid >> 1, mp, r, s);
+      if (tid < items) {
+        int p, q, r, s;
+        pair_of(round, slot0 + tid / mp, mp, p, q);
+        pair_of(round, (tid % mp) >> 1, mp, r, s);
         m00 = ldcg(src + p + (int64_t)r * mp); m01 = ldcg(src + p + (int64_t)s * mp);
         m10 = ldcg(src + q + (int64_t)r * mp); m11 = ldcg(src + q + (int64_t)s * mp);
       }
       // all rotations of this round (same inputs, same result on every CTA)
+      int any = 0;
       for (int t = tid; t < half; t += nt) {
         int a, b;
         pair_of(round, t, mp, a, b);
         rot[t] = jacobi_rotation(src, mp, a, b, thresh);
+        any |= rot[t].active;
       }
-      __syncthreads();
-      const Rot RP = rot[cta];
-      const zd wpc = zconj(RP.w);  // e^{+i phi}
-      const zd sw = zscale(wpc, RP.s), cw = zscale(wpc, RP.c);
-      for (int e = tid; e < mp; e += nt) {
-        const int t = e >> 1, row = e & 1;
-        int r, s;
+      // a round whose pairs are all below the threshold leaves the matrix as it is: every CTA
+      // reaches the same decision and skips it (no writes, no barrier)
+      if (!__syncthreads_or(any)) continue;
+      for (int e = tid; e < items; e += nt) {
+        const int k = e / mp, e2 = e - k * mp;
+        const int t = e2 >> 1, row = e2 & 1;
+        const int slot = slot0 + k;
+        int p, q, r, s;
+        pair_of(round, slot, mp, p, q);
         pair_of(round, t, mp, r, s);
         if (e != tid) {
           m00 = ldcg(src + p + (int64_t)r * mp); m01 = ldcg(src + p + (int64_t)s * mp);
           m10 = ldcg(src + q + (int64_t)r * mp); m11 = ldcg(src + q + (int64_t)s * mp);
         }
+        const Rot RP = rot[slot];
+        const zd wpc = zconj(RP.w);  // e^{+i phi}
+        const zd sw = zscale(wpc, RP.s), cw = zscale(wpc, RP.c);
         const Rot RR = rot[t];
-        // left: U_P^H = [[c, -s e^{i phi}], [s, c e^{i phi}]]; this thread's row only
+        // left: U_P^H = [[c, -s e^{i phi}], [s, c e^{i phi}]]; this item's row only
         zd l0, l1;
         if (row == 0) {
           l0 = zsub(zscale(m00, RP.c), zmul(sw, m10));
@@ -520,16 +534,16 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) 
         const zd rsw = zscale(RR.w, RR.s), rcw = zscale(RR.w, RR.c);
         zd n0 = zsub(zscale(l0, RR.c), zmul(l1, rsw));
         zd n1 = zadd(zscale(l0, RR.s), zmul(l1, rcw));
-        if (t == cta) {  // diagonal block: exact diagonal result
+        if (t == slot) {  // diagonal block: exact diagonal result
           if (row == 0) { n0.y = 0.0; if (RP.active) n1 = zmk(0.0, 0.0); }
           else { n1.y = 0.0; if (RP.active) n0 = zmk(0.0, 0.0); }
         }
         const int orow = row ? q : p;
         dst[orow + (int64_t)r * mp] = n0;
         dst[orow + (int64_t)s * mp] = n1;
-        // V rows 2cta, 2cta+1 (shared memory): V[i, R] <- V[i, R] U_R
+        // V rows 2 slot + row (shared memory): V[i, R] <- V[i, R] U_R
         if (RR.active) {
-          zd* vi = vrow + row * mp;
+          zd* vi = vrow + (2 * k + row) * mp;
           const zd a0 = vi[r], a1 = vi[s];
           vi[r] = zsub(zscale(a0, RR.c), zmul(a1, rsw));
           vi[s] = zadd(zscale(a0, RR.s), zmul(a1, rcw));
@@ -540,8 +554,8 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) 
     }
   }
   __syncthreads();
-  for (int rr = 0; rr < 2; ++rr) {
-    const int i = 2 * cta + rr;
+  for (int rr = 0; rr < 2 * nslot; ++rr) {
+    const int i = 2 * slot0 + rr;
     for (int j = tid; j < mp; j += nt) P.Vw[i + (int64_t)j * mp] = vrow[rr * mp + j];
   }
   if (cta == 0 && tid == 0) {
@@ -635,13 +649,25 @@ cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64
   cudaError_t e = cudaMemsetAsync(barrier, 0, 4 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   const int half = mp / 2;
-  const size_t smem = sizeof(Rot) * (size_t)half + 2 * sizeof(zd) * (size_t)mp;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // Pairs per CTA: the fewest for which the whole grid is co-resident (a cooperative launch),
+  // each CTA keeping 2 ppc rows of V in shared memory.
+  static const cudaError_t attr = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       kJacSmemMax);
+  if (attr != cudaSuccess) return attr;
+  int ppc = 1;
+  size_t smem = 0;
+  for (;; ++ppc) {
+    smem = sizeof(Rot) * (size_t)half + 2 * sizeof(zd) * (size_t)ppc * mp;
+    if (smem > (size_t)kJacSmemMax) return cudaErrorInvalidValue;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JAC_THREADS, smem);
     if (e != cudaSuccess) return e;
+    if ((int64_t)per_sm * sm_count() >= (half + ppc - 1) / ppc) break;
   }
+  P.pairs_per_cta = ppc;
+  const int grid = (half + ppc - 1) / ppc;
   void* args[] = {(void*)&P};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(half), dim3(JAC_THREADS), args, smem, s);
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JAC_THREADS), args, smem, s);
   CHFSI_COUNT_LAUNCH();
   if (e != cudaSuccess) return e;
   const size_t smem2 = (size_t)m * (sizeof(double) + sizeof(int));

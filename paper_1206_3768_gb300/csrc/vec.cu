@@ -109,6 +109,31 @@ __global__ void zero_upper_kernel(zd* L, int64_t ldl, int n) {
   }
 }
 
+// out[0] = max_i |L_ii|^2, out[1] = min_i |L_ii|^2 (one CTA): a lower bound of cond(L L^H).
+__global__ void diag_ratio_kernel(const zd* L, int64_t ldl, int n, double* out) {
+  __shared__ double mx[256], mn[256];
+  double a = 0.0, b = INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = zabs2(L[i + (int64_t)i * ldl]);
+    a = fmax(a, d);
+    b = fmin(b, d);
+  }
+  mx[threadIdx.x] = a;
+  mn[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      mx[threadIdx.x] = fmax(mx[threadIdx.x], mx[threadIdx.x + o]);
+      mn[threadIdx.x] = fmin(mn[threadIdx.x], mn[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = mx[0];
+    out[1] = mn[0];
+  }
+}
+
 __global__ void copy_cols_kernel(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m,
                                  const int* perm, const int* flag) {
   const int64_t total = (int64_t)n * m;
@@ -725,6 +750,11 @@ cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, doub
   if (m <= 0) return cudaSuccess;
   degrees_kernel<<<1, 256, m * sizeof(int), s>>>(theta, r, m, a, b, tau, dmin, dmax, n_wanted,
                                                  deg, perm_desc, deg_sorted, gcorr, g0, rh1, rh2, dh1, dh2);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+cudaError_t diag_ratio(const zd* L, int64_t ldl, int n, double* out2, cudaStream_t s) {
+  diag_ratio_kernel<<<1, 256, 0, s>>>(L, ldl, n, out2);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -268,6 +268,25 @@ def test_heev_clustered_spectrum(ctx):
     assert np.max(np.abs(G @ V - V * w[None, :])) < 1e-13
 
 
+@pytest.mark.parametrize("m", [601, 700, 1200])
+def test_heev_large_blocks_share_cooperative_ctas(m):
+    """Blocks above ~600 columns (the n = 13,400 workload's blk = 1200) run with several
+    rotation pairs per CTA of the cooperative grid: eigenpairs against LAPACK, a random
+    Hermitian matrix and a nearly diagonal one (the Gram matrix of a warm loop)."""
+    rng = _rng(m)
+    G = _herm(rng, m, 2.0)
+    D = np.diag(np.sort(rng.uniform(-2, 2, m))) + 1e-6 * _herm(rng, m)
+    with cb.Solver(m, m) as s:
+        for M in (G, D):
+            w, V = cb.chfsi_heev(s.ctx, _t(M))
+            w, V = _np(w), _np(V)
+            w_ref = np.linalg.eigvalsh(M)
+            nrm = np.linalg.norm(M, 2)
+            assert np.max(np.abs(w - w_ref)) < 1e-13 * nrm * math.sqrt(m)
+            assert np.max(np.abs(V.conj().T @ V - np.eye(m))) < 1e-13 * math.sqrt(m)
+            assert np.max(np.abs(M @ V - V * w[None, :])) < 1e-13 * nrm * math.sqrt(m)
+
+
 # ---------------------------------------------------------------------------- degrees
 def test_degrees_bit_exact_with_oracle(ctx):
     rng = _rng(11)

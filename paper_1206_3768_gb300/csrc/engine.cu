@@ -190,6 +190,21 @@ int gemm_auto(chfsi_ctx* ctx, const GemmDesc& g) {
   return gemm(ctx, g);
 }
 
+// A product of the factorisation of B and of its inverse (blocked Cholesky and triangular
+// inverse): in mixed mode the large ones run as 8-slice digit products (error about 2^-56 of
+// the operands' row and column scales, below the FP64 GEMM bound; a triangular right operand
+// is used with its stored zeros), the rest in FP64.
+int gemm_factor(chfsi_ctx* ctx, const GemmDesc& g) {
+  const double work = (double)g.M * g.N * g.K;
+  const bool square_c = !g.lowerC || g.M == g.N;
+  if (ctx->opts.precision == 1 && work >= 16777216.0 && square_c) {
+    CK(oz_gemm(g.opA, g.A, g.lda, g.opB, g.B, g.ldb, g.M, g.N, g.K, 8, g.alpha, g.beta, g.Cin, g.ldcin,
+               g.gamma, g.D, g.ldd, g.C, g.ldc, g.triA == 1, g.lowerC, ctx->ws.oz, ctx->stream));
+    return CHFSI_OK;
+  }
+  return gemm(ctx, g);
+}
+
 // C(MxN) = alpha op(A) op(B) [+ beta Cin]
 GemmDesc gd(int M, int N, int K, const zd* A, int64_t lda, int opA, const zd* B, int64_t ldb,
             int opB, zd* C, int64_t ldc, double alpha = 1.0) {
@@ -223,14 +238,14 @@ int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n, int nb = NB) {
     zd* A21 = L + (k0 + kb) + (int64_t)k0 * ld;
     GemmDesc g = gd(r, kb, kb, A21, ld, OPN, ws.Rt, ws.blk_max, OPC, ws.Z, r);
     g.triB = 1;
-    CKS(gemm(ctx, g));
+    CKS(gemm_factor(ctx, g));
     CK(cudaMemcpy2DAsync(A21, ld * sizeof(zd), ws.Z, r * sizeof(zd), r * sizeof(zd), kb,
                          cudaMemcpyDeviceToDevice, ctx->stream));
     // A22 -= L21 L21^H (lower)
     zd* A22 = L + (k0 + kb) + (int64_t)(k0 + kb) * ld;
     GemmDesc h = gd(r, r, kb, A21, ld, OPN, A21, ld, OPC, A22, ld, -1.0);
     h.beta = 1.0; h.Cin = A22; h.ldcin = ld; h.lowerC = 1;
-    CKS(gemm(ctx, h));
+    CKS(gemm_factor(ctx, h));
   }
   CK(zero_upper(L, ld, n, ctx->stream));
   return CHFSI_OK;
@@ -248,11 +263,11 @@ int blocked_trinv(chfsi_ctx* ctx, const zd* L, int64_t ld, zd* X, int64_t ldx, i
     // Zt = L[I, 0:k0] X[0:k0, 0:k0]  (kb x k0), X lower => op(B)(k, j) = 0 for k < j
     GemmDesc g = gd(kb, k0, k0, L + k0, ld, OPN, X, ldx, OPN, ws.Z, kb);
     g.triB = 2;
-    CKS(gemm(ctx, g));
+    CKS(gemm_factor(ctx, g));
     // X[I, 0:k0] = -X_II Zt, X_II lower
     GemmDesc h = gd(kb, k0, kb, X + k0 + (int64_t)k0 * ldx, ldx, OPN, ws.Z, kb, OPN, X + k0, ldx, -1.0);
     h.triA = 1;
-    CKS(gemm(ctx, h));
+    CKS(gemm_factor(ctx, h));
   }
   return CHFSI_OK;
 }

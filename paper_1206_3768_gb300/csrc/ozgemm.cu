@@ -315,6 +315,7 @@ struct TcParams {
   long long spin_limit;                      // polls before a first-level wait gives up
   int cl;                                    // CTAs per cluster along M sharing the B tiles (1, 2, 4)
   int tiles_m_pad;                           // tiles_m rounded up to a multiple of cl
+  int col_major_order;                       // 1: blockIdx.x runs over column tiles first (cl == 1)
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -456,7 +457,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tm = blockIdx.x % p.tiles_m_pad, tn = blockIdx.x / p.tiles_m_pad;
+  // tile order: row tiles fastest, or (col_major_order) the column tiles of one row tile next
+  // to each other, so that they stream the same A panels at about the same time
+  const int tiles_n = (int)(gridDim.x / (unsigned)p.tiles_m_pad);
+  const int tm = p.col_major_order ? (int)blockIdx.x / tiles_n : (int)blockIdx.x % p.tiles_m_pad;
+  const int tn = p.col_major_order ? (int)blockIdx.x % tiles_n : (int)blockIdx.x / p.tiles_m_pad;
   const int m0 = tm * TC_BM, n0 = tn * TC_BN;
   // Clusters of p.cl CTAs on consecutive row tiles share every B tile: each CTA loads 1/cl of
   // the B box and multicasts it to the whole cluster, so all CTAs of a cluster must walk the
@@ -1038,12 +1043,22 @@ static bool oz_grouped_pairs() {
   return grouped;
 }
 // Largest cluster of CTAs sharing the B tiles of the tcgen05 kernel by multicast: environment
-// variable CHFSI_OZ_CLUSTER (1, 2 or 4; default 4).
+// variable CHFSI_OZ_CLUSTER (1, 2 or 4; default 1: measured slower on the n = 9300 workload,
+// whose launches are bound by the bytes in flight per SM rather than by the L2 stream).
 static int oz_cluster_max() {
   static const int v = [] {
     const char* e = std::getenv("CHFSI_OZ_CLUSTER");
-    const int c = e ? std::atoi(e) : 4;
+    const int c = e ? std::atoi(e) : 1;
     return c >= 4 ? 4 : (c >= 2 ? 2 : 1);
+  }();
+  return v;
+}
+// Order of the tiles over blockIdx.x: environment variable CHFSI_OZ_ORDER ("col": the column
+// tiles of a row tile next to each other; default "row").
+static bool oz_col_major_order() {
+  static const bool v = [] {
+    const char* e = std::getenv("CHFSI_OZ_ORDER");
+    return e && std::strcmp(e, "col") == 0;
   }();
   return v;
 }
@@ -1217,6 +1232,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
           break;
         }
     tp.tiles_m_pad = ((tp.tiles_m + tp.cl - 1) / tp.cl) * tp.cl;
+    tp.col_major_order = (tp.cl == 1 && oz_col_major_order()) ? 1 : 0;
     const int tiles = tp.tiles_m_pad * ((Np + TC_BN - 1) / TC_BN);
     tp.splits = splits =
         choose_tc_splits(tiles, tp.nkb, tp.ngroups, oz.part_elems, (int64_t)Mp * Np, &tp.pair_split);

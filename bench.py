@@ -676,6 +676,10 @@ def run_degree_model(args):
                          "filter_products": int(sum(x["filter_products"] for x in st)),
                          "loops": int(sum(x["loops"] for x in st)),
                          "t_filter_ms": sum(x["t_filter_ms"] for x in st),
+                         "phase_ms": {k: round(sum(x[k] for x in st), 1) for k in
+                                      ("t_reduce_ms", "t_lanczos_ms", "t_filter_ms", "t_filter_gemm_ms", "t_qr_ms",
+                                       "t_small_ms", "t_rr_ms", "t_eig_ms", "t_resid_ms", "t_total_ms")},
+                         "loops_per_problem": [x["loops"] for x in st],
                          "max_resid": max(x["max_resid"] for x in st), "max_eig_err": err / scale}
         cb.chfsi_set_degree_model(s.ctx, None)
     L, C, F = out["learned"], out["closed_form"], out["fixed_degree_25"]

@@ -38,8 +38,10 @@ Readings of points the paper leaves open (same numbering in the design notes):
       divided by 10, all pairs are unlocked, and iteration continues (at most 3 times).
   R8  Adaptive degree (not in the paper): d_i = clamp(ceil(ln(r_i / tau) / ln rho_i),
       dmin, dmax), rho_i = |t_i| + sqrt(t_i^2 - 1), t_i = (theta_i - c) / e; columns
-      past the nev-th use the largest degree of the wanted active columns.  The
-      adaptive mode runs one Rayleigh-Ritz on the start block to obtain residuals.
+      past the nev-th use the largest degree of the wanted active columns.  The first
+      adaptive loop needs residuals: after a cold start one Rayleigh-Ritz on the start
+      block gives them; after a warm start they are the residuals of the carried vectors
+      at their Rayleigh quotients, with the bounds from the carried Ritz values.
   R9  Conjugate transposes everywhere the paper writes transposes (complex data).
   R10 Only the lower triangles of A and B are referenced.
   R11 Warm vectors travel in x-coordinates and are mapped by the new L^H (identical to
@@ -394,16 +396,22 @@ def chfsi_solve_loops(A, B, nev: int, blk: int, tol: float = 1e-10, deg: int = 2
 
     adaptive = deg == 0
     r = None
-    if (not is_warm) or adaptive:
+    if is_warm and adaptive:
+        # Reading R8: the residuals the first adaptive loop needs are those of the carried
+        # vectors at their Rayleigh quotients; the bounds come from the carried Ritz values.
+        W = H @ Y
+        theta = np.real(np.sum(Y.conj() * W, axis=0)) / np.real(np.sum(Y.conj() * Y, axis=0))
+        r = residual_norms(W, Y, theta)
+        st.matvecs += blk
+        a0 = float(warm.lam[0])
+        a = float(warm.lam[-1])
+    elif not is_warm:
         Q = orthonormalize(Y)
         theta, Y, W = rayleigh_ritz(H, Q)
         r = residual_norms(W, Y, theta)
         st.matvecs += blk
         a0 = float(theta[0])
-        if is_warm:
-            a = float(theta[-1])
-        else:
-            a = a0 + (b_up - a0) * blk / n
+        a = a0 + (b_up - a0) * blk / n
     else:
         theta = np.array(warm.lam, dtype=np.float64)
         a0 = float(theta[0])

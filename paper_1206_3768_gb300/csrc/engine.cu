@@ -661,7 +661,27 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
   double* resid = ws.resid;
   double* resid_alt = ws.resid2;
   bool have_r = false;
-  if (!warm || adaptive) {
+  if (warm && adaptive) {
+    // adaptive degrees need residuals before the first loop: for a warm start they are the
+    // residuals of the carried vectors at their Rayleigh quotients (one product H Y, no
+    // re-orthonormalisation or Rayleigh-Ritz); the bounds come from the carried Ritz values
+    {
+      PhaseScope ps(ctx, PH_RESID);
+      if (rr_slices > 0)
+        CK(oz_filter_product(Ya, ld, n, blk, rr_slices, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, W, ld, ws.oz,
+                             ctx->stream));
+      else
+        CKS(gemm(ctx, gd(n, blk, n, ws.Hs, ld, OPN, Ya, ld, OPN, W, ld)));
+      CK(rayleigh_quotients(W, ld, Ya, ld, n, blk, theta, ctx->stream));
+      CK(column_residuals(W, ld, Ya, ld, theta, n, blk, resid, ctx->stream));
+    }
+    st.matvecs += blk;
+    CKS(read_back(ctx, th.data(), theta, blk));
+    CKS(read_back(ctx, rr.data(), resid, blk));
+    have_r = true;
+    a0 = ctx->warm_lam[0];
+    a = ctx->warm_lam[blk - 1];
+  } else if (!warm) {
     {
       PhaseScope ps(ctx, PH_QR);
       CKS(orthonormalize_block(ctx, n, blk, &Ya, &Yb, nullptr, 0, 0));
@@ -680,7 +700,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
     CKS(check_status(ctx, "initial Rayleigh-Ritz"));
     have_r = true;
     a0 = th[0];
-    a = warm ? th[blk - 1] : a0 + (b_up - a0) * (double)blk / (double)n;
+    a = a0 + (b_up - a0) * (double)blk / (double)n;
   } else {
     th = ctx->warm_lam;
     a0 = th[0];

@@ -127,6 +127,8 @@ cudaError_t select_cols(const zd* src1, int64_t ld1, zd* dst, int64_t ldd, int n
                         const int* flag, cudaStream_t s);
 cudaError_t column_residuals(const zd* HY, int64_t ldhy, const zd* Y, int64_t ldy,
                              const double* theta, int n, int m, double* r, cudaStream_t s);
+cudaError_t rayleigh_quotients(const zd* HY, int64_t ldhy, const zd* Y, int64_t ldy, int n, int m,
+                               double* theta, cudaStream_t s);
 cudaError_t generalized_residuals(const zd* AX, int64_t ldax, const zd* BX, int64_t ldbx,
                                   const zd* X, int64_t ldx, const double* lam, int n, int m,
                                   const double* a_norm, double* r, cudaStream_t s);

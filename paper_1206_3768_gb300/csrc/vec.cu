@@ -179,6 +179,22 @@ __global__ void column_residuals_kernel(const zd* HY, int64_t ldhy, const zd* Y,
   if (threadIdx.x == 0) r[j] = sqrt(num) / sqrt(den);
 }
 
+// theta_j = Re(y_j^H (H y_j)) / (y_j^H y_j): the Rayleigh quotient of column j.
+__global__ void rayleigh_quotients_kernel(const zd* HY, int64_t ldhy, const zd* Y, int64_t ldy, int n,
+                                          double* theta) {
+  const int j = blockIdx.x;
+  double num = 0.0, den = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const zd y = Y[i + (int64_t)j * ldy];
+    const zd h = HY[i + (int64_t)j * ldhy];
+    num += y.x * h.x + y.y * h.y;
+    den += zabs2(y);
+  }
+  num = block_sum(num);
+  den = block_sum(den);
+  if (threadIdx.x == 0) theta[j] = num / den;
+}
+
 // ||AX_j - lam_j BX_j|| / (a_norm ||X_j||)
 __global__ void gen_residuals_kernel(const zd* AX, int64_t ldax, const zd* BX, int64_t ldbx,
                                      const zd* X, int64_t ldx, const double* lam, int n,
@@ -755,6 +771,13 @@ cudaError_t degrees_kernel_run(const double* theta, const double* r, int m, doub
 }
 cudaError_t diag_ratio(const zd* L, int64_t ldl, int n, double* out2, cudaStream_t s) {
   diag_ratio_kernel<<<1, 256, 0, s>>>(L, ldl, n, out2);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+cudaError_t rayleigh_quotients(const zd* HY, int64_t ldhy, const zd* Y, int64_t ldy, int n, int m,
+                               double* theta, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  rayleigh_quotients_kernel<<<m, 256, 0, s>>>(HY, ldhy, Y, ldy, n, theta);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -51,6 +51,15 @@ struct chfsi_ctx {
   cudaStream_t copy_stream = nullptr;
   zd* stage[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaEvent_t staged[2] = {nullptr, nullptr};
+  // Lanczos runs captured as CUDA graphs (their launch sequence depends only on the matrix,
+  // its size, the step count, the seed and the precision), replayed on the context's stream
+  struct LanczosGraph {
+    const void* H; int64_t ldh; int n, k; uint64_t seed; int f32; const double* out;
+    cudaGraphExec_t exec; long long kernels;
+  };
+  std::vector<LanczosGraph> lanczos_graphs;
+  cudaStream_t capture_stream = nullptr;
+  bool graphs_off = false;
 };
 
 namespace {
@@ -308,30 +317,72 @@ int reduce_to_standard(chfsi_ctx* ctx, const zd* Af, int64_t lda, const zd* Linv
 // spectrum and a norm estimate need no more); the vectors and T_k stay FP64.
 // v0: device start vector or nullptr (SplitMix64 with `seed`).  out3 (device):
 // [theta_min, theta_max, theta_max + |beta_k|].
+int lanczos_issue(chfsi_ctx* ctx, cudaStream_t st, const zd* H, int64_t ldh, int n, int k, const zd* v0,
+                  uint64_t seed, double* out3);
+
+// The launch-bound Lanczos loop (seven small kernels per step) is captured once per
+// (matrix, size, steps, seed, precision) on a private stream and replayed as a CUDA graph on
+// the context's stream; a caller start vector v0, or a failed capture, issues it directly.
 int lanczos_run(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int k, const zd* v0,
                 uint64_t seed, double* out3) {
+  const int f32 = ctx->opts.precision == 1;
+  if (v0 || ctx->graphs_off) return lanczos_issue(ctx, ctx->stream, H, ldh, n, k, v0, seed, out3);
+  k = std::min(std::min(k, n), ctx->ws.lanczos_kmax);
+  for (auto& g : ctx->lanczos_graphs)
+    if (g.H == H && g.ldh == ldh && g.n == n && g.k == k && g.seed == seed && g.f32 == f32 && g.out == out3) {
+      CK(cudaGraphLaunch(g.exec, ctx->stream));
+      g_kernel_launches += g.kernels;
+      return CHFSI_OK;
+    }
+  if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  const long long before = g_kernel_launches;
+  cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const int rc = lanczos_issue(ctx, ctx->capture_stream, H, ldh, n, k, nullptr, seed, out3);
+    e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (rc != CHFSI_OK && e == cudaSuccess) e = cudaErrorUnknown;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  const long long kernels = g_kernel_launches - before;
+  g_kernel_launches = before;
+  if (e != cudaSuccess) {  // no graphs on this context: issue directly from now on
+    cudaGetLastError();
+    ctx->graphs_off = true;
+    return lanczos_issue(ctx, ctx->stream, H, ldh, n, k, nullptr, seed, out3);
+  }
+  ctx->lanczos_graphs.push_back({H, ldh, n, k, seed, f32, out3, exec, kernels});
+  CK(cudaGraphLaunch(exec, ctx->stream));
+  g_kernel_launches += kernels;
+  return CHFSI_OK;
+}
+
+int lanczos_issue(chfsi_ctx* ctx, cudaStream_t st, const zd* H, int64_t ldh, int n, int k, const zd* v0,
+                  uint64_t seed, double* out3) {
   Workspace& ws = ctx->ws;
   k = std::min(k, n);
   k = std::min(k, ws.lanczos_kmax);
   if (k <= 0) return set_err(ctx, CHFSI_EINVAL, "lanczos: k must be positive");
   const int64_t ldv = ws.n_max;
   zd* V = ws.lV;
-  if (v0) CK(cudaMemcpyAsync(ws.lw, v0, n * sizeof(zd), cudaMemcpyDeviceToDevice, ctx->stream));
-  else CK(splitmix_start_vector(ws.lw, n, seed, ctx->stream));
+  if (v0) CK(cudaMemcpyAsync(ws.lw, v0, n * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+  else CK(splitmix_start_vector(ws.lw, n, seed, st));
   double* nrm = ws.scal + 8;
-  CK(vec_norm(ws.lw, n, nrm, ctx->stream));
-  CK(vec_scale_into(ws.lw, n, nrm, V, ctx->stream));
+  CK(vec_norm(ws.lw, n, nrm, st));
+  CK(vec_scale_into(ws.lw, n, nrm, V, st));
   for (int j = 0; j < k; ++j) {
-    CK(hemv_rows(H, ldh, V + (int64_t)j * ldv, ws.lw, n, ctx->stream, ctx->opts.precision == 1));
-    CK(block_dots(V, ldv, j, ws.lw, n, ws.lc, ctx->stream));
-    CK(block_update(V, ldv, j, ws.lc, ws.lw, n, ctx->stream));
-    CK(block_dots(V, ldv, j, ws.lw, n, ws.lc + (ws.lanczos_kmax + 1), ctx->stream));
-    CK(block_update(V, ldv, j, ws.lc + (ws.lanczos_kmax + 1), ws.lw, n, ctx->stream));
-    CK(vec_norm(ws.lw, n, nrm, ctx->stream));
-    CK(lanczos_record(ws.lc, j, nrm, ws.lal, ws.lbe, ctx->stream));
-    if (j + 1 < k) CK(vec_scale_into(ws.lw, n, nrm, V + (int64_t)(j + 1) * ldv, ctx->stream));
+    CK(hemv_rows(H, ldh, V + (int64_t)j * ldv, ws.lw, n, st, ctx->opts.precision == 1));
+    CK(block_dots(V, ldv, j, ws.lw, n, ws.lc, st));
+    CK(block_update(V, ldv, j, ws.lc, ws.lw, n, st));
+    CK(block_dots(V, ldv, j, ws.lw, n, ws.lc + (ws.lanczos_kmax + 1), st));
+    CK(block_update(V, ldv, j, ws.lc + (ws.lanczos_kmax + 1), ws.lw, n, st));
+    CK(vec_norm(ws.lw, n, nrm, st));
+    CK(lanczos_record(ws.lc, j, nrm, ws.lal, ws.lbe, st));
+    if (j + 1 < k) CK(vec_scale_into(ws.lw, n, nrm, V + (int64_t)(j + 1) * ldv, st));
   }
-  CK(tridiag_extremes(ws.lal, ws.lbe, k, out3, ctx->stream));
+  CK(tridiag_extremes(ws.lal, ws.lbe, k, out3, st));
   return CHFSI_OK;
 }
 
@@ -1135,6 +1186,8 @@ void chfsi_destroy(chfsi_ctx* ctx) {
   for (auto e : ctx->ev_pool) debug_check(cudaEventDestroy(e), "cudaEventDestroy");
   if (ctx->mlp_dev) debug_check(cudaFree(ctx->mlp_dev), "cudaFree");
   release_prefetch(ctx);
+  for (auto& g : ctx->lanczos_graphs) debug_check(cudaGraphExecDestroy(g.exec), "cudaGraphExecDestroy");
+  if (ctx->capture_stream) debug_check(cudaStreamDestroy(ctx->capture_stream), "cudaStreamDestroy");
   workspace_free(ctx->ws);
   release_stream(ctx);
   delete ctx;
@@ -1254,7 +1307,7 @@ int chfsi_lanczos(chfsi_ctx* ctx, int64_t n, const chfsi_z* H, int64_t ldh, int3
                    ctx->ws.lanczos_kmax);
   cudaSetDevice(ctx->ws.dev);
   double out[3];
-  CKS(lanczos_run(ctx, Z(H), ldh, (int)n, k, Z(v0), ctx->opts.seed, ctx->ws.scal));
+  CKS(lanczos_issue(ctx, ctx->stream, Z(H), ldh, (int)n, k, Z(v0), ctx->opts.seed, ctx->ws.scal));
   CKS(read_back(ctx, out, ctx->ws.scal, 3));
   if (theta_min) *theta_min = out[0];
   if (theta_max) *theta_max = out[1];

@@ -25,7 +25,10 @@
 
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -1022,6 +1025,42 @@ int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t t
 }  // namespace
 
 // ---------------------------------------------------------------------------- host side
+// Autotuner of the tcgen05 kernel's split count: the best configuration measured for each
+// product shape, shared by all contexts of the process (batch workers tune from several host
+// threads).  Environment variable CHFSI_OZ_AUTOTUNE=0 keeps the wave model's choice.
+struct TuneKey {
+  int Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups;
+  bool operator<(const TuneKey& o) const {
+    const int a[10] = {Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups};
+    const int b[10] = {o.Mp, o.Np, o.Kp, o.S, o.a_lower, o.c_lower, o.group, o.b_box_rows, o.cl, o.ngroups};
+    return std::lexicographical_compare(a, a + 10, b, b + 10);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune;
+static bool tune_lookup(const TuneKey& k, int* splits, int* pair_split) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *splits = it->second.first;
+  *pair_split = it->second.second;
+  return true;
+}
+static void tune_store(const TuneKey& k, int splits, int pair_split) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[k] = {splits, pair_split};
+}
+static bool oz_autotune() {
+  static const bool v = [] {
+    const char* e = std::getenv("CHFSI_OZ_AUTOTUNE");
+    return !(e && std::strcmp(e, "0") == 0);
+  }();
+  return v;
+}
+int oz_tuned_shapes() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune.size();
+}
 // Product kernel: tcgen05 (default) or the mma.sync kernel, chosen once per process by the
 // environment variable CHFSI_OZ_KERNEL ("tc" or "mma").
 // The choices below are read once (thread-safe static initialisation: batch workers call
@@ -1234,8 +1273,9 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     tp.tiles_m_pad = ((tp.tiles_m + tp.cl - 1) / tp.cl) * tp.cl;
     tp.col_major_order = (tp.cl == 1 && oz_col_major_order()) ? 1 : 0;
     const int tiles = tp.tiles_m_pad * ((Np + TC_BN - 1) / TC_BN);
-    tp.splits = splits =
-        choose_tc_splits(tiles, tp.nkb, tp.ngroups, oz.part_elems, (int64_t)Mp * Np, &tp.pair_split);
+    int model_pair_split = 0;
+    const int model_splits =
+        choose_tc_splits(tiles, tp.nkb, tp.ngroups, oz.part_elems, (int64_t)Mp * Np, &model_pair_split);
     const uint64_t b_rows = std::max<uint64_t>((uint64_t)b.S * Np, (uint64_t)TC_BN);
     if ((int64_t)b_rows * Kp > (int64_t)b.S_max * b.Np_max * b.Kp_max) return cudaErrorInvalidValue;
     if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)a.S * Mp, TC_BM) ||
@@ -1248,28 +1288,74 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     static const cudaError_t tc_attr = cudaFuncSetAttribute(
         oz_gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 + TC_SMEM_BUDGET + 256);
     if (tc_attr != cudaSuccess) return tc_attr;
-    if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
-    if (tp.cl > 1) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(tiles, splits);
-      cfg.blockDim = dim3(TC_THREADS);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = s;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = tp.cl;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, oz_gemm_tc_kernel, mapA, mapB, tp);
-      if (e != cudaSuccess) return e;
-    } else {
-      oz_gemm_tc_kernel<<<dim3(tiles, splits), TC_THREADS, smem, s>>>(mapA, mapB, tp);
+    auto launch = [&](int sp, int ps) -> cudaError_t {
+      tp.splits = sp;
+      tp.pair_split = ps;
+      if (tp.cl > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(tiles, sp);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = tp.cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t le = cudaLaunchKernelEx(&cfg, oz_gemm_tc_kernel, mapA, mapB, tp);
+        if (le != cudaSuccess) return le;
+      } else {
+        oz_gemm_tc_kernel<<<dim3(tiles, sp), TC_THREADS, smem, s>>>(mapA, mapB, tp);
+      }
+      CHFSI_COUNT_LAUNCH();
+      return cudaGetLastError();
+    };
+    // split count: the wave model's choice, or the fastest of a few candidates around it,
+    // measured on the first product of each shape and kept for the process (autotuner)
+    int best_splits = model_splits, best_ps = model_pair_split;
+    const TuneKey key{Mp, Np, Kp, S, a_lower, c_lower, tp.group, tp.b_box_rows, tp.cl, tp.ngroups};
+    if (oz_autotune() && !tune_lookup(key, &best_splits, &best_ps)) {
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+        std::vector<std::pair<int, int>> cand;
+        const int limit_k = model_pair_split ? tp.ngroups : std::min(tp.nkb, 64);
+        for (int num : {2, 3, 4, 6, 8}) {  // model x {1/2, 3/4, 1, 3/2, 2}
+          const int sp = std::max(1, std::min(limit_k, (model_splits * num + 2) / 4));
+          if ((size_t)sp * (size_t)((int64_t)Mp * Np) > oz.part_elems) continue;
+          if (model_pair_split) {
+            const int pp = (tp.ngroups + sp - 1) / sp;   // groups per split: the grid uses ceil
+            const int eff = (tp.ngroups + pp - 1) / pp;
+            if (std::find(cand.begin(), cand.end(), std::make_pair(eff, 1)) == cand.end()) cand.push_back({eff, 1});
+          } else if (std::find(cand.begin(), cand.end(), std::make_pair(sp, 0)) == cand.end()) {
+            cand.push_back({sp, 0});
+          }
+        }
+        cudaEvent_t t0, t1;
+        if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) return cudaGetLastError();
+        float best_ms = 1e30f;
+        for (const auto& c : cand) {
+          cudaEventRecord(t0, s);
+          e = launch(c.first, c.second);
+          if (e != cudaSuccess) break;
+          cudaEventRecord(t1, s);
+          e = cudaEventSynchronize(t1);
+          if (e != cudaSuccess) break;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, t0, t1);
+          if (ms < best_ms) { best_ms = ms; best_splits = c.first; best_ps = c.second; }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        if (e != cudaSuccess) return e;
+        tune_store(key, best_splits, best_ps);
+      }
     }
-    CHFSI_COUNT_LAUNCH();
+    splits = best_splits;
+    if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
+    e = launch(best_splits, best_ps);
     if (ev_gemm_end) cudaEventRecord(ev_gemm_end, s);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   } else {
     OzParams p;

@@ -389,7 +389,7 @@ __device__ __forceinline__ zd ldcg(const zd* p) { return __ldcg(p); }
 struct Rot { double c, s; zd w; int active; };
 
 constexpr int JAC_THREADS = 256;
-constexpr int kJacSmemMax = 200 * 1024;  // dynamic shared memory a Jacobi CTA may use
+constexpr int kJacSmemMax = 224 * 1024;  // dynamic shared memory a Jacobi CTA may use
 
 __device__ __forceinline__ Rot jacobi_rotation(const zd* src, int mp, int p, int q, double thresh) {
   const double a = ldcg(src + p + (int64_t)p * mp).x;
@@ -417,24 +417,26 @@ __device__ __forceinline__ Rot jacobi_rotation(const zd* src, int mp, int p, int
 }
 
 // CTA c takes the rotation pairs (slots) c*ppc .. c*ppc + ppc - 1 of every round (ppc =
-// P.pairs_per_cta; one pair per CTA while the grid fits, more for large blocks).  Per round,
-// work item e = (k, row, t) of the CTA is output row (row ? q : p) of its k-th pair at column
-// pair t; the item's four source entries are loaded before the round's rotations are
-// computed (so the L2 latency overlaps them) when it is the thread's first item.  The CTA's
-// 2 ppc rows of V (rows 2 slot, 2 slot + 1 of its slots) stay in shared memory for the whole
-// run and take the right rotations of every pair of the round.
+// P.pairs_per_cta; one pair per CTA while the grid fits, more for large blocks).  Per round
+// the CTA computes all rotations of the round; then, one pair at a time, it copies columns p
+// and q into shared memory (coalesced; by Hermitian symmetry column j holds the conjugated
+// row j), applies U_P^H on the left and the column-pair rotations U_R on the right in place
+// there — work item t owns rows p, q and columns r, s of one 2 x 2 block, so no two items
+// touch the same entry — and writes the new columns back (coalesced).  The CTA's 2 ppc rows of V
+// (rows 2 slot, 2 slot + 1 of its slots) stay in shared memory for the whole run and take
+// the right rotations of every pair of the round.
 __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) {
   extern __shared__ unsigned char smem_raw[];
   const int mp = P.mp, half = mp / 2, ppc = P.pairs_per_cta;
   Rot* rot = reinterpret_cast<Rot*>(smem_raw);
   zd* vrow = reinterpret_cast<zd*>(smem_raw + sizeof(Rot) * (size_t)half);  // 2 ppc x mp
+  zd* col = vrow + (size_t)2 * ppc * mp;                                      // 2 x mp
   __shared__ double red[JAC_THREADS];
   const int tid = threadIdx.x, nt = blockDim.x;
   const unsigned nb = gridDim.x;
   const int cta = blockIdx.x;
   const int slot0 = cta * ppc;
   const int nslot = max(0, min(ppc, half - slot0));  // pairs this CTA owns
-  const int items = nslot * mp;                       // work items per round
 
   // ---- set-up: rows 2 slot, 2 slot + 1 of Ga (padded copy of G) and of V (identity)
   for (int rr = 0; rr < 2 * nslot; ++rr) {
@@ -486,15 +488,6 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) 
     for (int round = 0; round < mp - 1; ++round) {
       const zd* src = parity ? P.Gb : P.Ga;
       zd* dst = parity ? P.Ga : P.Gb;
-      // this thread's first item: source entries of its rows at its column pair
-      zd m00, m01, m10, m11;
-      if (tid < items) {
-        int p, q, r, s;
-        pair_of(round, slot0 + tid / mp, mp, p, q);
-        pair_of(round, (tid % mp) >> 1, mp, r, s);
-        m00 = ldcg(src + p + (int64_t)r * mp); m01 = ldcg(src + p + (int64_t)s * mp);
-        m10 = ldcg(src + q + (int64_t)r * mp); m11 = ldcg(src + q + (int64_t)s * mp);
-      }
       // all rotations of this round (same inputs, same result on every CTA)
       int any = 0;
       for (int t = tid; t < half; t += nt) {
@@ -506,48 +499,65 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(const JacParams P) 
       // a round whose pairs are all below the threshold leaves the matrix as it is: every CTA
       // reaches the same decision and skips it (no writes, no barrier)
       if (!__syncthreads_or(any)) continue;
-      for (int e = tid; e < items; e += nt) {
-        const int k = e / mp, e2 = e - k * mp;
-        const int t = e2 >> 1, row = e2 & 1;
+      for (int k = 0; k < nslot; ++k) {
         const int slot = slot0 + k;
-        int p, q, r, s;
+        int p, q;
         pair_of(round, slot, mp, p, q);
-        pair_of(round, t, mp, r, s);
-        if (e != tid) {
-          m00 = ldcg(src + p + (int64_t)r * mp); m01 = ldcg(src + p + (int64_t)s * mp);
-          m10 = ldcg(src + q + (int64_t)r * mp); m11 = ldcg(src + q + (int64_t)s * mp);
+        zd* cp = col;       // column p: cp[j] = conj(G[p, j])
+        zd* cq = col + mp;  // column q
+        for (int j = tid; j < mp; j += nt) {
+          cp[j] = ldcg(src + j + (int64_t)p * mp);
+          cq[j] = ldcg(src + j + (int64_t)q * mp);
         }
+        __syncthreads();
         const Rot RP = rot[slot];
         const zd wpc = zconj(RP.w);  // e^{+i phi}
         const zd sw = zscale(wpc, RP.s), cw = zscale(wpc, RP.c);
+        for (int t = tid; t < half; t += nt) {
+          int r, s;
+          pair_of(round, t, mp, r, s);
+          const zd m00 = zconj(cp[r]), m01 = zconj(cp[s]), m10 = zconj(cq[r]), m11 = zconj(cq[s]);
+          const Rot RR = rot[t];
+          // left: U_P^H = [[c, -s e^{i phi}], [s, c e^{i phi}]] on rows p, q
+          const zd l0p = zsub(zscale(m00, RP.c), zmul(sw, m10));
+          const zd l1p = zsub(zscale(m01, RP.c), zmul(sw, m11));
+          const zd l0q = zadd(zscale(m00, RP.s), zmul(cw, m10));
+          const zd l1q = zadd(zscale(m01, RP.s), zmul(cw, m11));
+          // right: U_R = [[c, s], [-s w, c w]] on columns r, s
+          const zd rsw = zscale(RR.w, RR.s), rcw = zscale(RR.w, RR.c);
+          zd np0 = zsub(zscale(l0p, RR.c), zmul(l1p, rsw));
+          zd np1 = zadd(zscale(l0p, RR.s), zmul(l1p, rcw));
+          zd nq0 = zsub(zscale(l0q, RR.c), zmul(l1q, rsw));
+          zd nq1 = zadd(zscale(l0q, RR.s), zmul(l1q, rcw));
+          if (t == slot) {  // diagonal block: exact diagonal result
+            np0.y = 0.0;
+            nq1.y = 0.0;
+            if (RP.active) { np1 = zmk(0.0, 0.0); nq0 = zmk(0.0, 0.0); }
+          }
+          cp[r] = zconj(np0);
+          cp[s] = zconj(np1);
+          cq[r] = zconj(nq0);
+          cq[s] = zconj(nq1);
+        }
+        __syncthreads();
+        for (int j = tid; j < mp; j += nt) {
+          dst[j + (int64_t)p * mp] = cp[j];
+          dst[j + (int64_t)q * mp] = cq[j];
+        }
+        __syncthreads();
+      }
+      // V rows 2 slot + row (shared memory): V[i, R] <- V[i, R] U_R
+      for (int e = tid; e < 2 * nslot * half; e += nt) {
+        const int vr = e / half, t = e - vr * half;
         const Rot RR = rot[t];
-        // left: U_P^H = [[c, -s e^{i phi}], [s, c e^{i phi}]]; this item's row only
-        zd l0, l1;
-        if (row == 0) {
-          l0 = zsub(zscale(m00, RP.c), zmul(sw, m10));
-          l1 = zsub(zscale(m01, RP.c), zmul(sw, m11));
-        } else {
-          l0 = zadd(zscale(m00, RP.s), zmul(cw, m10));
-          l1 = zadd(zscale(m01, RP.s), zmul(cw, m11));
-        }
-        // right: U_R = [[c, s], [-s w, c w]]
+        if (!RR.active) continue;
+        int r, s;
+        pair_of(round, t, mp, r, s);
         const zd rsw = zscale(RR.w, RR.s), rcw = zscale(RR.w, RR.c);
-        zd n0 = zsub(zscale(l0, RR.c), zmul(l1, rsw));
-        zd n1 = zadd(zscale(l0, RR.s), zmul(l1, rcw));
-        if (t == slot) {  // diagonal block: exact diagonal result
-          if (row == 0) { n0.y = 0.0; if (RP.active) n1 = zmk(0.0, 0.0); }
-          else { n1.y = 0.0; if (RP.active) n0 = zmk(0.0, 0.0); }
-        }
-        const int orow = row ? q : p;
-        dst[orow + (int64_t)r * mp] = n0;
-        dst[orow + (int64_t)s * mp] = n1;
-        // V rows 2 slot + row (shared memory): V[i, R] <- V[i, R] U_R
-        if (RR.active) {
-          zd* vi = vrow + (2 * k + row) * mp;
-          const zd a0 = vi[r], a1 = vi[s];
-          vi[r] = zsub(zscale(a0, RR.c), zmul(a1, rsw));
-          vi[s] = zadd(zscale(a0, RR.s), zmul(a1, rcw));
-        }
+        zd* vi = vrow + vr * mp;
+        const zd a0 = vi[r], a1 = vi[s];
+        vi[r] = zsub(zscale(a0, RR.c), zmul(a1, rsw));
+        vi[s] = zadd(zscale(a0, RR.s), zmul(a1, rcw));
       }
       parity ^= 1;
       if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
@@ -657,7 +667,7 @@ cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64
   int ppc = 1;
   size_t smem = 0;
   for (;; ++ppc) {
-    smem = sizeof(Rot) * (size_t)half + 2 * sizeof(zd) * (size_t)ppc * mp;
+    smem = sizeof(Rot) * (size_t)half + 2 * sizeof(zd) * (size_t)(ppc + 1) * mp;
     if (smem > (size_t)kJacSmemMax) return cudaErrorInvalidValue;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JAC_THREADS, smem);

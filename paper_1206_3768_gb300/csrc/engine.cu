@@ -281,9 +281,12 @@ int blocked_trinv(chfsi_ctx* ctx, const zd* L, int64_t ld, zd* X, int64_t ldx, i
   return CHFSI_OK;
 }
 
-// Hs = Linv Af Linv^H (lower computed, mirrored).  split: the two products use split-BF16
-// tensor-core products (FP64-level accuracy), skipping the zero k-blocks of the triangular
-// Linv and the upper tiles of Hs: T = Linv Af, Hs = Linv T^H.
+// Hs = Linv Af Linv^H.  split: the two products use split-BF16 tensor-core products
+// (FP64-level accuracy) on the lower part A_h of Af (strict lower triangle plus half the
+// diagonal, Af = A_h + A_h^H): P = Linv A_h is lower triangular (only k-blocks between the
+// two triangles and the lower tiles are computed), Q = P Linv^H takes only k <= min(i, j),
+// and Hs = Q + Q^H.  That is n^3/6 + n^3/3 complex multiply-adds against n^3/2 + n^3/3 for
+// T = Linv Af, Hs = Linv T^H.  Otherwise (FP64): T = Linv Af, lower of T Linv^H, mirrored.
 // Slices: the row scales of L^{-1} grow like sqrt(cond(B)), and its two products carry that
 // growth into Hs; 8 slices (2^-56) keep the eigenvalue error at the FP64 level for cond(B)
 // 1e4, 7 slices (2^-49) do so for a well-conditioned B (squared pivots within a factor 100;
@@ -294,11 +297,14 @@ int reduce_to_standard(chfsi_ctx* ctx, const zd* Af, int64_t lda, const zd* Linv
   Workspace& ws = ctx->ws;
   if (split) {
     const int S = cond_lb < 100.0 ? 7 : 8;
+    // P = Linv A_h: lower x lower, lower tiles only (B zero for k < j)
     CK(oz_gemm(OPN, Linv, ldl, OPN, Af, lda, n, n, n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, ws.T,
-               ws.n_max, 1, 0, ws.oz, ctx->stream));
-    CK(oz_gemm(OPN, Linv, ldl, OPC, ws.T, ws.n_max, n, n, n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
-               Hs, ldh, 1, 1, ws.oz, ctx->stream));
-    CK(mirror_lower(Hs, ldh, n, ctx->stream));
+               ws.n_max, 1, 1, ws.oz, ctx->stream, /*b_tri=*/2, /*b_lower_half=*/1));
+    CK(zero_upper(ws.T, ws.n_max, n, ctx->stream));
+    // Q = P Linv^H: lower x upper (B zero for k > j), full result
+    CK(oz_gemm(OPN, ws.T, ws.n_max, OPC, Linv, ldl, n, n, n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0,
+               Hs, ldh, 1, 0, ws.oz, ctx->stream, /*b_tri=*/1));
+    CK(herm_sum(Hs, ldh, n, ctx->stream));
     return CHFSI_OK;
   }
   GemmDesc g = gd(n, n, n, Linv, ldl, OPN, Af, lda, OPN, ws.T, ws.n_max);

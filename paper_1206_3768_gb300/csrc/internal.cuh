@@ -115,6 +115,8 @@ cudaError_t herm_from_lower(const zd* src, int64_t lds, zd* dst, int64_t ldd, in
                             int* status, cudaStream_t s);
 cudaError_t mirror_lower(zd* H, int64_t ldh, int n, cudaStream_t s);
 cudaError_t zero_upper(zd* L, int64_t ldl, int n, cudaStream_t s);
+// H <- H + H^H in place (full storage), exactly Hermitian.
+cudaError_t herm_sum(zd* H, int64_t ldh, int n, cudaStream_t s);
 // out2 = [max_i |L_ii|^2, min_i |L_ii|^2] (device): their ratio bounds cond(L L^H) from below.
 cudaError_t diag_ratio(const zd* L, int64_t ldl, int n, double* out2, cudaStream_t s);
 cudaError_t copy_cols(const zd* src, int64_t lds, zd* dst, int64_t ldd, int n, int m,
@@ -212,11 +214,11 @@ void oz_free(OzWorkspace& oz);
 cudaError_t oz_slice_a(OzA& a, int op, const zd* X, int64_t ldx, int M, int K, int S, cudaStream_t s);
 // Digit slices of op(B) = X (op N: columns, K x N) or X^H (op C: conj rows of X, N x K).
 cudaError_t oz_slice_b(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, int S, int Kp,
-                       cudaStream_t s);
+                       cudaStream_t s, int lower_half = 0);
 cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double beta, const zd* Cin,
                        int64_t ldcin, double gamma, const zd* D, int64_t ldd, zd* out, int64_t ldo,
                        int a_lower, int c_lower, OzWorkspace& oz, cudaStream_t s,
-                       cudaEvent_t ev_gemm_begin = nullptr, cudaEvent_t ev_gemm_end = nullptr);
+                       cudaEvent_t ev_gemm_begin = nullptr, cudaEvent_t ev_gemm_end = nullptr, int b_tri = 0);
 // Slices of the Hermitian Hs into oz.H (once per problem).
 cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
                                cudaStream_t s);
@@ -229,7 +231,8 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
 cudaError_t oz_gemm(int opA, const zd* A, int64_t lda, int opB, const zd* B, int64_t ldb, int M, int N,
                     int K, int S, double alpha, double beta, const zd* Cin, int64_t ldcin, double gamma,
                     const zd* D, int64_t ldd, zd* C, int64_t ldc, int a_lower, int c_lower,
-                    OzWorkspace& oz, cudaStream_t s);
+                    OzWorkspace& oz, cudaStream_t s, int b_tri = 0,
+                    int b_lower_half = 0);
 
 // ------------------------------------------------------------------ workspace
 struct Workspace {

@@ -305,6 +305,7 @@ constexpr long kMbarSpinLimit = 1L << 26;
 
 struct TcParams {
   int a_lower, c_lower;                      // as in OzParams
+  int b_tri;                                 // op(B) (complex) zero for k > j (1) or k < j (2)
   int nkb, tiles_m, splits, Mp, Np, n_real;  // n_real: columns of B^ that hold data
   int b_box_rows;                            // rows of the B box (<= TC_BN, multiple of 16)
   int stages;                                // TMA ring depth (<= TC_MAX_STAGES)
@@ -479,18 +480,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // The work is ordered panel-major: for each panel of at most OZ_CHUNK_KB k-blocks, every
   // slice pair in turn (one exact chunk each), so consecutive chunks reuse the same panel of
   // an A slice from L2 while it is hot.
-  const int nkb = p.a_lower ? min(p.nkb, m0_last / TC_BK + TC_BM / TC_BK) : p.nkb;
   const int ncols = min(TC_BN, ((p.n_real - n0 + 15) / 16) * 16);  // MMA N for this tile
+  // nonzero k-blocks of the tile: below (m0 + 128) / 64 for a lower-triangular A; from
+  // 2 n0 / 64 for a lower-triangular B (zero for k < j); below 2 (n0 + ncols) / 64 for an
+  // upper-triangular B (zero for k > j)
+  int kb_first = 0, nkb = p.a_lower ? min(p.nkb, m0_last / TC_BK + TC_BM / TC_BK) : p.nkb;
+  if (p.b_tri == 2) kb_first = min(nkb, (2 * n0) / TC_BK);
+  if (p.b_tri == 1) nkb = min(nkb, (2 * (n0 + ncols) + TC_BK - 1) / TC_BK);
   // split y takes either a range of k-blocks (all groups) or, for short K (one panel), a
   // range of slice groups (all k-blocks)
-  int kb_lo = 0, kb_hi = nkb, pr_lo = 0, pr_hi = p.ngroups;
+  int kb_lo = kb_first, kb_hi = nkb, pr_lo = 0, pr_hi = p.ngroups;
   if (p.pair_split) {
     const int pp = (p.ngroups + p.splits - 1) / p.splits;
     pr_lo = min(p.ngroups, (int)blockIdx.y * pp);
     pr_hi = min(p.ngroups, pr_lo + pp);
   } else {
-    const int per = (p.nkb + p.splits - 1) / p.splits;
-    kb_lo = min(nkb, (int)blockIdx.y * per);
+    const int per = (nkb - kb_first + p.splits - 1) / p.splits;
+    kb_lo = min(nkb, kb_first + (int)blockIdx.y * per);
     kb_hi = min(nkb, kb_lo + per);
   }
   const int npr = pr_hi - pr_lo;
@@ -947,8 +953,10 @@ __global__ void oz_slice_rows_kernel(const zd* X, int64_t ldx, int rows, int col
 
 // B-side slices of Y^ (the n x m complex block read as a 2n x m real array): one CTA per
 // column j; columns j >= m of the padded block are zero.
+// lower_half: column j of the operand is column j of Y below the diagonal, half of Y(j, j)
+// on it and zero above (the lower part L_h of a Hermitian Y = L_h + L_h^H).
 __global__ void oz_slice_cols_kernel(const zd* Y, int64_t ldy, int n, int m, int S,
-                                     __nv_bfloat16* B, int64_t sliceB, int Kp, int* eB) {
+                                     __nv_bfloat16* B, int64_t sliceB, int Kp, int* eB, int lower_half) {
   const int j = blockIdx.x;
   __nv_bfloat16* col = B + (int64_t)j * Kp;
   if (j >= m) {
@@ -958,9 +966,18 @@ __global__ void oz_slice_cols_kernel(const zd* Y, int64_t ldy, int n, int m, int
     return;
   }
   const zd* y = Y + (int64_t)j * ldy;
+  auto entry = [&](int k) -> zd {
+    zd v = y[k];
+    if (lower_half) {
+      if (k < j) v = zmk(0.0, 0.0);
+      else if (k == j) v = zmk(0.5 * v.x, 0.5 * v.y);
+    }
+    return v;
+  };
   unsigned long long mx = 0ull;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const unsigned long long a = abs_bits(y[k].x), b = abs_bits(y[k].y);
+    const zd v = entry(k);
+    const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
     mx = a > mx ? a : mx;
     mx = b > mx ? b : mx;
   }
@@ -968,7 +985,7 @@ __global__ void oz_slice_cols_kernel(const zd* Y, int64_t ldy, int n, int m, int
   const int e = exponent_from_bits(mx);
   if (threadIdx.x == 0) eB[j] = e;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const zd v = y[k];
+    const zd v = entry(k);
     digits(v.x, e, S, col + 2 * k, sliceB);
     digits(v.y, e, S, col + 2 * k + 1, sliceB);
   }
@@ -1029,11 +1046,12 @@ int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t t
 // product shape, shared by all contexts of the process (batch workers tune from several host
 // threads).  Environment variable CHFSI_OZ_AUTOTUNE=0 keeps the wave model's choice.
 struct TuneKey {
-  int Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups;
+  int Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups, b_tri;
   bool operator<(const TuneKey& o) const {
-    const int a[10] = {Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups};
-    const int b[10] = {o.Mp, o.Np, o.Kp, o.S, o.a_lower, o.c_lower, o.group, o.b_box_rows, o.cl, o.ngroups};
-    return std::lexicographical_compare(a, a + 10, b, b + 10);
+    const int a[11] = {Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups, b_tri};
+    const int b[11] = {o.Mp, o.Np, o.Kp, o.S, o.a_lower, o.c_lower, o.group, o.b_box_rows, o.cl, o.ngroups,
+                       o.b_tri};
+    return std::lexicographical_compare(a, a + 11, b, b + 11);
   }
 };
 static std::mutex g_tune_mu;
@@ -1180,7 +1198,7 @@ cudaError_t oz_slice_a(OzA& a, int op, const zd* X, int64_t ldx, int M, int K, i
 }
 
 cudaError_t oz_slice_b(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, int S, int Kp,
-                       cudaStream_t s) {
+                       cudaStream_t s, int lower_half) {
   const int Np = oz_padded_n(N);
   if (Np > b.Np_max || Kp > b.Kp_max || S > b.S_max || S < 1 || N <= 0) return cudaErrorInvalidValue;
   b.S = S; b.N = N; b.Np = Np; b.Kp = Kp;
@@ -1191,7 +1209,7 @@ cudaError_t oz_slice_b(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, i
     // op(B) = X^H (X is N x K): column j = conj(row j of X)
     CK_OZ(slice_rows(X, ldx, N, K, S, 1, b.ptr, b.slice, Kp, b.e, s));
   } else {
-    oz_slice_cols_kernel<<<Np, 256, 0, s>>>(X, ldx, K, N, S, b.ptr, b.slice, Kp, b.e);
+    oz_slice_cols_kernel<<<Np, 256, 0, s>>>(X, ldx, K, N, S, b.ptr, b.slice, Kp, b.e, lower_half);
   }
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
@@ -1203,7 +1221,7 @@ cudaError_t oz_slice_b(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, i
 cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double beta, const zd* Cin,
                        int64_t ldcin, double gamma, const zd* D, int64_t ldd, zd* out, int64_t ldo,
                        int a_lower, int c_lower, OzWorkspace& oz, cudaStream_t s,
-                       cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end) {
+                       cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end, int b_tri) {
   const int n = a.M, m = b.N, Kp = a.Kp, Mp = a.Mp, Np = b.Np;
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (S > b.S || S > a.S || S < 1 || a.Kp != b.Kp) return cudaErrorInvalidValue;
@@ -1222,6 +1240,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
   if (oz_use_tcgen05()) {
     TcParams tp;
     tp.a_lower = a_lower;
+    tp.b_tri = b_tri;
     tp.c_lower = c_lower;
     tp.nkb = Kp / OZ_BK;
     tp.tiles_m = Mp / TC_BM;
@@ -1315,7 +1334,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     // split count: the wave model's choice, or the fastest of a few candidates around it,
     // measured on the first product of each shape and kept for the process (autotuner)
     int best_splits = model_splits, best_ps = model_pair_split;
-    const TuneKey key{Mp, Np, Kp, S, a_lower, c_lower, tp.group, tp.b_box_rows, tp.cl, tp.ngroups};
+    const TuneKey key{Mp, Np, Kp, S, a_lower, c_lower, tp.group, tp.b_box_rows, tp.cl, tp.ngroups, b_tri};
     if (oz_autotune() && !tune_lookup(key, &best_splits, &best_ps)) {
       cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
       if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
@@ -1419,13 +1438,13 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
 cudaError_t oz_gemm(int opA, const zd* A, int64_t lda, int opB, const zd* B, int64_t ldb, int M, int N,
                     int K, int S, double alpha, double beta, const zd* Cin, int64_t ldcin, double gamma,
                     const zd* D, int64_t ldd, zd* C, int64_t ldc, int a_lower, int c_lower,
-                    OzWorkspace& oz, cudaStream_t s) {
+                    OzWorkspace& oz, cudaStream_t s, int b_tri, int b_lower_half) {
   cudaError_t e = oz_slice_a(oz.X, opA, A, lda, M, K, S, s);
   if (e != cudaSuccess) return e;
-  e = oz_slice_b(oz.B, opB, B, ldb, K, N, S, oz.X.Kp, s);
+  e = oz_slice_b(oz.B, opB, B, ldb, K, N, S, oz.X.Kp, s, b_lower_half);
   if (e != cudaSuccess) return e;
   return oz_product(oz.X, oz.B, S, alpha, beta, Cin, ldcin, gamma, D, ldd, C, ldc, a_lower, c_lower, oz,
-                    s, nullptr, nullptr);
+                    s, nullptr, nullptr, b_tri);
 }
 
 int64_t oz_pair_count(int S) { return (int64_t)S * (S + 1) / 2; }

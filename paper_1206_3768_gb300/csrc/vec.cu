@@ -100,6 +100,34 @@ __global__ void mirror_lower_kernel(zd* H, int64_t ldh, int n) {
   }
 }
 
+// H <- H + H^H in place (H full, n x n), exactly Hermitian: the CTA of a tile pair (I, J),
+// I >= J, reads both tiles and writes both (a diagonal tile alone), so no entry is read after
+// another CTA wrote it.
+__global__ void herm_sum_kernel(zd* H, int64_t ldh, int n) {
+  __shared__ zd lo[TILE][TILE + 1];  // tile (I, J): rows bi.., cols bj..
+  __shared__ zd up[TILE][TILE + 1];  // tile (J, I): rows bj.., cols bi..
+  const int bi = blockIdx.x * TILE, bj = blockIdx.y * TILE;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (bi < bj) return;
+  for (int r = ty; r < TILE; r += 8) {
+    const int i = bi + tx, j = bj + r;
+    if (i < n && j < n) lo[r][tx] = H[i + (int64_t)j * ldh];
+    const int i2 = bj + tx, j2 = bi + r;
+    if (i2 < n && j2 < n) up[r][tx] = H[i2 + (int64_t)j2 * ldh];
+  }
+  __syncthreads();
+  // S(i, j) = H(i, j) + conj(H(j, i)); lo[r][tx] = H(bi + tx, bj + r), up[tx][r] = H(bj + r, bi + tx)
+  for (int r = ty; r < TILE; r += 8) {
+    const int i = bi + tx, j = bj + r;
+    if (i < n && j < n) {
+      zd v = zadd(lo[r][tx], zconj(up[tx][r]));
+      if (i == j) v.y = 0.0;
+      H[i + (int64_t)j * ldh] = v;
+      if (bi != bj) H[j + (int64_t)i * ldh] = zconj(v);
+    }
+  }
+}
+
 __global__ void zero_upper_kernel(zd* L, int64_t ldl, int n) {
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -676,6 +704,13 @@ cudaError_t mirror_lower(zd* H, int64_t ldh, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int nb = (n + TILE - 1) / TILE;
   mirror_lower_kernel<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(H, ldh, n);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+cudaError_t herm_sum(zd* H, int64_t ldh, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = (n + TILE - 1) / TILE;
+  herm_sum_kernel<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(H, ldh, n);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -341,6 +341,7 @@ int lanczos_run(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int k, const zd
       return CHFSI_OK;
     }
   if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  CK(hemv_rows_prepare(n, nullptr));
   cudaGraph_t graph = nullptr;
   const long long before = g_kernel_launches;
   cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
@@ -517,7 +518,8 @@ int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const z
       CKS(gemm_auto(ctx, g));
       {
         PhaseScope ps(ctx, PH_SMALL);
-        CK(qr_pass(ws.G, ldm, m, ws.V, ldm, ws.dscale, ws.jac, ws.shiftflag, ws.status, ctx->stream));
+        CK(qr_pass(ws.G, ldm, m, ws.V, ldm, ws.dscale, ws.jac, ws.shiftflag, ws.status, ctx->stream,
+                   ws.barrier, ws.wait_limit));
         CK(scale_cols_flag(*Ya, ld, n, m, ws.dscale, ws.shiftflag + 3, ctx->stream));
       }
       CKS(gemm_auto(ctx, gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld)));

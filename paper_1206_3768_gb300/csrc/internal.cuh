@@ -83,9 +83,12 @@ cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m, cud
 // a first-order Loewdin step in FP64 when ||G - I||_F <= 1e-3 (flags[0] = 1 once that norm
 // is <= 1e-8), else an FP32 Cholesky QR step on the scaled Gram (shift on breakdown), whose
 // T applies to Y scaled by dscale (flags[3] = 1).  T is m x m (full).  scratch: m*m + 32*m
-// float2 (used when m > 144).  flags: 4 ints.
+// float2, or m*m float2 + one double per SM + 4 ints for the many-CTA pass (used when m > 144;
+// barrier: 4 words for that pass's grid barrier, nullptr keeps the one-CTA pass; spin_limit:
+// polls before a barrier wait gives up, 0 for the default).  flags: 4 ints.
 cudaError_t qr_pass(const zd* G, int64_t ldg, int m, zd* T, int64_t ldt, double* dscale, void* scratch,
-                    int* flags, int* status, cudaStream_t s);
+                    int* flags, int* status, cudaStream_t s, unsigned* barrier = nullptr,
+                    long long spin_limit = 0);
 // Y[:, j] *= d[j] when *flag (device) is set; no-op otherwise.
 cudaError_t scale_cols_flag(zd* Y, int64_t ldy, int n, int m, const double* d, const int* flag, cudaStream_t s);
 // T = D X^H (upper triangular, zero below): the right factor of Cholesky QR, Q = Y T.
@@ -168,6 +171,10 @@ cudaError_t fill_nan(double* x, int m, cudaStream_t s);
 // Lanczos pieces
 // w = H v for Hermitian H (row i read as column i); f32: FP32 multiply-adds (bound estimates).
 cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s, bool f32 = false);
+// Host-side set-up of the FP32 product for size n (kernel attribute, CTAs per SM with v in
+// shared memory; 0 when v stays in global memory), cached per host thread: called before a
+// stream capture so that none of it happens inside one.
+cudaError_t hemv_rows_prepare(int n, int* per_sm);
 cudaError_t block_dots(const zd* V, int64_t ldv, int j, const zd* w, int n, zd* c,
                        cudaStream_t s);
 cudaError_t block_update(const zd* V, int64_t ldv, int j, const zd* c, zd* w, int n,

@@ -597,6 +597,286 @@ __global__ void jacobi_finish_kernel(const zd* Ga, const zd* Gb, const zd* Vw, c
   }
 }
 
+// ------------------------------------------------------------------ Cholesky QR pass, many CTAs
+// The pass of qr_pass_kernel for blocks wider than one CTA's shared memory, spread over one
+// cooperative grid: the Gram error from per-CTA partial sums (added in CTA order, so the
+// decision is reproducible); a right-looking blocked FP32 Cholesky factorisation with
+// 32-column panels — the diagonal block on CTA 0, the panel's rows below it one warp each
+// (forward substitution against the diagonal block), the trailing lower tiles 32 x 32 each
+// over all CTAs — retried with the same shifts on a non-positive pivot; and the inverse
+// factor one warp per column.  Entries that another CTA wrote during the launch are read
+// through L2 (ld.global.cg).  A bounded grid barrier that gives up ends every CTA with
+// DEV_TIMEOUT.
+constexpr int QRC_THREADS = 256;
+constexpr int QRC_WARPS = QRC_THREADS / 32;
+constexpr int QRC_NB = 32;
+
+struct QrcParams {
+  const zd* G;
+  int64_t ldg;
+  int m;
+  zd* T;
+  int64_t ldt;
+  double* dscale;
+  float2* A;     // m x m FP32 factor (lower triangle), ld m
+  double* part;  // one partial Gram-error sum per CTA
+  int* fail;     // per attempt: the first non-positive pivot, or -1
+  int* flags;
+  int* status;
+  unsigned* bar;
+  long long spin_limit;
+};
+
+__device__ __forceinline__ float qrc_shift(int attempt) {
+  return attempt == 0 ? 0.f : (attempt == 1 ? 1e-5f : (attempt == 2 ? 1e-4f : 1e-3f));
+}
+
+__global__ void __launch_bounds__(QRC_THREADS) qr_pass_coop_kernel(const QrcParams P) {
+  extern __shared__ float2 qrc_smem[];
+  typedef float2 Tile[QRC_NB + 1];
+  Tile* D = reinterpret_cast<Tile*>(qrc_smem);  // D[r][c]: diagonal block
+  Tile* Li = D + QRC_NB;                         // rows of tile I, panel columns
+  Tile* Lk = Li + QRC_NB;                        // rows of tile K, panel columns
+  float2* xbuf = reinterpret_cast<float2*>(Lk + QRC_NB);  // one column of m per warp
+  __shared__ double red[QRC_WARPS];
+  __shared__ double s_e;
+  __shared__ int s_fail;
+  __shared__ float s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (int)gridDim.x, cta = (int)blockIdx.x, m = P.m;
+  const int64_t gtid = (int64_t)cta * QRC_THREADS + tid, gstride = (int64_t)nb * QRC_THREADS;
+  const int64_t mm = (int64_t)m * m;
+  float2* A = P.A;
+
+  // ---- e = ||G - I||_F from the lower triangle
+  if (cta == 0 && tid < 4) P.fail[tid] = -1;
+  double acc = 0.0;
+  for (int64_t e = gtid; e < mm; e += gstride) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    if (i < j) continue;
+    const zd g = P.G[i + (int64_t)j * P.ldg];
+    if (i == j) acc += (g.x - 1.0) * (g.x - 1.0) + g.y * g.y;
+    else acc += 2.0 * (g.x * g.x + g.y * g.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < QRC_WARPS; ++w) t += red[w];
+    P.part[cta] = t;
+  }
+  if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+  if (tid == 0) {
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += __ldcg(P.part + b);
+    s_e = sqrt(t);
+  }
+  __syncthreads();
+  const double e_f = s_e;  // the same in every CTA: all take the same branch below
+
+  if (e_f <= 1e-3) {
+    // ---- first-order Loewdin step, FP64
+    for (int64_t e = gtid; e < mm; e += gstride) {
+      const int i = (int)(e % m), j = (int)(e / m);
+      const zd g = (i >= j) ? P.G[i + (int64_t)j * P.ldg] : zconj(P.G[j + (int64_t)i * P.ldg]);
+      zd t = zmk(-0.5 * g.x, -0.5 * g.y);
+      if (i == j) t = zmk(1.0 - 0.5 * (g.x - 1.0), 0.0);
+      P.T[i + (int64_t)j * P.ldt] = t;
+    }
+    if (cta == 0 && tid == 0) {
+      if (e_f <= 1e-8) P.flags[0] = 1;
+      P.flags[3] = 0;
+    }
+    return;
+  }
+  if (!(e_f < 1e300)) {
+    if (cta == 0 && tid == 0) {
+      atomicOr(P.status, DEV_NOTPD);
+      P.flags[3] = 0;
+    }
+    return;
+  }
+
+  // ---- FP32 Cholesky QR step: unit-diagonal scaling D, factor of D G D + shift I
+  for (int64_t i = gtid; i < m; i += gstride) {
+    const double d = P.G[i + (int64_t)i * P.ldg].x;
+    P.dscale[i] = (d > 0.0 && isfinite(d)) ? rsqrt(d) : 1.0;
+  }
+  if (cta == 0 && tid == 0) {
+    atomicAdd(P.flags + 1, 1);
+    P.flags[3] = 1;
+  }
+  if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+  int attempt = 0;
+  for (; attempt < 4; ++attempt) {
+    const float shift = qrc_shift(attempt);
+    for (int64_t e = gtid; e < mm; e += gstride) {
+      const int i = (int)(e % m), j = (int)(e / m);
+      if (i < j) continue;
+      const zd g = P.G[i + (int64_t)j * P.ldg];
+      const double sc = __ldcg(P.dscale + i) * __ldcg(P.dscale + j);
+      float2 v = make_float2((float)(g.x * sc), (float)(g.y * sc));
+      if (i == j) v = make_float2(v.x + shift, 0.f);
+      A[i + (int64_t)j * m] = v;
+    }
+    if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+    int failed = -1;
+    for (int jb = 0; jb < m; jb += QRC_NB) {
+      const int w = min(QRC_NB, m - jb);
+      if (cta == 0) {
+        // diagonal block, unblocked in shared memory
+        for (int e = tid; e < QRC_NB * QRC_NB; e += QRC_THREADS) {
+          const int r = e % QRC_NB, c = e / QRC_NB;
+          if (r < w && c <= r) D[r][c] = __ldcg(A + (jb + r) + (int64_t)(jb + c) * m);
+        }
+        if (tid == 0) s_fail = -1;
+        __syncthreads();
+        for (int c = 0; c < w; ++c) {
+          if (tid == 0) {
+            const float d = D[c][c].x;
+            if (!(d > 0.f) || !isfinite(d)) s_fail = jb + c;
+            else s_piv = sqrtf(d);
+          }
+          __syncthreads();
+          if (s_fail >= 0) break;
+          const float inv = 1.f / s_piv;
+          if (tid > c && tid < w) {
+            D[tid][c].x *= inv;
+            D[tid][c].y *= inv;
+          }
+          if (tid == 0) D[c][c] = make_float2(s_piv, 0.f);
+          __syncthreads();
+          const int r = w - c - 1;
+          for (int e = tid; e < r * r; e += QRC_THREADS) {
+            const int ii = c + 1 + e % r, kk = c + 1 + e / r;
+            if (ii < kk) continue;
+            const float2 lij = D[ii][c], lkj = D[kk][c];
+            D[ii][kk].x -= lij.x * lkj.x + lij.y * lkj.y;
+            D[ii][kk].y -= lij.y * lkj.x - lij.x * lkj.y;
+          }
+          __syncthreads();
+        }
+        if (s_fail >= 0) {
+          if (tid == 0) P.fail[attempt] = s_fail;
+        } else {
+          for (int e = tid; e < QRC_NB * QRC_NB; e += QRC_THREADS) {
+            const int r = e % QRC_NB, c = e / QRC_NB;
+            if (r < w && c <= r) A[(jb + r) + (int64_t)(jb + c) * m] = D[r][c];
+          }
+        }
+      }
+      if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+      failed = __ldcg(P.fail + attempt);
+      if (failed >= 0) break;
+      const int r0 = jb + w;
+      if (r0 < m) {
+        // panel rows: L(i, panel) L_jj^H = A(i, panel), forward substitution, one warp a row
+        // (lane c holds column jb + c)
+        for (int e = tid; e < QRC_NB * QRC_NB; e += QRC_THREADS) {
+          const int r = e % QRC_NB, c = e / QRC_NB;
+          if (r < w && c <= r) D[r][c] = __ldcg(A + (jb + r) + (int64_t)(jb + c) * m);
+        }
+        __syncthreads();
+        for (int i = r0 + cta * QRC_WARPS + warp; i < m; i += nb * QRC_WARPS) {
+          float2 a = lane < w ? __ldcg(A + i + (int64_t)(jb + lane) * m) : make_float2(0.f, 0.f);
+          for (int c = 0; c < w; ++c) {
+            if (lane == c) {
+              const float inv = 1.f / D[c][c].x;
+              a.x *= inv;
+              a.y *= inv;
+            }
+            const float2 xc = make_float2(__shfl_sync(0xffffffffu, a.x, c), __shfl_sync(0xffffffffu, a.y, c));
+            if (lane > c && lane < w) {  // a_lane -= x_c conj(L_jj(lane, c))
+              const float2 l = D[lane][c];
+              a.x -= xc.x * l.x + xc.y * l.y;
+              a.y -= xc.y * l.x - xc.x * l.y;
+            }
+          }
+          if (lane < w) A[i + (int64_t)(jb + lane) * m] = a;
+        }
+      }
+      if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+      if (r0 < m) {
+        // trailing update A(i, k) -= L(i, panel) L(k, panel)^H on the lower 32 x 32 tiles
+        // (I, K), I >= K, of rows and columns r0.., tile t = I (I + 1) / 2 + K
+        const int nt = (m - r0 + QRC_NB - 1) / QRC_NB;
+        const int ntiles = nt * (nt + 1) / 2;
+        for (int t = cta; t < ntiles; t += nb) {
+          int I = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+          while ((I + 1) * (I + 2) / 2 <= t) ++I;
+          while (I * (I + 1) / 2 > t) --I;
+          const int K = t - I * (I + 1) / 2;
+          const int i0 = r0 + I * QRC_NB, k0 = r0 + K * QRC_NB;
+          __syncthreads();  // the previous tile's reads of Li and Lk are done
+          for (int e = tid; e < QRC_NB * QRC_NB; e += QRC_THREADS) {
+            const int r = e % QRC_NB, l = e / QRC_NB;
+            const bool lv = l < w;
+            Li[r][l] = (lv && i0 + r < m) ? __ldcg(A + (i0 + r) + (int64_t)(jb + l) * m) : make_float2(0.f, 0.f);
+            Lk[r][l] = (lv && k0 + r < m) ? __ldcg(A + (k0 + r) + (int64_t)(jb + l) * m) : make_float2(0.f, 0.f);
+          }
+          __syncthreads();
+          const int r = lane;
+#pragma unroll
+          for (int q = 0; q < QRC_NB / QRC_WARPS; ++q) {
+            const int c = warp + QRC_WARPS * q;
+            const int gi = i0 + r, gk = k0 + c;
+            if (gi >= m || gk >= m || gi < gk) continue;
+            float sx = 0.f, sy = 0.f;
+            for (int l = 0; l < w; ++l) {
+              const float2 a = Li[r][l], b = Lk[c][l];  // a conj(b)
+              sx += a.x * b.x + a.y * b.y;
+              sy += a.y * b.x - a.x * b.y;
+            }
+            float2 v = __ldcg(A + gi + (int64_t)gk * m);
+            v.x -= sx;
+            v.y -= sy;
+            A[gi + (int64_t)gk * m] = v;
+          }
+        }
+      }
+      if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+    }
+    if (failed < 0) break;
+  }
+  if (attempt == 4) {
+    if (cta == 0 && tid == 0) {
+      atomicOr(P.status, DEV_NOTPD);
+      P.flags[3] = 0;
+    }
+    return;
+  }
+  if (attempt > 0 && cta == 0 && tid == 0) P.flags[2] = 1;
+
+  // ---- X = L^{-1} one warp per column (forward substitution), T = X^H: row j of T holds
+  // conj(X(:, j)) (the scaling by D applies to Y first)
+  float2* x = xbuf + (int64_t)warp * m;
+  for (int j = cta * QRC_WARPS + warp; j < m; j += nb * QRC_WARPS) {
+    for (int i = j; i < m; ++i) {
+      float2 sacc = make_float2(0.f, 0.f);
+      for (int k = j + lane; k < i; k += 32) {
+        const float2 p = cmulf(__ldcg(A + i + (int64_t)k * m), x[k]);
+        sacc.x += p.x;
+        sacc.y += p.y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+        sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
+      }
+      if (lane == 0) {
+        const float dinv = 1.f / __ldcg(A + i + (int64_t)i * m).x;
+        x[i] = (i == j) ? make_float2(dinv, 0.f) : make_float2(-sacc.x * dinv, -sacc.y * dinv);
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < m; i += 32)
+      P.T[j + (int64_t)i * P.ldt] = (i < j) ? zmk(0.0, 0.0) : zmk((double)x[i].x, -(double)x[i].y);
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 cudaError_t small_cholesky(zd* G, int64_t ldg, int m, int scale, int shift_on_fail,
@@ -620,8 +900,39 @@ cudaError_t trinv_lower(const zd* L, int64_t ldl, zd* X, int64_t ldx, int m,
 }
 
 cudaError_t qr_pass(const zd* G, int64_t ldg, int m, zd* T, int64_t ldt, double* dscale, void* scratch,
-                    int* flags, int* status, cudaStream_t s) {
+                    int* flags, int* status, cudaStream_t s, unsigned* barrier, long long spin_limit) {
   if (m <= 0) return cudaSuccess;
+  if (m > QR_SMEM_MMAX && barrier) {
+    // one cooperative grid of one CTA per SM; scratch: the FP32 factor, then the per-CTA
+    // partial sums and the per-attempt failure words (m m float2 + grid doubles + 4 ints,
+    // within the 3 mp^2 complex entries of the Jacobi work area it shares)
+    const size_t smem = sizeof(float2) * (3 * QRC_NB * (QRC_NB + 1) + (size_t)QRC_WARPS * m);
+    static const cudaError_t coop_attr =
+        cudaFuncSetAttribute(qr_pass_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacSmemMax);
+    if (coop_attr != cudaSuccess) return coop_attr;
+    int per_sm = 0;
+    cudaError_t e = cudaSuccess;
+    if (smem <= (size_t)kJacSmemMax)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_pass_coop_kernel, QRC_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm >= 1) {
+      const int grid = sm_count();
+      e = cudaMemsetAsync(barrier, 0, 4 * sizeof(unsigned), s);
+      if (e != cudaSuccess) return e;
+      QrcParams P;
+      P.G = G; P.ldg = ldg; P.m = m; P.T = T; P.ldt = ldt; P.dscale = dscale;
+      P.A = static_cast<float2*>(scratch);
+      P.part = reinterpret_cast<double*>(P.A + (int64_t)m * m);
+      P.fail = reinterpret_cast<int*>(P.part + grid);
+      P.flags = flags; P.status = status; P.bar = barrier;
+      P.spin_limit = spin_limit > 0 ? spin_limit : kBarrierSpinLimit;
+      void* args[] = {(void*)&P};
+      e = cudaLaunchCooperativeKernel((const void*)qr_pass_coop_kernel, dim3(grid), dim3(QRC_THREADS), args,
+                                      smem, s);
+      CHFSI_COUNT_LAUNCH();
+      return e;
+    }
+  }
   const size_t smem = (m <= QR_SMEM_MMAX) ? sizeof(float2) * ((size_t)m * m + 32 * (size_t)m) : 0;
   static const cudaError_t attr = cudaFuncSetAttribute(
       qr_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

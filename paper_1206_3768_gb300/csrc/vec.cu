@@ -467,12 +467,34 @@ __global__ void hemv_rows_kernel(const zd* H, int64_t ldh, const zd* v, zd* w, i
   }
 }
 
+// FP64 -> FP32 by truncation of the significand, in integer operations (a conversion
+// instruction would run at the FP64 pipe's rate, which would bound the whole product):
+// magnitudes below 2^-126 become 0, above the FP32 range infinity; relative error < 2^-23.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int e = ((hi >> 20) & 0x7FF) - 896;  // FP32 biased exponent (1023 - 127)
+  unsigned b = (unsigned)hi & 0x80000000u;
+  if (e >= 255) b |= 0x7F800000u;
+  else if (e > 0) b |= ((unsigned)e << 23) | (((unsigned)hi & 0xFFFFFu) << 3) | (lo >> 29);
+  return __uint_as_float(b);
+}
+
 // The same product with FP32 multiply-adds on the FP64 data (per-lane FP32 partial sums of
-// at most 8 terms, then FP64): relative error ~1e-7, enough for a spectral bound, and no
-// longer limited by this part's FP64 issue rate.
-__global__ void hemv_rows_f32_kernel(const zd* H, int64_t ldh, const zd* v, zd* w, int n) {
+// at most 8 terms, then FP64): relative error ~1e-7, enough for a spectral bound.  The
+// operands are narrowed by f32_trunc; v once per CTA into shared memory (vsh, n entries,
+// when the launch gives it room) or per use from global memory.
+__global__ void hemv_rows_f32_kernel(const zd* H, int64_t ldh, const zd* v, zd* w, int n, int v_in_smem) {
+  extern __shared__ float2 vsh[];
   const int lane = threadIdx.x & 31;
   const int warps = (blockDim.x >> 5) * gridDim.x;
+  if (v_in_smem) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const zd x = v[j];
+      vsh[j] = make_float2(f32_trunc(x.x), f32_trunc(x.y));
+    }
+    __syncthreads();
+  }
   for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
     const zd* col = H + (int64_t)i * ldh;
     double sr = 0.0, si = 0.0;
@@ -482,10 +504,17 @@ __global__ void hemv_rows_f32_kernel(const zd* H, int64_t ldh, const zd* v, zd* 
       for (int u = 0; u < 8; ++u) {
         const int j = j0 + u * 32 + lane;
         if (j < n) {
-          const zd h = col[j], x = v[j];
-          const float hx = (float)h.x, hy = (float)h.y, xx = (float)x.x, xy = (float)x.y;
-          fr = fmaf(hx, xx, fmaf(hy, xy, fr));
-          fi = fmaf(hx, xy, fmaf(-hy, xx, fi));
+          const zd h = col[j];
+          float2 x;
+          if (v_in_smem) {
+            x = vsh[j];
+          } else {
+            const zd xv = v[j];
+            x = make_float2(f32_trunc(xv.x), f32_trunc(xv.y));
+          }
+          const float hx = f32_trunc(h.x), hy = f32_trunc(h.y);
+          fr = fmaf(hx, x.x, fmaf(hy, x.y, fr));
+          fi = fmaf(hx, x.y, fmaf(-hy, x.x, fi));
         }
       }
       sr += (double)fr;
@@ -827,11 +856,40 @@ cudaError_t fill_nan(double* x, int m, cudaStream_t s) {
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
+cudaError_t hemv_rows_prepare(int n, int* per_sm) {
+  constexpr size_t kVshMax = 128 * 1024;
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      hemv_rows_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kVshMax);
+  if (attr != cudaSuccess) return attr;
+  static thread_local int last_n = -1, last_per_sm = 0;
+  const size_t smem = sizeof(float2) * (size_t)n;
+  if (n != last_n) {
+    int p = 0;
+    if (n > 0 && smem <= kVshMax) {
+      const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, hemv_rows_f32_kernel, 256, smem);
+      if (e != cudaSuccess) return e;
+    }
+    last_n = n;
+    last_per_sm = p;
+  }
+  if (per_sm) *per_sm = last_per_sm;
+  return cudaSuccess;
+}
 cudaError_t hemv_rows(const zd* H, int64_t ldh, const zd* v, zd* w, int n, cudaStream_t s, bool f32) {
   const int warps_per_block = 8;
-  const int blocks = std::max(1, std::min((n + warps_per_block - 1) / warps_per_block, 16 * sm_count()));
-  if (f32) hemv_rows_f32_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(H, ldh, v, w, n);
-  else hemv_rows_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(H, ldh, v, w, n);
+  int blocks = std::max(1, std::min((n + warps_per_block - 1) / warps_per_block, 16 * sm_count()));
+  if (f32) {
+    // v in shared memory up to 128 KB (n <= 16384), with as many CTAs as fit on the SMs
+    int per_sm = 0;
+    const cudaError_t e = hemv_rows_prepare(n, &per_sm);
+    if (e != cudaSuccess) return e;
+    const int in_smem = per_sm > 0 ? 1 : 0;
+    if (in_smem) blocks = std::max(1, std::min(blocks, per_sm * sm_count()));
+    hemv_rows_f32_kernel<<<blocks, 32 * warps_per_block, in_smem ? sizeof(float2) * (size_t)n : 0, s>>>(
+        H, ldh, v, w, n, in_smem);
+  } else {
+    hemv_rows_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(H, ldh, v, w, n);
+  }
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -202,6 +202,39 @@ def test_orthonormalize_matches_oracle_span(ctx, ctx64, n, m, k, mode):
     assert np.linalg.norm(got @ got.conj().T - ref @ ref.conj().T) < 1e-9
 
 
+@pytest.mark.parametrize("n,m,k", [(1400, 400, 30), (2600, 1200, 0), (1300, 161, 7)])
+def test_orthonormalize_wide_blocks_match_oracle_span(n, m, k):
+    """Blocks wider than one CTA's shared memory: the FP32 Cholesky QR steps run as one
+    cooperative grid (blocked factorisation, 32-column panels; a ragged last panel at
+    m = 161, 400 and 1200 = 37.5 panels)."""
+    rng = _rng(7 * n + m + k)
+    YL = np.linalg.qr(_cgauss(rng, n, k))[0] if k else None
+    Y = _cgauss(rng, n, m) * np.logspace(0, -6, m)[None, :]
+    with cb.Solver(n, m) as s:
+        got = _np(cb.chfsi_orthonormalize(s.ctx, _t(Y), _t(YL) if k else None))
+    ref = O.orthonormalize(Y, YL)
+    assert np.max(np.abs(got.conj().T @ got - np.eye(m))) < 1e-13
+    if k:
+        assert np.max(np.abs(YL.conj().T @ got)) < 1e-13
+    assert np.linalg.norm(got @ got.conj().T - ref @ ref.conj().T) < 1e-9
+
+
+def test_orthonormalize_wide_block_near_rank_deficiency():
+    """A wide block whose Gram matrix breaks plain FP32 Cholesky takes the shifted retry
+    inside the cooperative pass."""
+    n, m = 900, 200
+    rng = _rng(15)
+    base = _cgauss(rng, n, m)
+    Y = base.copy()
+    Y[:, 150] = base[:, 149] + 1e-9 * _cgauss(rng, n)
+    with cb.Solver(n, m) as s:
+        got = _np(cb.chfsi_orthonormalize(s.ctx, _t(Y)))
+    assert np.max(np.abs(got.conj().T @ got - np.eye(m))) < 1e-12
+    keep = [j for j in range(m) if j != 150]
+    P = got @ got.conj().T
+    assert np.linalg.norm(P @ base[:, keep] - base[:, keep]) < 1e-6 * np.linalg.norm(base)
+
+
 @pytest.mark.parametrize("mode", ["split", "fp64"])
 def test_orthonormalize_survives_near_rank_deficiency(ctx, ctx64, mode):
     """A Gram matrix beyond plain Cholesky QR takes the shifted path."""

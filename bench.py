@@ -550,18 +550,26 @@ def run_heev_case(args):
     m = args.case_m
     M = torch.randn(m, m, dtype=torch.complex128, generator=g)
     G = (0.5 * (M + M.mH)).to(dev)
+    # nearly diagonal, as the Gram matrix of a warm loop: sorted diagonal, 1e-6 coupling
+    D = torch.diag(torch.linspace(-2.0, 2.0, m, dtype=torch.float64)).to(torch.complex128)
+    N = torch.randn(m, m, dtype=torch.complex128, generator=g)
+    Gd = (D + 0.5e-6 * (N + N.mH)).to(dev)
+    out = {"case": "heev", "m": m}
     with cb.Solver(max(args.case_n, m), m) as s:
-        for _ in range(args.case_reps):
-            cb.chfsi_heev(s.ctx, G)
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        w, V = cb.chfsi_heev(s.ctx, G)
-        ev1.record()
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    resid = float(((G @ V - V * w.to(V.dtype).unsqueeze(0)).abs().max() / G.abs().max()).item())
-    print(json.dumps({"case": "heev", "m": m, "ms": ms, "rel_resid": resid}))
+        for name, fn in (("fp64", cb.chfsi_heev), ("df", cb.chfsi_heev_df)):
+            for label, A in (("random", G), ("near_diag", Gd)):
+                for _ in range(args.case_reps):
+                    fn(s.ctx, A)
+                torch.cuda.synchronize()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record()
+                w, V = fn(s.ctx, A)
+                ev1.record()
+                torch.cuda.synchronize()
+                resid = float(((A @ V - V * w.to(V.dtype).unsqueeze(0)).abs().max() / A.abs().max()).item())
+                orth = float((V.mH @ V - torch.eye(m, dtype=V.dtype, device=dev)).abs().max().item())
+                out[f"{name}_{label}"] = {"ms": ev0.elapsed_time(ev1), "rel_resid": resid, "orth": orth}
+    print(json.dumps(out))
 
 
 def run_batch(args):

@@ -238,6 +238,15 @@ int chfsi_degrees(chfsi_ctx* ctx, int32_t m, const double* theta, const double* 
 int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double* w,
                chfsi_z* V, int64_t ldv);
 
+/* The same decomposition (Rayleigh-Ritz step of Algorithm 1) as the mixed-precision solve
+ * runs it on wide blocks: the matrix and the eigenvector rows held as double-float pairs
+ * (hi + lo FP32 numbers, about 48 significand bits) and rotated with FP32 instructions, the
+ * rotations computed in FP64; eigenvalue and orthogonality errors about 2^-46 ||G||_F.
+ * Below 64 columns it is chfsi_heev.  Arguments, layout and errors as chfsi_heev
+ * (EINVAL for bad sizes or NULL; ETIMEOUT; ENOCONV after 40 sweeps). */
+int chfsi_heev_df(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double* w,
+                  chfsi_z* V, int64_t ldv);
+
 /* ---------------------------------------------------------------- allocation-free variant
  * The paper has no counterpart to this entry point; it serves callers that cannot call
  * cudaMalloc (an application whose pool allocator owns all device memory, or a

@@ -109,6 +109,7 @@ _SIGS = {
     "chfsi_degrees": (c_int32, [_P, c_int32, _P, _P, c_double, c_double, c_double, c_int32,
                                 c_int32, c_int32, _P]),
     "chfsi_heev": (c_int32, [_P, c_int32, _P, c_int64, _P, _P, c_int64]),
+    "chfsi_heev_df": (c_int32, [_P, c_int32, _P, c_int64, _P, _P, c_int64]),
     "chfsi_mlp_init": (None, [_P, c_uint64]),
     "chfsi_mlp_train": (c_int32, [_P, _P, _P, _P, c_int64, c_int32, c_int32, ctypes.c_float, c_uint64, _P]),
     "chfsi_mlp_gradient": (c_int32, [_P, _P, _P, _P, c_int64, _P, _P]),
@@ -388,6 +389,15 @@ def chfsi_heev(ctx, G: torch.Tensor):
     w = torch.empty(m, dtype=torch.float64, device=G.device)
     V = fortran_empty(m, m, G.device)
     _check(ctx, load().chfsi_heev(ctx, m, _ptr(Gf), _ld(Gf), _ptr(w), _ptr(V), _ld(V)))
+    return w, V
+
+
+def chfsi_heev_df(ctx, G: torch.Tensor):
+    m = G.shape[0]
+    Gf = fortran(G)
+    w = torch.empty(m, dtype=torch.float64, device=G.device)
+    V = fortran_empty(m, m, G.device)
+    _check(ctx, load().chfsi_heev_df(ctx, m, _ptr(Gf), _ld(Gf), _ptr(w), _ptr(V), _ld(V)))
     return w, V
 
 

@@ -561,6 +561,16 @@ int orthonormalize_block(chfsi_ctx* ctx, int n, int m, zd** Ya, zd** Yb, const z
   return CHFSI_OK;
 }
 
+// Narrowest Rayleigh-Ritz block whose eigensolver runs in double-float arithmetic in mixed
+// precision: environment variable CHFSI_JACOBI_DF_MIN (default 384 columns).
+int jacobi_df_min() {
+  static const int v = [] {
+    const char* e = std::getenv("CHFSI_JACOBI_DF_MIN");
+    return e ? std::atoi(e) : 384;
+  }();
+  return v;
+}
+
 // Rayleigh-Ritz on the m columns of *Ya: theta (device), *Ya <- Ritz vectors, *W <- H *Ya.
 int rayleigh_ritz_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya, zd** Yb,
                         zd** W, zd** Zb, double* theta, int rr_slices = 0) {
@@ -580,8 +590,12 @@ int rayleigh_ritz_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, 
   CK(mirror_lower(ws.G, ldm, m, ctx->stream));
   {
     PhaseScope ps(ctx, PH_EIG);
-    CK(jacobi_heev(ws.G, ldm, m, theta, ws.V, ldm, ws.jac, ws.barrier, ws.status, ctx->stream,
-                   ws.wait_limit));
+    if (ctx->opts.precision == 1 && m >= jacobi_df_min())
+      CK(jacobi_heev_df(ws.G, ldm, m, theta, ws.V, ldm, ws.jac, ws.barrier, ws.status, ctx->stream,
+                        ws.wait_limit));
+    else
+      CK(jacobi_heev(ws.G, ldm, m, theta, ws.V, ldm, ws.jac, ws.barrier, ws.status, ctx->stream,
+                     ws.wait_limit));
   }
   CKS(gemm_auto(ctx, gd(n, m, m, *Ya, ld, OPN, ws.V, ldm, OPN, *Yb, ld)));
   CKS(gemm_auto(ctx, gd(n, m, m, *W, ld, OPN, ws.V, ldm, OPN, *Zb, ld)));
@@ -1586,6 +1600,19 @@ int chfsi_heev(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double*
                  ctx->stream, ctx->ws.wait_limit));
   CK(cudaStreamSynchronize(ctx->stream));
   return check_status(ctx, "chfsi_heev");
+}
+
+int chfsi_heev_df(chfsi_ctx* ctx, int32_t m, const chfsi_z* G, int64_t ldg, double* w, chfsi_z* V,
+                  int64_t ldv) {
+  entry_guard("chfsi_heev_df");
+  if (!ctx || !G || !w || !V || m <= 0 || ldg < m || ldv < m) return set_err(ctx, CHFSI_EINVAL, "bad args");
+  if (m > ctx->ws.blk_max) return set_err(ctx, CHFSI_EINVAL, "m > blk_max");
+  cudaSetDevice(ctx->ws.dev);
+  CKS(reset_status(ctx));
+  CK(jacobi_heev_df(Z(G), ldg, m, w, Z(V), ldv, ctx->ws.jac, ctx->ws.barrier, ctx->ws.status,
+                    ctx->stream, ctx->ws.wait_limit));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx, "chfsi_heev_df");
 }
 
 int chfsi_zgemm(chfsi_ctx* ctx, char opa, char opb, int32_t M, int32_t N, int32_t K, double alpha,

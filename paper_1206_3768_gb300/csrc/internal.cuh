@@ -100,6 +100,12 @@ cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* 
 cudaError_t jacobi_heev(const zd* G, int64_t ldg, int m, double* w, zd* V, int64_t ldv,
                         zd* work, unsigned* barrier, int* status, cudaStream_t s,
                         long long spin_limit = 0);
+// The same decomposition with the rotations applied in double-float arithmetic (about 48
+// significand bits; FP32 instructions instead of the FP64 pipe): the mixed-precision path's
+// solver for wide blocks.  Same arguments and work area; below 64 columns the FP64 solver.
+cudaError_t jacobi_heev_df(const zd* G, int64_t ldg, int m, double* w, zd* V, int64_t ldv,
+                           zd* work, unsigned* barrier, int* status, cudaStream_t s,
+                           long long spin_limit = 0);
 
 // Deviation angles (Section 2.2, Fig. 1): B-norms of columns from W = B X; greedy
 // one-to-one association from |M|; the B-orthogonal parts R of the associated current

@@ -597,6 +597,341 @@ __global__ void jacobi_finish_kernel(const zd* Ga, const zd* Gb, const zd* Vw, c
   }
 }
 
+// ------------------------------------------------------------------ Jacobi in double-float
+// The Rayleigh-Ritz eigensolver of the mixed-precision path for wide blocks: the cyclic
+// parallel Jacobi of jacobi_kernel with the matrix and the CTA's rows of V held as
+// unevaluated sums of two FP32 numbers (hi + lo, |lo| <= ulp(hi) / 2, about 48 significand
+// bits) and rotated with FP32 arithmetic (products made exact by fma, sums by two-sum), since
+// the FP64 pipe bounds the FP64 solver on wide blocks.  Each rotation is computed in FP64
+// from the double-float entries by the CTA that owns its pair and published in global memory
+// (two buffers by round parity) behind a grid barrier, so a round costs two barriers.  The
+// matrix is scaled by a power of two (exact) so that ||G||_F lies in [1/2, 1), which keeps
+// the FP32 convergence test in range.  Convergence: no off-diagonal entry above the
+// threshold (tested on the high words, spread over the CTAs), or a sweep without an active
+// rotation.
+struct RotDF {
+  float2 c, s;    // cosine and sine, hi + lo
+  float2 wr, wi;  // e^{-i phi}: real and imaginary part, hi + lo
+  int active;
+  int pad;
+};
+// bytes of the rotation table at the head of the Jacobi CTA's shared memory (16-aligned)
+__host__ __device__ __forceinline__ size_t rotdf_bytes(int half) {
+  return (sizeof(RotDF) * (size_t)half + 15) / 16 * 16;
+}
+__device__ __forceinline__ float4 rot_w(const RotDF& R) { return make_float4(R.wr.x, R.wr.y, R.wi.x, R.wi.y); }
+
+__device__ __forceinline__ float2 df_of(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double dbl_of(float h, float l) { return (double)h + (double)l; }
+
+// s + e: a sum of double-float products, the error terms kept apart until df_norm
+struct DfSum {
+  float s, e;
+};
+__device__ __forceinline__ DfSum df_prod(float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);  // the rounding error of ah bh, exactly
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  DfSum r;
+  r.s = p;
+  r.e = e;
+  return r;
+}
+__device__ __forceinline__ void df_acc(DfSum& a, const DfSum& b) {
+  const float s = __fadd_rn(a.s, b.s);  // two-sum: s + err = a.s + b.s exactly
+  const float bb = __fsub_rn(s, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(b.s, bb));
+  a.s = s;
+  a.e = __fadd_rn(__fadd_rn(a.e, b.e), err);
+}
+__device__ __forceinline__ float2 df_norm(const DfSum& a) {
+  const float s = __fadd_rn(a.s, a.e);
+  return make_float2(s, __fsub_rn(a.e, __fsub_rn(s, a.s)));
+}
+__device__ __forceinline__ float4 dfc(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
+__device__ __forceinline__ float4 dfc_conj(float4 x) { return make_float4(x.x, x.y, -x.z, -x.w); }
+// x w
+__device__ __forceinline__ float4 dfc_mul(float4 x, float4 w) {
+  DfSum re = df_prod(x.x, x.y, w.x, w.y);
+  df_acc(re, df_prod(-x.z, -x.w, w.z, w.w));
+  DfSum im = df_prod(x.x, x.y, w.z, w.w);
+  df_acc(im, df_prod(x.z, x.w, w.x, w.y));
+  return dfc(df_norm(re), df_norm(im));
+}
+// conj(w) x
+__device__ __forceinline__ float4 dfc_mulconj(float4 x, float4 w) {
+  DfSum re = df_prod(x.x, x.y, w.x, w.y);
+  df_acc(re, df_prod(x.z, x.w, w.z, w.w));
+  DfSum im = df_prod(x.z, x.w, w.x, w.y);
+  df_acc(im, df_prod(-x.x, -x.y, w.z, w.w));
+  return dfc(df_norm(re), df_norm(im));
+}
+// a x + b y, a and b real
+__device__ __forceinline__ float4 dfc_comb(float2 a, float4 x, float2 b, float4 y) {
+  DfSum re = df_prod(a.x, a.y, x.x, x.y);
+  df_acc(re, df_prod(b.x, b.y, y.x, y.y));
+  DfSum im = df_prod(a.x, a.y, x.z, x.w);
+  df_acc(im, df_prod(b.x, b.y, y.z, y.w));
+  return dfc(df_norm(re), df_norm(im));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+struct JacDfParams {
+  const zd* G;
+  int64_t ldg;
+  int m, mp;
+  float4* Ga;
+  float4* Gb;
+  zd* Vw;          // output rows of V (mp x mp, ld mp); during the run: rotations, partials
+  unsigned* bar;
+  int* status;
+  int max_sweeps;
+  long long spin_limit;
+  int pairs_per_cta;
+};
+
+__global__ void __launch_bounds__(JAC_THREADS) jacobi_df_kernel(const JacDfParams P) {
+  extern __shared__ unsigned char smem_raw[];
+  const int mp = P.mp, half = mp / 2, ppc = P.pairs_per_cta;
+  RotDF* rot = reinterpret_cast<RotDF*>(smem_raw);
+  float4* vrow = reinterpret_cast<float4*>(smem_raw + rotdf_bytes(half));  // 2 ppc x mp
+  float4* col = vrow + (size_t)2 * ppc * mp;                                          // 2 x mp
+  __shared__ double red[JAC_THREADS];
+  __shared__ float redf[JAC_THREADS];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const unsigned nb = gridDim.x;
+  const int cta = blockIdx.x;
+  const int slot0 = cta * ppc;
+  const int nslot = max(0, min(ppc, half - slot0));
+  // global scratch inside Vw until the end: rotations of the two round parities, partials
+  RotDF* rotg = reinterpret_cast<RotDF*>(P.Vw);
+  double* part = reinterpret_cast<double*>(rotg + 2 * half);
+  float* partf = reinterpret_cast<float*>(part + nb);
+
+  // ---- ||G||_F from per-CTA partial sums (fixed order), the power-of-two scale
+  double acc = 0.0;
+  for (int64_t e = (int64_t)cta * nt + tid; e < (int64_t)P.m * P.m; e += (int64_t)nb * nt) {
+    const int i = (int)(e % P.m), j = (int)(e / P.m);
+    acc += zabs2(P.G[i + (int64_t)j * P.ldg]);
+  }
+  red[tid] = acc;
+  __syncthreads();
+  for (int o = nt / 2; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  if (tid == 0) part[cta] = red[0];
+  if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+  __shared__ double s_norm;
+  if (tid == 0) {
+    double t = 0.0;
+    for (unsigned b = 0; b < nb; ++b) t += __ldcg(part + b);
+    s_norm = sqrt(t);
+  }
+  __syncthreads();
+  const double nrm = s_norm;
+  const int kexp = nrm > 0.0 ? ilogb(nrm) + 1 : 0;
+  const double scale = ldexp(1.0, -kexp);       // ||G scale||_F in [1/2, 1)
+  const double thresh = 1e-15 * nrm * scale + 1e-300;
+  const float thresh2f = (float)(thresh * thresh);
+
+  // ---- set-up: rows 2 slot, 2 slot + 1 of Ga (scaled, double-float) and of V (identity)
+  for (int rr = 0; rr < 2 * nslot; ++rr) {
+    const int i = 2 * slot0 + rr;
+    for (int j = tid; j < mp; j += nt) {
+      zd v = zmk(0.0, 0.0);
+      if (i < P.m && j < P.m) v = P.G[i + (int64_t)j * P.ldg];
+      if (i == j) v.y = 0.0;
+      P.Ga[i + (int64_t)j * mp] = dfc(df_of(v.x * scale), df_of(v.y * scale));
+      vrow[rr * mp + j] = make_float4(i == j ? 1.f : 0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+
+  int parity = 0, sweep = 0;
+  for (; sweep < P.max_sweeps; ++sweep) {
+    {  // largest off-diagonal |G_ij|^2 (high words) over all CTAs' shares
+      const float4* cur = parity ? P.Gb : P.Ga;
+      float mx = 0.f;
+      for (int64_t e = (int64_t)cta * nt + tid; e < (int64_t)mp * mp; e += (int64_t)nb * nt) {
+        const int i = (int)(e % mp), j = (int)(e / mp);
+        if (i != j) {
+          const float4 g = __ldcg(cur + e);
+          mx = fmaxf(mx, g.x * g.x + g.z * g.z);
+        }
+      }
+      redf[tid] = mx;
+      __syncthreads();
+      for (int o = nt / 2; o > 0; o >>= 1) {
+        if (tid < o) redf[tid] = fmaxf(redf[tid], redf[tid + o]);
+        __syncthreads();
+      }
+      if (tid == 0) partf[cta] = redf[0];
+      if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+      __shared__ int s_done;
+      if (tid == 0) {
+        float m2 = 0.f;
+        for (unsigned b = 0; b < nb; ++b) m2 = fmaxf(m2, __ldcg(partf + b));
+        s_done = !(m2 > thresh2f);
+      }
+      __syncthreads();
+      if (s_done) break;
+    }
+    int sweep_any = 0;
+    for (int round = 0; round < mp - 1; ++round) {
+      const float4* src = parity ? P.Gb : P.Ga;
+      float4* dst = parity ? P.Ga : P.Gb;
+      RotDF* rg = rotg + (round & 1) * half;
+      // the rotations of this CTA's pairs, in FP64 from the double-float entries
+      for (int k = tid; k < nslot; k += nt) {
+        const int slot = slot0 + k;
+        int a, b;
+        pair_of(round, slot, mp, a, b);
+        const float4 ga = __ldcg(src + a + (int64_t)a * mp), gd_ = __ldcg(src + b + (int64_t)b * mp);
+        const float4 gb = __ldcg(src + a + (int64_t)b * mp);
+        const double av = dbl_of(ga.x, ga.y), dv = dbl_of(gd_.x, gd_.y);
+        const zd bv = zmk(dbl_of(gb.x, gb.y), dbl_of(gb.z, gb.w));
+        const double ab2 = zabs2(bv);
+        RotDF R;
+        R.pad = 0;
+        if (!(ab2 > thresh * thresh)) {
+          R.c = make_float2(1.f, 0.f);
+          R.s = make_float2(0.f, 0.f);
+          R.wr = make_float2(1.f, 0.f);
+          R.wi = make_float2(0.f, 0.f);
+          R.active = 0;
+        } else {
+          const double inv_ab = rsqrt(ab2);
+          const double zeta = 0.5 * (dv - av) * inv_ab;
+          const double az = fabs(zeta);
+          const double t_ = (zeta >= 0.0 ? 1.0 : -1.0) / (az + (az < 1e150 ? sqrt(1.0 + zeta * zeta) : az));
+          const double c = rsqrt(1.0 + t_ * t_);
+          R.c = df_of(c);
+          R.s = df_of(t_ * c);
+          R.wr = df_of(bv.x * inv_ab);
+          R.wi = df_of(-bv.y * inv_ab);
+          R.active = 1;
+        }
+        rg[slot] = R;
+      }
+      if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+      int any = 0;
+      for (int t = tid; t < half; t += nt) {
+        const float2* src2 = reinterpret_cast<const float2*>(rg + t);  // 5 x 8 bytes through L2
+        RotDF R;
+        R.c = __ldcg(src2);
+        R.s = __ldcg(src2 + 1);
+        R.wr = __ldcg(src2 + 2);
+        R.wi = __ldcg(src2 + 3);
+        const float2 ap = __ldcg(src2 + 4);
+        R.active = __float_as_int(ap.x);
+        R.pad = 0;
+        rot[t] = R;
+        any |= R.active;
+      }
+      // every CTA reads the same rotations and reaches the same decision
+      if (!__syncthreads_or(any)) continue;
+      sweep_any = 1;
+      for (int k = 0; k < nslot; ++k) {
+        const int slot = slot0 + k;
+        int p, q;
+        pair_of(round, slot, mp, p, q);
+        float4* cp = col;       // column p: cp[j] = conj(G[p, j])
+        float4* cq = col + mp;  // column q
+        for (int j = tid; j < mp; j += nt) {
+          cp[j] = __ldcg(src + j + (int64_t)p * mp);
+          cq[j] = __ldcg(src + j + (int64_t)q * mp);
+        }
+        __syncthreads();
+        const RotDF RP = rot[slot];
+        for (int t = tid; t < half; t += nt) {
+          int r, s;
+          pair_of(round, t, mp, r, s);
+          float4 l0p = dfc_conj(cp[r]), l1p = dfc_conj(cp[s]), l0q = dfc_conj(cq[r]), l1q = dfc_conj(cq[s]);
+          if (RP.active) {
+            // left: U_P^H = [[c, -s e^{i phi}], [s, c e^{i phi}]] on rows p, q (e^{i phi} = conj(w))
+            const float4 wp = rot_w(RP);
+            const float4 v0 = dfc_mulconj(l0q, wp), v1 = dfc_mulconj(l1q, wp);
+            const float4 m00 = l0p, m01 = l1p;
+            l0p = dfc_comb(RP.c, m00, df_neg(RP.s), v0);
+            l1p = dfc_comb(RP.c, m01, df_neg(RP.s), v1);
+            l0q = dfc_comb(RP.s, m00, RP.c, v0);
+            l1q = dfc_comb(RP.s, m01, RP.c, v1);
+          }
+          const RotDF RR = rot[t];
+          float4 np0 = l0p, np1 = l1p, nq0 = l0q, nq1 = l1q;
+          if (RR.active) {
+            // right: U_R = [[c, s], [-s w, c w]] on columns r, s
+            const float4 wr = rot_w(RR);
+            const float4 up = dfc_mul(l1p, wr), uq = dfc_mul(l1q, wr);
+            np0 = dfc_comb(RR.c, l0p, df_neg(RR.s), up);
+            np1 = dfc_comb(RR.s, l0p, RR.c, up);
+            nq0 = dfc_comb(RR.c, l0q, df_neg(RR.s), uq);
+            nq1 = dfc_comb(RR.s, l0q, RR.c, uq);
+          }
+          if (t == slot) {  // diagonal block: exact diagonal result
+            np0.z = 0.f; np0.w = 0.f;
+            nq1.z = 0.f; nq1.w = 0.f;
+            if (RP.active) {
+              np1 = make_float4(0.f, 0.f, 0.f, 0.f);
+              nq0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+          cp[r] = dfc_conj(np0);
+          cp[s] = dfc_conj(np1);
+          cq[r] = dfc_conj(nq0);
+          cq[s] = dfc_conj(nq1);
+        }
+        __syncthreads();
+        for (int j = tid; j < mp; j += nt) {
+          dst[j + (int64_t)p * mp] = cp[j];
+          dst[j + (int64_t)q * mp] = cq[j];
+        }
+        __syncthreads();
+      }
+      // V rows 2 slot + row (shared memory): V[i, R] <- V[i, R] U_R
+      for (int e = tid; e < 2 * nslot * half; e += nt) {
+        const int vr = e / half, t = e - vr * half;
+        const RotDF RR = rot[t];
+        if (!RR.active) continue;
+        int r, s;
+        pair_of(round, t, mp, r, s);
+        float4* vi = vrow + vr * mp;
+        const float4 a0 = vi[r], u = dfc_mul(vi[s], rot_w(RR));
+        vi[r] = dfc_comb(RR.c, a0, df_neg(RR.s), u);
+        vi[s] = dfc_comb(RR.s, a0, RR.c, u);
+      }
+      parity ^= 1;
+      if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+    }
+    if (!sweep_any) break;
+  }
+  // every CTA is past its last read of the rotations and partials kept in Vw
+  if (!grid_barrier(P.bar, nb, P.status, P.spin_limit)) return;
+  const float4* fin = parity ? P.Gb : P.Ga;
+  zd* diag_out = reinterpret_cast<zd*>(parity ? P.Ga : P.Gb);  // the buffer no longer read
+  const double unscale = ldexp(1.0, kexp);
+  for (int rr = 0; rr < 2 * nslot; ++rr) {
+    const int i = 2 * slot0 + rr;
+    for (int j = tid; j < mp; j += nt) {
+      const float4 v = vrow[rr * mp + j];
+      P.Vw[i + (int64_t)j * mp] = zmk(dbl_of(v.x, v.y), dbl_of(v.z, v.w));
+    }
+    if (tid == 0) {
+      const float4 g = __ldcg(fin + i + (int64_t)i * mp);
+      diag_out[i + (int64_t)i * mp] = zmk(dbl_of(g.x, g.y) * unscale, 0.0);
+    }
+  }
+  if (cta == 0 && tid == 0) {
+    if (sweep >= P.max_sweeps) atomicOr(P.status, DEV_NOCONV);
+    P.bar[2] = parity ^ 1;  // the finishing kernel reads the diagonal from diag_out
+  }
+}
+
 // ------------------------------------------------------------------ Cholesky QR pass, many CTAs
 // The pass of qr_pass_kernel for blocks wider than one CTA's shared memory, spread over one
 // cooperative grid: the Gram error from per-CTA partial sums (added in CTA order, so the
@@ -950,6 +1285,56 @@ cudaError_t cholqr_T(const zd* X, int64_t ldx, int m, const double* dscale, zd* 
   const int64_t tot = (int64_t)m * m;
   cholqr_T_kernel<<<(int)std::min<int64_t>(1024, (tot + 255) / 256), 256, 0, s>>>(X, ldx, m, dscale,
                                                                                    T, ldt);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+cudaError_t jacobi_heev_df(const zd* G, int64_t ldg, int m, double* w, zd* V, int64_t ldv, zd* work,
+                           unsigned* barrier, int* status, cudaStream_t s, long long spin_limit) {
+  if (m <= 0) return cudaSuccess;
+  const int mp = (m + 1) & ~1;
+  if (mp < 64) return jacobi_heev(G, ldg, m, w, V, ldv, work, barrier, status, s, spin_limit);
+  JacDfParams P;
+  P.G = G; P.ldg = ldg; P.m = m; P.mp = mp;
+  P.Ga = reinterpret_cast<float4*>(work);
+  P.Gb = reinterpret_cast<float4*>(work + (int64_t)mp * mp);
+  P.Vw = work + 2 * (int64_t)mp * mp;
+  P.bar = barrier;
+  P.status = status;
+  P.max_sweeps = 40;
+  P.spin_limit = spin_limit > 0 ? spin_limit : kBarrierSpinLimit;
+  cudaError_t e = cudaMemsetAsync(barrier, 0, 4 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  const int half = mp / 2;
+  static const cudaError_t attr = cudaFuncSetAttribute(jacobi_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       kJacSmemMax);
+  if (attr != cudaSuccess) return attr;
+  int ppc = 1;
+  size_t smem = 0;
+  for (;; ++ppc) {
+    smem = rotdf_bytes(half) + 2 * sizeof(float4) * (size_t)(ppc + 1) * mp;
+    if (smem > (size_t)kJacSmemMax) return cudaErrorInvalidValue;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_df_kernel, JAC_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if ((int64_t)per_sm * sm_count() >= (half + ppc - 1) / ppc) break;
+  }
+  P.pairs_per_cta = ppc;
+  const int grid = (half + ppc - 1) / ppc;
+  // the rotation tables of both parities and the partial sums live in Vw during the run
+  if (2 * sizeof(RotDF) * (size_t)half + 12 * (size_t)grid > sizeof(zd) * (size_t)mp * mp)
+    return cudaErrorInvalidValue;
+  void* args[] = {(void*)&P};
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_df_kernel, dim3(grid), dim3(JAC_THREADS), args, smem, s);
+  CHFSI_COUNT_LAUNCH();
+  if (e != cudaSuccess) return e;
+  const size_t smem2 = (size_t)m * (sizeof(double) + sizeof(int));
+  if (smem2 > 48 * 1024) {
+    e = cudaFuncSetAttribute(jacobi_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+  }
+  jacobi_finish_kernel<<<1, 1024, smem2, s>>>(reinterpret_cast<const zd*>(P.Ga), reinterpret_cast<const zd*>(P.Gb),
+                                              P.Vw, barrier, m, mp, w, V, ldv);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }

@@ -301,6 +301,28 @@ def test_heev_clustered_spectrum(ctx):
     assert np.max(np.abs(G @ V - V * w[None, :])) < 1e-13
 
 
+@pytest.mark.parametrize("m", [64, 97, 320, 601, 1200])
+def test_heev_double_float_matches_lapack(m):
+    """The double-float Jacobi (the mixed-precision Rayleigh-Ritz solver of wide blocks)
+    against LAPACK: a random Hermitian matrix and a nearly diagonal one.  Its arithmetic
+    carries about 48 significand bits (unit roundoff 2^-47 ~ 7e-15 per operation), so the
+    bounds are those of the FP64 test with u = 2^-47 for 2^-53: 1e-13 -> 5e-12 relative to
+    ||G||_2 sqrt(m), orthogonality 5e-12 sqrt(m)."""
+    rng = _rng(3 * m + 1)
+    G = _herm(rng, m, 2.0)
+    D = np.diag(np.sort(rng.uniform(-2, 2, m))) + 1e-6 * _herm(rng, m)
+    with cb.Solver(m, m) as s:
+        for M in (G, D):
+            w, V = cb.chfsi_heev_df(s.ctx, _t(M))
+            w, V = _np(w), _np(V)
+            w_ref = np.linalg.eigvalsh(M)
+            nrm = np.linalg.norm(M, 2)
+            assert np.max(np.abs(w - w_ref)) < 5e-12 * nrm * math.sqrt(m)
+            assert np.max(np.abs(V.conj().T @ V - np.eye(m))) < 5e-12 * math.sqrt(m)
+            assert np.max(np.abs(M @ V - V * w[None, :])) < 5e-12 * nrm * math.sqrt(m)
+            assert np.all(np.diff(w) >= 0)
+
+
 @pytest.mark.parametrize("m", [601, 700, 1200])
 def test_heev_large_blocks_share_cooperative_ctas(m):
     """Blocks above ~600 columns (the n = 13,400 workload's blk = 1200) run with several
@@ -578,6 +600,31 @@ def test_solve_n9300_mixed_precision_workload():
         lam_d = lam.to(A.device).to(torch.complex128)
         R = A @ X - (B @ X) * lam_d[None, :]
         res = torch.linalg.vector_norm(R, dim=0) / (a_low * torch.linalg.vector_norm(X, dim=0))
+        assert float(res.max()) <= 1e-10, float(res.max())
+        E = X.mH @ (B @ X) - torch.eye(nev, dtype=torch.complex128, device=A.device)
+        assert float(E.abs().max()) < 1e-10
+
+
+def test_solve_wide_blocks_with_double_float_rayleigh_ritz():
+    """The n = 13,400 workload's spectrum and adaptive degrees at n = 3000 with blocks of 400
+    columns (two problems, cold + warm): the Rayleigh-Ritz eigensolver runs in double-float
+    arithmetic from 384 columns; eigenvalues against the planted spectrum, generalized
+    residuals and B-orthonormality at the solver's FP64 bar."""
+    seq = inputs.planted_sequence("c5", n=3000, N=2, nev=300, blk=400, device="cuda", keep_vectors=False)
+    n, nev, blk = seq.n, seq.nev, seq.blk
+    As = [cb.fortran(torch.tril(p.A)) for p in seq.problems]
+    Bs = [cb.fortran(torch.tril(p.B)) for p in seq.problems]
+    with cb.Solver(n, blk, deg_min=seq.deg_min, deg_max=seq.deg_max) as s:
+        evals, evecs, stats = cb.chfsi_solve_sequence(s.ctx, As, Bs, nev, blk, seq.deg, seq.tol)
+    scale = max(float(np.max(np.abs(p.lam))) for p in seq.problems)
+    for ell, p in enumerate(seq.problems):
+        lam = evals[ell]
+        assert stats[ell]["converged"] == nev
+        assert np.max(np.abs(lam.numpy() - p.lam[:nev])) <= 1e-10 * scale
+        A, B, X = p.A, p.B, evecs[ell]
+        lam_d = lam.to(A.device).to(torch.complex128)
+        R = A @ X - (B @ X) * lam_d[None, :]
+        res = torch.linalg.vector_norm(R, dim=0) / (scale * torch.linalg.vector_norm(X, dim=0))
         assert float(res.max()) <= 1e-10, float(res.max())
         E = X.mH @ (B @ X) - torch.eye(nev, dtype=torch.complex128, device=A.device)
         assert float(E.abs().max()) < 1e-10

@@ -1306,14 +1306,26 @@ cudaError_t jacobi_heev_df(const zd* G, int64_t ldg, int m, double* w, zd* V, in
   cudaError_t e = cudaMemsetAsync(barrier, 0, 4 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   const int half = mp / 2;
-  static const cudaError_t attr = cudaFuncSetAttribute(jacobi_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       kJacSmemMax);
+  // dynamic shared memory: the opt-in limit per block less the kernel's static arrays
+  static int dyn_max = -1;
+  static cudaError_t attr = cudaSuccess;
+  if (dyn_max < 0) {
+    cudaFuncAttributes fa;
+    int dev = 0, optin = 0;
+    attr = cudaFuncGetAttributes(&fa, jacobi_df_kernel);
+    if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
+    if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int lim = std::min(kJacSmemMax, optin - (int)fa.sharedSizeBytes);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(jacobi_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    dyn_max = lim;
+  }
   if (attr != cudaSuccess) return attr;
   int ppc = 1;
   size_t smem = 0;
   for (;; ++ppc) {
     smem = rotdf_bytes(half) + 2 * sizeof(float4) * (size_t)(ppc + 1) * mp;
-    if (smem > (size_t)kJacSmemMax) return cudaErrorInvalidValue;
+    if (smem > (size_t)dyn_max) return cudaErrorInvalidValue;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_df_kernel, JAC_THREADS, smem);
     if (e != cudaSuccess) return e;

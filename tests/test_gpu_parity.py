@@ -206,16 +206,21 @@ def test_orthonormalize_matches_oracle_span(ctx, ctx64, n, m, k, mode):
 def test_orthonormalize_wide_blocks_match_oracle_span(n, m, k):
     """Blocks wider than one CTA's shared memory: the FP32 Cholesky QR steps run as one
     cooperative grid (blocked factorisation, 32-column panels; a ragged last panel at
-    m = 161, 400 and 1200 = 37.5 panels)."""
+    m = 161, 400 and 1200 = 37.5 panels).  The orthogonality bound of the narrow test
+    (1e-13 up to 160 columns) grows with the width like the rounding of the last step's
+    7-slice product Y T: each entry of Y T carries a relative error of about 2^-49 of its
+    scales, and an entry of (Y T)^H (Y T) sums m such products, so the bound is scaled by
+    sqrt(m / 160)."""
     rng = _rng(7 * n + m + k)
     YL = np.linalg.qr(_cgauss(rng, n, k))[0] if k else None
     Y = _cgauss(rng, n, m) * np.logspace(0, -6, m)[None, :]
     with cb.Solver(n, m) as s:
         got = _np(cb.chfsi_orthonormalize(s.ctx, _t(Y), _t(YL) if k else None))
     ref = O.orthonormalize(Y, YL)
-    assert np.max(np.abs(got.conj().T @ got - np.eye(m))) < 1e-13
+    bound = 1e-13 * max(1.0, math.sqrt(m / 160))
+    assert np.max(np.abs(got.conj().T @ got - np.eye(m))) < bound
     if k:
-        assert np.max(np.abs(YL.conj().T @ got)) < 1e-13
+        assert np.max(np.abs(YL.conj().T @ got)) < bound
     assert np.linalg.norm(got @ got.conj().T - ref @ ref.conj().T) < 1e-9
 
 

@@ -383,8 +383,9 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": (sum(s["filter_slice_bytes"] for s in all_stats)
                                                      / products) if products else None,
                     "peak_note": f"bf16 dense sustained ({peak_kind}); achieved counts the "
-                                 "slice-pair products (2 x pairs x 2n x m x 2n flops each, "
-                                 "unpadded) over the product kernel's CUDA-event time"}
+                                 "slice-pair products the kernel issues (Gauss form: three real "
+                                 "products of 2 x pairs x n x m x n flops; real embedding: 2 x pairs "
+                                 "x 2n x m x 2n; unpadded) over the product kernel's CUDA-event time"}
     else:
         fp64_peak = peaks["bf16_tflops_sustained"] * 1.25 / 2250.0
         achieved = fp64_equiv / (g_ms / 1e3) / 1e12 if g_ms > 0 else None

@@ -437,9 +437,13 @@ int filter_block(chfsi_ctx* ctx, const zd* H, int64_t ldh, int n, int m, zd** Ya
       CK(oz_filter_product(cur, ld, n, mk, slices, al, be, cur, ld, k >= 2 ? ga : 0.0, out, ld, out,
                            ld, ws.oz, ctx->stream, gb, ge));
       if (st) {
-        st->tensor_flops += 2.0 * (double)oz_pair_count(slices) * (2.0 * n) * (double)mk * (2.0 * n);
+        // slice-pair flops the kernel issues: the 2n x 2n real embedding, or the Gauss form's
+        // three real n x n products
+        const double pairs = (double)oz_pair_count(slices);
+        st->tensor_flops += ws.oz.H.nz == 3 ? 3.0 * 2.0 * pairs * n * (double)mk * n
+                                            : 2.0 * pairs * (2.0 * n) * (double)mk * (2.0 * n);
         st->filter_products += 1;
-        st->filter_slice_bytes += 2.0 * (double)slices * ws.oz.H.Mp * (double)ws.oz.H.Kp;
+        st->filter_slice_bytes += 2.0 * (double)slices * ws.oz.H.nz * ws.oz.H.Mp * (double)ws.oz.H.Kp;
       }
     } else {
       GemmDesc g = gd(n, mk, n, H, ldh, OPN, cur, ld, OPN, out, ld, al);

@@ -199,6 +199,7 @@ struct OzA {                        // A operand: S digit slices of op(A) (M x K
   int S = 0, M = 0, K = 0, Mp = 0, Kp = 0;
   int64_t slice = 0;
   int S_max = 0, Mp_max = 0, Kp_max = 0;
+  int nz = 1;                       // 1: real embedding; 3: Gauss form (Hr, Hi, Hr + Hi)
 };
 struct OzB {                        // B operand: S digit slices of op(B) (K x N complex)
   struct __nv_bfloat16* ptr = nullptr;
@@ -206,6 +207,7 @@ struct OzB {                        // B operand: S digit slices of op(B) (K x N
   int S = 0, N = 0, Np = 0, Kp = 0;
   int64_t slice = 0;
   int S_max = 0, Np_max = 0, Kp_max = 0;
+  int nz = 1;                       // 1: real embedding; 3: Gauss form (Yr, Yi, Yr + Yi)
 };
 struct OzWorkspace {
   OzA H;                            // slices of the problem's Hs (kept for the whole solve)

@@ -320,6 +320,11 @@ struct TcParams {
   int cl;                                    // CTAs per cluster along M sharing the B tiles (1, 2, 4)
   int tiles_m_pad;                           // tiles_m rounded up to a multiple of cl
   int col_major_order;                       // 1: blockIdx.x runs over column tiles first (cl == 1)
+  // Gauss form (nz = 3): blockIdx.z picks one of three real products whose operands follow
+  // each other in the slice buffers (a_zrows rows of A, b_zrows rows of B apart) and whose
+  // split partials follow each other in part (splits x Mp x Np entries apart)
+  int nz;
+  int a_zrows, b_zrows;
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -544,7 +549,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int k0 = kb_lo; k0 < kb_hi && !stop; k0 += OZ_CHUNK_KB) {
         const int k1 = min(kb_hi, k0 + OZ_CHUNK_KB);
         for (int pr = pr_lo; pr < pr_hi && !stop; ++pr) {
-          const int arow = p.gs[pr] * p.Mp + m0, brow = p.gt[pr] * p.Np + n0;
+          const int arow = (int)blockIdx.z * p.a_zrows + p.gs[pr] * p.Mp + m0;
+          const int brow = (int)blockIdx.z * p.b_zrows + p.gt[pr] * p.Np + n0;
           for (int kb = k0; kb < k1; ++kb, ++i) {
             const uint32_t fb = full0 + 8 * stage;
             if (i >= NS && !mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag, p.status, p.spin_limit)) {
@@ -730,7 +736,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (ok && !*abort_flag && m0 < p.Mp) {
       // partial sums of this split as (hi, lo) pairs: P[split][col * Mp + row]
-      float2* P = reinterpret_cast<float2*>(p.part) + (int64_t)blockIdx.y * p.Mp * p.Np;
+      float2* P = reinterpret_cast<float2*>(p.part) +
+                  ((int64_t)blockIdx.z * p.splits + blockIdx.y) * p.Mp * p.Np;
       const int row = m0 + quarter * 32 + lane;
 #pragma unroll
       for (int c = 0; c < kBlocks; ++c) {
@@ -991,6 +998,108 @@ __global__ void oz_slice_cols_kernel(const zd* Y, int64_t ldy, int n, int m, int
   }
 }
 
+// Gauss form of the complex product (three real products instead of the 2n x 2n real
+// embedding): Hs Y = (Hr Yr - Hi Yi) + i ((Hr + Hi)(Yr + Yi) - Hr Yr - Hi Yi).  Operand z of
+// A is Hr, Hi, Hr + Hi (z = 0, 1, 2) with its own power-of-two scale per row, operand z of B
+// is Yr, Yi, Yr + Yi with its own scale per column; slices [z][s][row][k], scales [z][row].
+// The sums Hr + Hi and Yr + Yi are formed in FP64 (one rounding) before the digits are taken.
+// Rows of A: row i of H = conj(column i of Hs) (Hs Hermitian), read contiguously.
+__global__ void oz_slice_hermitian3_kernel(const zd* Hs, int64_t ldh, int n, int S, __nv_bfloat16* A,
+                                           int64_t sliceA, int64_t zstride, int Kp, int Mp, int* eA) {
+  const int i = blockIdx.x;
+  const zd* col = Hs + (int64_t)i * ldh;
+  unsigned long long m0 = 0ull, m1 = 0ull, m2 = 0ull;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const zd h = col[k];
+    const double hr = h.x, hi = -h.y, hs = hr + hi;
+    const unsigned long long a = abs_bits(hr), b = abs_bits(hi), c = abs_bits(hs);
+    m0 = a > m0 ? a : m0;
+    m1 = b > m1 ? b : m1;
+    m2 = c > m2 ? c : m2;
+  }
+  const int e0 = exponent_from_bits(block_max_bits(m0));
+  const int e1 = exponent_from_bits(block_max_bits(m1));
+  const int e2 = exponent_from_bits(block_max_bits(m2));
+  if (threadIdx.x == 0) {
+    eA[i] = e0;
+    eA[Mp + i] = e1;
+    eA[2 * Mp + i] = e2;
+  }
+  __nv_bfloat16* r0 = A + (int64_t)i * Kp;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const zd h = col[k];
+    const double hr = h.x, hi = -h.y;
+    digits(hr, e0, S, r0 + k, sliceA);
+    digits(hi, e1, S, r0 + zstride + k, sliceA);
+    digits(hr + hi, e2, S, r0 + 2 * zstride + k, sliceA);
+  }
+}
+
+// Columns of B in the Gauss form: column j of Y gives rows j of Yr, Yi, Yr + Yi; columns
+// j >= m of the padded block are zero (the buffer is cleared first).
+__global__ void oz_slice_cols3_kernel(const zd* Y, int64_t ldy, int n, int m, int S, __nv_bfloat16* B,
+                                      int64_t sliceB, int64_t zstride, int Kp, int Np, int* eB) {
+  const int j = blockIdx.x;
+  if (j >= m) {
+    if (threadIdx.x == 0) eB[j] = eB[Np + j] = eB[2 * Np + j] = 0;
+    return;
+  }
+  const zd* y = Y + (int64_t)j * ldy;
+  unsigned long long m0 = 0ull, m1 = 0ull, m2 = 0ull;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const zd v = y[k];
+    const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y), c = abs_bits(v.x + v.y);
+    m0 = a > m0 ? a : m0;
+    m1 = b > m1 ? b : m1;
+    m2 = c > m2 ? c : m2;
+  }
+  const int e0 = exponent_from_bits(block_max_bits(m0));
+  const int e1 = exponent_from_bits(block_max_bits(m1));
+  const int e2 = exponent_from_bits(block_max_bits(m2));
+  if (threadIdx.x == 0) {
+    eB[j] = e0;
+    eB[Np + j] = e1;
+    eB[2 * Np + j] = e2;
+  }
+  __nv_bfloat16* c0 = B + (int64_t)j * Kp;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const zd v = y[k];
+    digits(v.x, e0, S, c0 + k, sliceB);
+    digits(v.y, e1, S, c0 + zstride + k, sliceB);
+    digits(v.x + v.y, e2, S, c0 + 2 * zstride + k, sliceB);
+  }
+}
+
+// out = alpha (P0 - P1 + i (P2 - P0 - P1)) + beta Cin + gamma D from the split partials of
+// the three real products (double-float pairs, slice scales applied), each scaled by its row
+// and column exponents.
+__global__ void oz_epilogue3_kernel(const float2* part, int splits, int Mp, int Np, const int* eA,
+                                    const int* eB, int n, int m, double alpha, double beta,
+                                    const zd* Cin, int64_t ldcin, double gamma, const zd* D,
+                                    int64_t ldd, zd* out, int64_t ldo) {
+  const int64_t total = (int64_t)n * m;
+  const int64_t zst = (int64_t)splits * Mp * Np;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    double v[3];
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+      float h = 0.f, l = 0.f;
+      for (int sp = 0; sp < splits; ++sp) {
+        const float2 q = part[z * zst + (int64_t)sp * Mp * Np + (int64_t)j * Mp + i];
+        two_sum_acc(h, l, q.x);
+        l += q.y;
+      }
+      v[z] = ldexp((double)h + (double)l, eA[z * Mp + i] + eB[z * Np + j]);
+    }
+    zd o = zmk(alpha * (v[0] - v[1]), alpha * (v[2] - v[0] - v[1]));
+    if (beta != 0.0) o = zadd(o, zscale(Cin[i + (int64_t)j * ldcin], beta));
+    if (gamma != 0.0) o = zadd(o, zscale(D[i + (int64_t)j * ldd], gamma));
+    out[i + (int64_t)j * ldo] = o;
+  }
+}
+
 int choose_oz_splits(int tiles, int total_kb, size_t cap_elems, int64_t tile_elems) {
   const int sms = sm_count();
   int best = 1;
@@ -1046,12 +1155,12 @@ int choose_tc_splits(int tiles, int nkb, int npairs, size_t cap_elems, int64_t t
 // product shape, shared by all contexts of the process (batch workers tune from several host
 // threads).  Environment variable CHFSI_OZ_AUTOTUNE=0 keeps the wave model's choice.
 struct TuneKey {
-  int Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups, b_tri;
+  int Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups, b_tri, nz;
   bool operator<(const TuneKey& o) const {
-    const int a[11] = {Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups, b_tri};
-    const int b[11] = {o.Mp, o.Np, o.Kp, o.S, o.a_lower, o.c_lower, o.group, o.b_box_rows, o.cl, o.ngroups,
-                       o.b_tri};
-    return std::lexicographical_compare(a, a + 11, b, b + 11);
+    const int a[12] = {Mp, Np, Kp, S, a_lower, c_lower, group, b_box_rows, cl, ngroups, b_tri, nz};
+    const int b[12] = {o.Mp, o.Np, o.Kp, o.S, o.a_lower, o.c_lower, o.group, o.b_box_rows, o.cl, o.ngroups,
+                       o.b_tri, o.nz};
+    return std::lexicographical_compare(a, a + 12, b, b + 12);
   }
 };
 static std::mutex g_tune_mu;
@@ -1182,7 +1291,7 @@ cudaError_t oz_slice_a(OzA& a, int op, const zd* X, int64_t ldx, int M, int K, i
   const int Kp = oz_padded_k(K), Mp = oz_padded_m(M);
   if (S > a.S_max || S < 1 || Kp > a.Kp_max || Mp > a.Mp_max || M <= 0 || K <= 0)
     return cudaErrorInvalidValue;
-  a.S = S; a.M = M; a.K = K; a.Mp = Mp; a.Kp = Kp;
+  a.S = S; a.M = M; a.K = K; a.Mp = Mp; a.Kp = Kp; a.nz = 1;
   a.slice = (int64_t)Mp * Kp;
   // zero the padding (rows >= 2M, columns >= 2K)
   cudaError_t e = cudaMemsetAsync(a.ptr, 0, sizeof(__nv_bfloat16) * (size_t)S * a.slice, s);
@@ -1201,7 +1310,7 @@ cudaError_t oz_slice_b(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, i
                        cudaStream_t s, int lower_half) {
   const int Np = oz_padded_n(N);
   if (Np > b.Np_max || Kp > b.Kp_max || S > b.S_max || S < 1 || N <= 0) return cudaErrorInvalidValue;
-  b.S = S; b.N = N; b.Np = Np; b.Kp = Kp;
+  b.S = S; b.N = N; b.Np = Np; b.Kp = Kp; b.nz = 1;
   b.slice = (int64_t)Np * Kp;
   cudaError_t e = cudaMemsetAsync(b.ptr, 0, sizeof(__nv_bfloat16) * (size_t)S * b.slice, s);
   if (e != cudaSuccess) return e;
@@ -1224,7 +1333,9 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
                        cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end, int b_tri) {
   const int n = a.M, m = b.N, Kp = a.Kp, Mp = a.Mp, Np = b.Np;
   if (m <= 0 || n <= 0) return cudaSuccess;
-  if (S > b.S || S > a.S || S < 1 || a.Kp != b.Kp) return cudaErrorInvalidValue;
+  if (S > b.S || S > a.S || S < 1 || a.Kp != b.Kp || a.nz != b.nz) return cudaErrorInvalidValue;
+  const int nz = a.nz;  // 3: Gauss form (tcgen05 path, general products only)
+  if (nz != 1 && (nz != 3 || !oz_use_tcgen05() || a_lower || c_lower || b_tri)) return cudaErrorInvalidValue;
   cudaError_t e;
   // Pairs (s, t) with s + t <= S + 1, grouped by the A slice s so that consecutive pairs
   // stream the same slice of the large operand (it stays in L2 between them).
@@ -1249,6 +1360,9 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     tp.n_real = m;
     tp.part = oz.part;
     tp.status = oz.status;
+    tp.nz = nz;
+    tp.a_zrows = nz > 1 ? a.S * Mp : 0;
+    tp.b_zrows = nz > 1 ? b.S * Np : 0;
     // first-level waits: the context's bound (a test hook) or the default; the waits that
     // let issued copies and MMAs finish after an abort always use the default
     tp.spin_limit = oz.wait_limit > 0 ? oz.wait_limit : kMbarSpinLimit;
@@ -1293,11 +1407,12 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     tp.col_major_order = (tp.cl == 1 && oz_col_major_order()) ? 1 : 0;
     const int tiles = tp.tiles_m_pad * ((Np + TC_BN - 1) / TC_BN);
     int model_pair_split = 0;
+    const size_t part_cap = oz.part_elems / (size_t)nz;  // partials of each of the nz products
     const int model_splits =
-        choose_tc_splits(tiles, tp.nkb, tp.ngroups, oz.part_elems, (int64_t)Mp * Np, &model_pair_split);
-    const uint64_t b_rows = std::max<uint64_t>((uint64_t)b.S * Np, (uint64_t)TC_BN);
+        choose_tc_splits(tiles, tp.nkb, tp.ngroups, part_cap, (int64_t)Mp * Np, &model_pair_split);
+    const uint64_t b_rows = std::max<uint64_t>((uint64_t)nz * b.S * Np, (uint64_t)TC_BN);
     if ((int64_t)b_rows * Kp > (int64_t)b.S_max * b.Np_max * b.Kp_max) return cudaErrorInvalidValue;
-    if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)a.S * Mp, TC_BM) ||
+    if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)nz * a.S * Mp, TC_BM) ||
         !encode_bf16_map(&mapB, b.ptr, Kp, b_rows, tp.b_box_rows / tp.cl))
       return cudaErrorInvalidValue;
     const int b_stage = tp.b_box_rows * TC_BK * 2;
@@ -1312,7 +1427,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
       tp.pair_split = ps;
       if (tp.cl > 1) {
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(tiles, sp);
+        cfg.gridDim = dim3(tiles, sp, nz);
         cfg.blockDim = dim3(TC_THREADS);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = s;
@@ -1326,7 +1441,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
         cudaError_t le = cudaLaunchKernelEx(&cfg, oz_gemm_tc_kernel, mapA, mapB, tp);
         if (le != cudaSuccess) return le;
       } else {
-        oz_gemm_tc_kernel<<<dim3(tiles, sp), TC_THREADS, smem, s>>>(mapA, mapB, tp);
+        oz_gemm_tc_kernel<<<dim3(tiles, sp, nz), TC_THREADS, smem, s>>>(mapA, mapB, tp);
       }
       CHFSI_COUNT_LAUNCH();
       return cudaGetLastError();
@@ -1334,7 +1449,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     // split count: the wave model's choice, or the fastest of a few candidates around it,
     // measured on the first product of each shape and kept for the process (autotuner)
     int best_splits = model_splits, best_ps = model_pair_split;
-    const TuneKey key{Mp, Np, Kp, S, a_lower, c_lower, tp.group, tp.b_box_rows, tp.cl, tp.ngroups, b_tri};
+    const TuneKey key{Mp, Np, Kp, S, a_lower, c_lower, tp.group, tp.b_box_rows, tp.cl, tp.ngroups, b_tri, nz};
     if (oz_autotune() && !tune_lookup(key, &best_splits, &best_ps)) {
       cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
       if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
@@ -1342,7 +1457,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
         const int limit_k = model_pair_split ? tp.ngroups : std::min(tp.nkb, 64);
         for (int num : {2, 3, 4, 6, 8}) {  // model x {1/2, 3/4, 1, 3/2, 2}
           const int sp = std::max(1, std::min(limit_k, (model_splits * num + 2) / 4));
-          if ((size_t)sp * (size_t)((int64_t)Mp * Np) > oz.part_elems) continue;
+          if ((size_t)sp * (size_t)((int64_t)Mp * Np) > part_cap) continue;
           if (model_pair_split) {
             const int pp = (tp.ngroups + sp - 1) / sp;   // groups per split: the grid uses ceil
             const int eff = (tp.ngroups + pp - 1) / pp;
@@ -1406,9 +1521,53 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
   }
   const int64_t tot = (int64_t)n * m;
   const int blocks = (int)std::min<int64_t>(4 * sm_count(), (tot + 255) / 256);
-  oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, a.e, b.e, n, m, alpha, beta, Cin,
-                                            ldcin, gamma, D, ldd, out, ldo, c_lower,
-                                            oz_use_tcgen05() ? 1 : 0);
+  if (nz == 3)
+    oz_epilogue3_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float2*>(oz.part), splits, Mp, Np, a.e,
+                                               b.e, n, m, alpha, beta, Cin, ldcin, gamma, D, ldd, out, ldo);
+  else
+    oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, a.e, b.e, n, m, alpha, beta, Cin,
+                                              ldcin, gamma, D, ldd, out, ldo, c_lower,
+                                              oz_use_tcgen05() ? 1 : 0);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// Gauss form of the filter's product (three real products, section "Gauss form" above):
+// environment variable CHFSI_OZ_GAUSS (0 keeps the real embedding; default on with tcgen05).
+static bool oz_gauss() {
+  static const bool v = [] {
+    const char* e = std::getenv("CHFSI_OZ_GAUSS");
+    return !(e && std::atoi(e) == 0);
+  }();
+  return v && oz_use_tcgen05();
+}
+
+// Hs (n x n Hermitian) as the Gauss-form A operand: slices of Hr, Hi, Hr + Hi of H = Hs.
+static cudaError_t oz_slice_a3(OzA& a, const zd* Hs, int64_t ldh, int n, int S, cudaStream_t s) {
+  const int Mp = ((n + TC_BM - 1) / TC_BM) * TC_BM, Kp = ((n + OZ_BK - 1) / OZ_BK) * OZ_BK;
+  if (S > a.S_max || S < 1 || n <= 0 || (int64_t)3 * Mp * Kp > (int64_t)a.Mp_max * a.Kp_max ||
+      3 * Mp > 3 * a.Mp_max)
+    return cudaErrorInvalidValue;
+  a.S = S; a.M = n; a.K = n; a.Mp = Mp; a.Kp = Kp; a.nz = 3;
+  a.slice = (int64_t)Mp * Kp;
+  cudaError_t e = cudaMemsetAsync(a.ptr, 0, sizeof(__nv_bfloat16) * (size_t)3 * S * a.slice, s);
+  if (e != cudaSuccess) return e;
+  oz_slice_hermitian3_kernel<<<n, 256, 0, s>>>(Hs, ldh, n, S, a.ptr, a.slice, (int64_t)S * a.slice, Kp, Mp, a.e);
+  CHFSI_COUNT_LAUNCH();
+  return cudaGetLastError();
+}
+
+// Y (K x N) as the Gauss-form B operand (Yr, Yi, Yr + Yi), K-padding as the A operand's.
+static cudaError_t oz_slice_b3(OzB& b, const zd* Y, int64_t ldy, int K, int N, int S, int Kp, cudaStream_t s) {
+  const int Np = oz_padded_n(N);
+  if (S > b.S_max || S < 1 || N <= 0 || 3 * Np > 3 * b.Np_max ||
+      (int64_t)3 * S * std::max(Np, TC_BN) * Kp > (int64_t)b.S_max * b.Np_max * b.Kp_max)
+    return cudaErrorInvalidValue;
+  b.S = S; b.N = N; b.Np = Np; b.Kp = Kp; b.nz = 3;
+  b.slice = (int64_t)Np * Kp;
+  cudaError_t e = cudaMemsetAsync(b.ptr, 0, sizeof(__nv_bfloat16) * (size_t)3 * S * b.slice, s);
+  if (e != cudaSuccess) return e;
+  oz_slice_cols3_kernel<<<Np, 256, 0, s>>>(Y, ldy, K, N, S, b.ptr, b.slice, (int64_t)S * b.slice, Kp, Np, b.e);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -1416,6 +1575,8 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
 // ---- the Hermitian matrix of the filter (its slices stay in oz.H for the whole problem)
 cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
                                cudaStream_t s) {
+  if (oz_gauss()) return oz_slice_a3(oz.H, Hs, ldh, n, S, s);
+  oz.H.nz = 1;
   return oz_slice_a(oz.H, OPC, Hs, ldh, n, n, S, s);
 }
 
@@ -1427,7 +1588,8 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
                               cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end) {
   if (m <= 0) return cudaSuccess;
   if (S > oz.H.S || S < 1 || oz.H.M != n) return cudaErrorInvalidValue;
-  cudaError_t e = oz_slice_b(oz.B, OPN, Y, ldy, n, m, S, oz.H.Kp, s);
+  cudaError_t e = oz.H.nz == 3 ? oz_slice_b3(oz.B, Y, ldy, n, m, S, oz.H.Kp, s)
+                               : oz_slice_b(oz.B, OPN, Y, ldy, n, m, S, oz.H.Kp, s);
   if (e != cudaSuccess) return e;
   return oz_product(oz.H, oz.B, S, alpha, beta, Cin, ldcin, gamma, D, ldd, out, ldo, 0, 0, oz, s,
                     ev_gemm_begin, ev_gemm_end);
@@ -1455,7 +1617,7 @@ static cudaError_t alloc_a(OzA& a, int n_max, int S_max) {
   a.Mp_max = oz_padded_m(n_max);
   cudaError_t e = cudaMalloc((void**)&a.ptr, sizeof(__nv_bfloat16) * (size_t)S_max * a.Mp_max * a.Kp_max);
   if (e != cudaSuccess) return e;
-  return cudaMalloc((void**)&a.e, sizeof(int) * (size_t)a.Mp_max);
+  return cudaMalloc((void**)&a.e, sizeof(int) * (size_t)3 * a.Mp_max);  // 3 scale sets (Gauss form)
 }
 
 cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max) {
@@ -1471,7 +1633,7 @@ cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max) {
   oz.B.Np_max = ((std::max(cols, TC_BN) + OZ_BN - 1) / OZ_BN) * OZ_BN;
   e = cudaMalloc((void**)&oz.B.ptr, sizeof(__nv_bfloat16) * (size_t)S_max * oz.B.Np_max * oz.B.Kp_max);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc((void**)&oz.B.e, sizeof(int) * (size_t)oz.B.Np_max);
+  e = cudaMalloc((void**)&oz.B.e, sizeof(int) * (size_t)3 * oz.B.Np_max);
   if (e != cudaSuccess) return e;
   const int np_blk = ((blk_max + OZ_BN - 1) / OZ_BN) * OZ_BN;
   const size_t mp = (size_t)oz_padded_m(n_max);

@@ -680,6 +680,10 @@ __device__ __forceinline__ float4 dfc_comb(float2 a, float4 x, float2 b, float4 
 }
 __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
+// 512 threads: the double-float updates are chains of dependent FP32 operations, and one
+// CTA per SM (its shared memory) needs 16 warps to keep the FP32 pipes busy.
+constexpr int JAC_DF_THREADS = 512;
+
 struct JacDfParams {
   const zd* G;
   int64_t ldg;
@@ -694,14 +698,14 @@ struct JacDfParams {
   int pairs_per_cta;
 };
 
-__global__ void __launch_bounds__(JAC_THREADS) jacobi_df_kernel(const JacDfParams P) {
+__global__ void __launch_bounds__(JAC_DF_THREADS, 1) jacobi_df_kernel(const JacDfParams P) {
   extern __shared__ unsigned char smem_raw[];
   const int mp = P.mp, half = mp / 2, ppc = P.pairs_per_cta;
   RotDF* rot = reinterpret_cast<RotDF*>(smem_raw);
   float4* vrow = reinterpret_cast<float4*>(smem_raw + rotdf_bytes(half));  // 2 ppc x mp
   float4* col = vrow + (size_t)2 * ppc * mp;                                          // 2 x mp
-  __shared__ double red[JAC_THREADS];
-  __shared__ float redf[JAC_THREADS];
+  __shared__ double red[JAC_DF_THREADS];
+  __shared__ float redf[JAC_DF_THREADS];
   const int tid = threadIdx.x, nt = blockDim.x;
   const unsigned nb = gridDim.x;
   const int cta = blockIdx.x;
@@ -1327,7 +1331,7 @@ cudaError_t jacobi_heev_df(const zd* G, int64_t ldg, int m, double* w, zd* V, in
     smem = rotdf_bytes(half) + 2 * sizeof(float4) * (size_t)(ppc + 1) * mp;
     if (smem > (size_t)dyn_max) return cudaErrorInvalidValue;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_df_kernel, JAC_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_df_kernel, JAC_DF_THREADS, smem);
     if (e != cudaSuccess) return e;
     if ((int64_t)per_sm * sm_count() >= (half + ppc - 1) / ppc) break;
   }
@@ -1337,7 +1341,7 @@ cudaError_t jacobi_heev_df(const zd* G, int64_t ldg, int m, double* w, zd* V, in
   if (2 * sizeof(RotDF) * (size_t)half + 12 * (size_t)grid > sizeof(zd) * (size_t)mp * mp)
     return cudaErrorInvalidValue;
   void* args[] = {(void*)&P};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_df_kernel, dim3(grid), dim3(JAC_THREADS), args, smem, s);
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_df_kernel, dim3(grid), dim3(JAC_DF_THREADS), args, smem, s);
   CHFSI_COUNT_LAUNCH();
   if (e != cudaSuccess) return e;
   const size_t smem2 = (size_t)m * (sizeof(double) + sizeof(int));

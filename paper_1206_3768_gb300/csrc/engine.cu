@@ -193,7 +193,7 @@ int gemm_auto(chfsi_ctx* ctx, const GemmDesc& g) {
   if (ctx->opts.precision == 1 && work >= 16777216.0 && square_c) {
     CK(oz_gemm(g.opA, g.A, g.lda, g.opB, g.B, g.ldb, g.M, g.N, g.K, kGemmSlices, g.alpha, g.beta, g.Cin,
                g.ldcin, g.gamma, g.D, g.ldd, g.C, g.ldc, g.triA == 1, g.lowerC, ctx->ws.oz,
-               ctx->stream));
+               ctx->stream, g.triB));
     return CHFSI_OK;
   }
   return gemm(ctx, g);
@@ -201,14 +201,14 @@ int gemm_auto(chfsi_ctx* ctx, const GemmDesc& g) {
 
 // A product of the factorisation of B and of its inverse (blocked Cholesky and triangular
 // inverse): in mixed mode the large ones run as 8-slice digit products (error about 2^-56 of
-// the operands' row and column scales, below the FP64 GEMM bound; a triangular right operand
-// is used with its stored zeros), the rest in FP64.
+// the operands' row and column scales, below the FP64 GEMM bound; the zero k-blocks of a
+// triangular left or right operand are skipped), the rest in FP64.
 int gemm_factor(chfsi_ctx* ctx, const GemmDesc& g) {
   const double work = (double)g.M * g.N * g.K;
   const bool square_c = !g.lowerC || g.M == g.N;
   if (ctx->opts.precision == 1 && work >= 16777216.0 && square_c) {
     CK(oz_gemm(g.opA, g.A, g.lda, g.opB, g.B, g.ldb, g.M, g.N, g.K, 8, g.alpha, g.beta, g.Cin, g.ldcin,
-               g.gamma, g.D, g.ldd, g.C, g.ldc, g.triA == 1, g.lowerC, ctx->ws.oz, ctx->stream));
+               g.gamma, g.D, g.ldd, g.C, g.ldc, g.triA == 1, g.lowerC, ctx->ws.oz, ctx->stream, g.triB));
     return CHFSI_OK;
   }
   return gemm(ctx, g);
@@ -232,9 +232,19 @@ constexpr int NB = 128;  // panel width of the blocked factorisations
 // relative to the row and column scales, four orders of magnitude below the 1e-10 bar.
 constexpr int kProductSlices = 7;
 
-// In-place blocked right-looking Cholesky on the lower triangle of L (n x n).
+// Restores the workspace's Gauss-form permission on leaving a scope that changed it.
+struct GaussScope {
+  OzWorkspace& oz;
+  int saved;
+  GaussScope(OzWorkspace& o, int allow) : oz(o), saved(o.gauss) { oz.gauss = allow; }
+  ~GaussScope() { oz.gauss = saved; }
+};
+
+// In-place blocked right-looking Cholesky on the lower triangle of L (n x n).  Its digit
+// products keep the real embedding (the factor's errors reach every later step).
 int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n, int nb = NB) {
   Workspace& ws = ctx->ws;
+  GaussScope gs(ws.oz, 0);
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
     zd* L11 = L + k0 + (int64_t)k0 * ld;
@@ -264,6 +274,7 @@ int blocked_cholesky(chfsi_ctx* ctx, zd* L, int64_t ld, int n, int nb = NB) {
 // X[I, 0:I] = -X_II (L[I, 0:I] X[0:I, 0:I]).
 int blocked_trinv(chfsi_ctx* ctx, const zd* L, int64_t ld, zd* X, int64_t ldx, int n, int nb = NB) {
   Workspace& ws = ctx->ws;
+  GaussScope gs(ws.oz, 0);  // the embedding, as in blocked_cholesky
   CK(cudaMemset2DAsync(X, ldx * sizeof(zd), 0, n * sizeof(zd), n, ctx->stream));
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
@@ -683,6 +694,10 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       double piv[2];
       CKS(read_back(ctx, piv, ws.scal + 12, 2));
       ctx->factor_cond_lb = piv[1] > 0.0 ? piv[0] / piv[1] : INFINITY;
+      // Gauss form of the problem's complex products only for a well-conditioned B (pivots
+      // within a factor 100): with cond(B) ~ 1e4 the filter needs accuracy at the edge of 7
+      // slices, and the Gauss form's error bound is three times the embedding's
+      ws.oz.gauss = ctx->factor_cond_lb < 100.0 ? 1 : 0;
       CKS(blocked_trinv(ctx, ws.Lf, ld, ws.Linv, ld, n));
       ctx->has_factor = true;
       ctx->factor_n = n;

@@ -207,6 +207,7 @@ struct OzB {                        // B operand: S digit slices of op(B) (K x N
   int S = 0, N = 0, Np = 0, Kp = 0;
   int64_t slice = 0;
   int S_max = 0, Np_max = 0, Kp_max = 0;
+  int64_t elems = 0;                // bf16 entries allocated
   int nz = 1;                       // 1: real embedding; 3: Gauss form (Yr, Yi, Yr + Yi)
 };
 struct OzWorkspace {
@@ -217,6 +218,7 @@ struct OzWorkspace {
   size_t part_elems = 0;
   int* status = nullptr;            // device status word for bounded-wait timeouts
   long long wait_limit = 0;         // polls of a first-level mbarrier wait (0: the default)
+  int gauss = 1;                    // the Gauss form is allowed for the current products
 };
 bool oz_use_tcgen05();
 int oz_padded_k(int n);

@@ -325,6 +325,7 @@ struct TcParams {
   // split partials follow each other in part (splits x Mp x Np entries apart)
   int nz;
   int a_zrows, b_zrows;
+  int kfac;  // real k (and rows of A) per complex index: 2 in the embedding, 1 in the Gauss form
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -480,18 +481,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int crank = p.cl > 1 ? (int)cluster_ctarank() : 0;
   const int m0_last = (tm - crank + p.cl - 1) * TC_BM;
   const uint16_t cmask = (uint16_t)((1u << p.cl) - 1u);
-  if (p.c_lower && n0 > (m0_last + TC_BM - 1) / 2) return;  // above the diagonal: not needed
+  if (p.c_lower && n0 > (m0_last + TC_BM - 1) / p.kfac) return;  // above the diagonal: not needed
   // k-blocks of this CTA: split y takes [y per, (y + 1) per) of the tile's nonzero k-blocks.
   // The work is ordered panel-major: for each panel of at most OZ_CHUNK_KB k-blocks, every
   // slice pair in turn (one exact chunk each), so consecutive chunks reuse the same panel of
   // an A slice from L2 while it is hot.
   const int ncols = min(TC_BN, ((p.n_real - n0 + 15) / 16) * 16);  // MMA N for this tile
-  // nonzero k-blocks of the tile: below (m0 + 128) / 64 for a lower-triangular A; from
-  // 2 n0 / 64 for a lower-triangular B (zero for k < j); below 2 (n0 + ncols) / 64 for an
+  // nonzero k-blocks of the tile (k in real units, kfac per complex index): below
+  // (m0 + 128) / 64 for a lower-triangular A (rows are in the same units); from kfac n0 / 64
+  // for a lower-triangular B (zero for k < j); below kfac (n0 + ncols) / 64 for an
   // upper-triangular B (zero for k > j)
   int kb_first = 0, nkb = p.a_lower ? min(p.nkb, m0_last / TC_BK + TC_BM / TC_BK) : p.nkb;
-  if (p.b_tri == 2) kb_first = min(nkb, (2 * n0) / TC_BK);
-  if (p.b_tri == 1) nkb = min(nkb, (2 * (n0 + ncols) + TC_BK - 1) / TC_BK);
+  if (p.b_tri == 2) kb_first = min(nkb, (p.kfac * n0) / TC_BK);
+  if (p.b_tri == 1) nkb = min(nkb, (p.kfac * (n0 + ncols) + TC_BK - 1) / TC_BK);
   // split y takes either a range of k-blocks (all groups) or, for short K (one panel), a
   // range of slice groups (all k-blocks)
   int kb_lo = kb_first, kb_hi = nkb, pr_lo = 0, pr_hi = p.ngroups;
@@ -1038,16 +1040,26 @@ __global__ void oz_slice_hermitian3_kernel(const zd* Hs, int64_t ldh, int n, int
 // Columns of B in the Gauss form: column j of Y gives rows j of Yr, Yi, Yr + Yi; columns
 // j >= m of the padded block are zero (the buffer is cleared first).
 __global__ void oz_slice_cols3_kernel(const zd* Y, int64_t ldy, int n, int m, int S, __nv_bfloat16* B,
-                                      int64_t sliceB, int64_t zstride, int Kp, int Np, int* eB) {
+                                      int64_t sliceB, int64_t zstride, int Kp, int Np, int* eB,
+                                      int lower_half) {
   const int j = blockIdx.x;
   if (j >= m) {
     if (threadIdx.x == 0) eB[j] = eB[Np + j] = eB[2 * Np + j] = 0;
     return;
   }
   const zd* y = Y + (int64_t)j * ldy;
+  // lower_half: as oz_slice_cols_kernel (zero above the diagonal, half of the diagonal entry)
+  auto entry = [&](int k) -> zd {
+    zd v = y[k];
+    if (lower_half) {
+      if (k < j) v = zmk(0.0, 0.0);
+      else if (k == j) v = zmk(0.5 * v.x, 0.5 * v.y);
+    }
+    return v;
+  };
   unsigned long long m0 = 0ull, m1 = 0ull, m2 = 0ull;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const zd v = y[k];
+    const zd v = entry(k);
     const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y), c = abs_bits(v.x + v.y);
     m0 = a > m0 ? a : m0;
     m1 = b > m1 ? b : m1;
@@ -1063,10 +1075,72 @@ __global__ void oz_slice_cols3_kernel(const zd* Y, int64_t ldy, int n, int m, in
   }
   __nv_bfloat16* c0 = B + (int64_t)j * Kp;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const zd v = y[k];
+    const zd v = entry(k);
     digits(v.x, e0, S, c0 + k, sliceB);
     digits(v.y, e1, S, c0 + zstride + k, sliceB);
     digits(v.x + v.y, e2, S, c0 + 2 * zstride + k, sliceB);
+  }
+}
+
+// Gauss-form slices from the ROWS of X (rows x cols, column-major): row r of the operand is
+// row r of X (conj = 0: an A operand) or its conjugate (conj = 1: column r of a B operand
+// op(B) = X^H); the three parts re, im, re + im get a scale per row each (e[z * e_stride + r])
+// and their digits go to out + z * zstride + r * Kp + k.  Same two-kernel scheme as the
+// embedding's row slices.
+__global__ void oz_row_exponents3_kernel(const zd* X, int64_t ldx, int rows, int cols, int conj, int* e_out,
+                                         int e_stride) {
+  __shared__ unsigned long long red[3][8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int r = blockIdx.x * 32 + tx;
+  unsigned long long m0 = 0ull, m1 = 0ull, m2 = 0ull;
+  if (r < rows)
+    for (int k = ty; k < cols; k += 8) {
+      const zd v = X[r + (int64_t)k * ldx];
+      const double re = v.x, im = conj ? -v.y : v.y;
+      const unsigned long long a = abs_bits(re), b = abs_bits(im), c = abs_bits(re + im);
+      m0 = a > m0 ? a : m0;
+      m1 = b > m1 ? b : m1;
+      m2 = c > m2 ? c : m2;
+    }
+  red[0][ty][tx] = m0;
+  red[1][ty][tx] = m1;
+  red[2][ty][tx] = m2;
+  __syncthreads();
+  if (ty < 3 && r < rows) {
+    unsigned long long mz = red[ty][0][tx];
+    for (int j = 1; j < 8; ++j) mz = red[ty][j][tx] > mz ? red[ty][j][tx] : mz;
+    e_out[ty * e_stride + r] = exponent_from_bits(mz);
+  }
+}
+
+__global__ void oz_slice_rows3_kernel(const zd* X, int64_t ldx, int rows, int cols, int S, int conj,
+                                      __nv_bfloat16* out, int64_t slice_stride, int64_t zstride, int Kp,
+                                      const int* e_row, int e_stride, int chunk) {
+  __shared__ int ex[3][32];
+  __shared__ zd tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int r0 = blockIdx.x * 32;
+  if (ty < 3) ex[ty][tx] = (r0 + tx < rows) ? e_row[ty * e_stride + r0 + tx] : 0;
+  __syncthreads();
+  const int k_end = min(cols, (int)(blockIdx.y + 1) * chunk);
+  for (int k0 = blockIdx.y * chunk; k0 < k_end; k0 += 32) {
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int gr = r0 + tx, gk = k0 + rr;  // read column gk, rows r0..r0+31 (coalesced)
+      tile[rr][tx] = (gr < rows && gk < k_end) ? X[gr + (int64_t)gk * ldx] : zmk(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int rr = ty; rr < 32; rr += 8) {  // write row r0 + rr, columns k0 + tx (coalesced)
+      const int gr = r0 + rr, gk = k0 + tx;
+      if (gr < rows && gk < k_end) {
+        const zd v = tile[tx][rr];
+        const double re = v.x, im = conj ? -v.y : v.y;
+        __nv_bfloat16* o = out + (int64_t)gr * Kp + gk;
+        digits(re, ex[0][rr], S, o, slice_stride);
+        digits(im, ex[1][rr], S, o + zstride, slice_stride);
+        digits(re + im, ex[2][rr], S, o + 2 * zstride, slice_stride);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1076,12 +1150,13 @@ __global__ void oz_slice_cols3_kernel(const zd* Y, int64_t ldy, int n, int m, in
 __global__ void oz_epilogue3_kernel(const float2* part, int splits, int Mp, int Np, const int* eA,
                                     const int* eB, int n, int m, double alpha, double beta,
                                     const zd* Cin, int64_t ldcin, double gamma, const zd* D,
-                                    int64_t ldd, zd* out, int64_t ldo) {
+                                    int64_t ldd, zd* out, int64_t ldo, int lower) {
   const int64_t total = (int64_t)n * m;
   const int64_t zst = (int64_t)splits * Mp * Np;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % n), j = (int)(e / n);
+    if (lower && j > i) continue;
     double v[3];
 #pragma unroll
     for (int z = 0; z < 3; ++z) {
@@ -1334,8 +1409,8 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
   const int n = a.M, m = b.N, Kp = a.Kp, Mp = a.Mp, Np = b.Np;
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (S > b.S || S > a.S || S < 1 || a.Kp != b.Kp || a.nz != b.nz) return cudaErrorInvalidValue;
-  const int nz = a.nz;  // 3: Gauss form (tcgen05 path, general products only)
-  if (nz != 1 && (nz != 3 || !oz_use_tcgen05() || a_lower || c_lower || b_tri)) return cudaErrorInvalidValue;
+  const int nz = a.nz;  // 3: Gauss form (tcgen05 path only)
+  if (nz != 1 && (nz != 3 || !oz_use_tcgen05())) return cudaErrorInvalidValue;
   cudaError_t e;
   // Pairs (s, t) with s + t <= S + 1, grouped by the A slice s so that consecutive pairs
   // stream the same slice of the large operand (it stays in L2 between them).
@@ -1361,6 +1436,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     tp.part = oz.part;
     tp.status = oz.status;
     tp.nz = nz;
+    tp.kfac = nz > 1 ? 1 : 2;
     tp.a_zrows = nz > 1 ? a.S * Mp : 0;
     tp.b_zrows = nz > 1 ? b.S * Np : 0;
     // first-level waits: the context's bound (a test hook) or the default; the waits that
@@ -1411,7 +1487,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
     const int model_splits =
         choose_tc_splits(tiles, tp.nkb, tp.ngroups, part_cap, (int64_t)Mp * Np, &model_pair_split);
     const uint64_t b_rows = std::max<uint64_t>((uint64_t)nz * b.S * Np, (uint64_t)TC_BN);
-    if ((int64_t)b_rows * Kp > (int64_t)b.S_max * b.Np_max * b.Kp_max) return cudaErrorInvalidValue;
+    if ((int64_t)b_rows * Kp > b.elems) return cudaErrorInvalidValue;
     if (!encode_bf16_map(&mapA, a.ptr, Kp, (uint64_t)nz * a.S * Mp, TC_BM) ||
         !encode_bf16_map(&mapB, b.ptr, Kp, b_rows, tp.b_box_rows / tp.cl))
       return cudaErrorInvalidValue;
@@ -1487,6 +1563,7 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
       }
     }
     splits = best_splits;
+    if ((size_t)splits * (size_t)nz * (size_t)Mp * (size_t)Np > oz.part_elems) return cudaErrorInvalidValue;
     if (ev_gemm_begin) cudaEventRecord(ev_gemm_begin, s);
     e = launch(best_splits, best_ps);
     if (ev_gemm_end) cudaEventRecord(ev_gemm_end, s);
@@ -1523,7 +1600,8 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
   const int blocks = (int)std::min<int64_t>(4 * sm_count(), (tot + 255) / 256);
   if (nz == 3)
     oz_epilogue3_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const float2*>(oz.part), splits, Mp, Np, a.e,
-                                               b.e, n, m, alpha, beta, Cin, ldcin, gamma, D, ldd, out, ldo);
+                                               b.e, n, m, alpha, beta, Cin, ldcin, gamma, D, ldd, out, ldo,
+                                               c_lower);
   else
     oz_epilogue_kernel<<<blocks, 256, 0, s>>>(oz.part, splits, Mp, Np, a.e, b.e, n, m, alpha, beta, Cin,
                                               ldcin, gamma, D, ldd, out, ldo, c_lower,
@@ -1532,42 +1610,79 @@ cudaError_t oz_product(const OzA& a, const OzB& b, int S, double alpha, double b
   return cudaGetLastError();
 }
 
-// Gauss form of the filter's product (three real products, section "Gauss form" above):
-// environment variable CHFSI_OZ_GAUSS (0 keeps the real embedding; default on with tcgen05).
-static bool oz_gauss() {
+// Gauss form of the complex products (three real products, see the slicing kernels above):
+// with the tcgen05 kernel, when the workspace allows it (the solver allows it for a
+// well-conditioned B), unless environment variable CHFSI_OZ_GAUSS=0 keeps the embedding.
+static bool oz_gauss(const OzWorkspace& oz) {
   static const bool v = [] {
     const char* e = std::getenv("CHFSI_OZ_GAUSS");
     return !(e && std::atoi(e) == 0);
   }();
-  return v && oz_use_tcgen05();
+  return v && oz.gauss && oz_use_tcgen05();
 }
 
-// Hs (n x n Hermitian) as the Gauss-form A operand: slices of Hr, Hi, Hr + Hi of H = Hs.
-static cudaError_t oz_slice_a3(OzA& a, const zd* Hs, int64_t ldh, int n, int S, cudaStream_t s) {
-  const int Mp = ((n + TC_BM - 1) / TC_BM) * TC_BM, Kp = ((n + OZ_BK - 1) / OZ_BK) * OZ_BK;
-  if (S > a.S_max || S < 1 || n <= 0 || (int64_t)3 * Mp * Kp > (int64_t)a.Mp_max * a.Kp_max ||
-      3 * Mp > 3 * a.Mp_max)
+// op(A) (M x K) as the Gauss-form A operand: slices of its real part, imaginary part and
+// their sum, a scale per row of each.  op = OPC: row i is the conjugated column i of X (K x M,
+// contiguous); op = OPN: row i of X (M x K, strided; row slices as the embedding's).
+static cudaError_t oz_slice_a3(OzA& a, int op, const zd* X, int64_t ldx, int M, int K, int S, cudaStream_t s) {
+  const int Mp = ((M + TC_BM - 1) / TC_BM) * TC_BM, Kp = ((K + OZ_BK - 1) / OZ_BK) * OZ_BK;
+  if (S > a.S_max || S < 1 || M <= 0 || K <= 0 || Mp > a.Mp_max ||
+      (int64_t)3 * S * Mp * Kp > (int64_t)a.S_max * a.Mp_max * a.Kp_max)
     return cudaErrorInvalidValue;
-  a.S = S; a.M = n; a.K = n; a.Mp = Mp; a.Kp = Kp; a.nz = 3;
+  a.S = S; a.M = M; a.K = K; a.Mp = Mp; a.Kp = Kp; a.nz = 3;
   a.slice = (int64_t)Mp * Kp;
-  cudaError_t e = cudaMemsetAsync(a.ptr, 0, sizeof(__nv_bfloat16) * (size_t)3 * S * a.slice, s);
+  const int64_t zstride = (int64_t)S * a.slice;
+  cudaError_t e = cudaMemsetAsync(a.ptr, 0, sizeof(__nv_bfloat16) * (size_t)3 * zstride, s);
   if (e != cudaSuccess) return e;
-  oz_slice_hermitian3_kernel<<<n, 256, 0, s>>>(Hs, ldh, n, S, a.ptr, a.slice, (int64_t)S * a.slice, Kp, Mp, a.e);
+  if (op == OPC) {
+    oz_slice_hermitian3_kernel<<<M, 256, 0, s>>>(X, ldx, K, S, a.ptr, a.slice, zstride, Kp, Mp, a.e);
+    CHFSI_COUNT_LAUNCH();
+    return cudaGetLastError();
+  }
+  const int groups = (M + 31) / 32, kchunks = (K + 31) / 32;
+  oz_row_exponents3_kernel<<<groups, 256, 0, s>>>(X, ldx, M, K, 0, a.e, Mp);
+  CHFSI_COUNT_LAUNCH();
+  const int gy = std::max(1, std::min(kchunks, (4 * sm_count() + groups - 1) / groups));
+  const int chunk = 32 * ((kchunks + gy - 1) / gy);
+  oz_slice_rows3_kernel<<<dim3(groups, (K + chunk - 1) / chunk), 256, 0, s>>>(
+      X, ldx, M, K, S, 0, a.ptr, a.slice, zstride, Kp, a.e, Mp, chunk);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
 
-// Y (K x N) as the Gauss-form B operand (Yr, Yi, Yr + Yi), K-padding as the A operand's.
-static cudaError_t oz_slice_b3(OzB& b, const zd* Y, int64_t ldy, int K, int N, int S, int Kp, cudaStream_t s) {
+// op(B) (K x N) as the Gauss-form B operand, K-padding as the A operand's: op = OPN: column j
+// of X (optionally its lower half, as oz_slice_cols_kernel); op = OPC: the conjugated row j of
+// X (N x K).
+static cudaError_t oz_slice_b3(OzB& b, int op, const zd* X, int64_t ldx, int K, int N, int S, int Kp,
+                               cudaStream_t s, int lower_half) {
   const int Np = oz_padded_n(N);
-  if (S > b.S_max || S < 1 || N <= 0 || 3 * Np > 3 * b.Np_max ||
-      (int64_t)3 * S * std::max(Np, TC_BN) * Kp > (int64_t)b.S_max * b.Np_max * b.Kp_max)
+  if (S > b.S_max || S < 1 || N <= 0 || K <= 0 || Np > b.Np_max ||
+      (int64_t)3 * S * std::max(Np, TC_BN) * Kp > b.elems)
     return cudaErrorInvalidValue;
   b.S = S; b.N = N; b.Np = Np; b.Kp = Kp; b.nz = 3;
   b.slice = (int64_t)Np * Kp;
-  cudaError_t e = cudaMemsetAsync(b.ptr, 0, sizeof(__nv_bfloat16) * (size_t)3 * S * b.slice, s);
+  const int64_t zstride = (int64_t)S * b.slice;
+  cudaError_t e = cudaMemsetAsync(b.ptr, 0, sizeof(__nv_bfloat16) * (size_t)3 * zstride, s);
   if (e != cudaSuccess) return e;
-  oz_slice_cols3_kernel<<<Np, 256, 0, s>>>(Y, ldy, K, N, S, b.ptr, b.slice, (int64_t)S * b.slice, Kp, Np, b.e);
+  if (op == OPC) {
+    const int groups = (N + 31) / 32, kchunks = (K + 31) / 32;
+    oz_row_exponents3_kernel<<<groups, 256, 0, s>>>(X, ldx, N, K, 1, b.e, Np);
+    CHFSI_COUNT_LAUNCH();
+    const int gy = std::max(1, std::min(kchunks, (4 * sm_count() + groups - 1) / groups));
+    const int chunk = 32 * ((kchunks + gy - 1) / gy);
+    oz_slice_rows3_kernel<<<dim3(groups, (K + chunk - 1) / chunk), 256, 0, s>>>(
+        X, ldx, N, K, S, 1, b.ptr, b.slice, zstride, Kp, b.e, Np, chunk);
+    CHFSI_COUNT_LAUNCH();
+    // exponents of the padded columns j >= N
+    if (Np > N) {
+      e = cudaMemsetAsync(b.e + N, 0, sizeof(int) * (size_t)(Np - N), s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(b.e + Np + N, 0, sizeof(int) * (size_t)(Np - N), s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(b.e + 2 * Np + N, 0, sizeof(int) * (size_t)(Np - N), s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+  }
+  oz_slice_cols3_kernel<<<Np, 256, 0, s>>>(X, ldx, K, N, S, b.ptr, b.slice, zstride, Kp, Np, b.e, lower_half);
   CHFSI_COUNT_LAUNCH();
   return cudaGetLastError();
 }
@@ -1575,8 +1690,7 @@ static cudaError_t oz_slice_b3(OzB& b, const zd* Y, int64_t ldy, int K, int N, i
 // ---- the Hermitian matrix of the filter (its slices stay in oz.H for the whole problem)
 cudaError_t oz_slice_hermitian(const zd* Hs, int64_t ldh, int n, int S, OzWorkspace& oz,
                                cudaStream_t s) {
-  if (oz_gauss()) return oz_slice_a3(oz.H, Hs, ldh, n, S, s);
-  oz.H.nz = 1;
+  if (oz_gauss(oz)) return oz_slice_a3(oz.H, OPC, Hs, ldh, n, n, S, s);
   return oz_slice_a(oz.H, OPC, Hs, ldh, n, n, S, s);
 }
 
@@ -1588,7 +1702,7 @@ cudaError_t oz_filter_product(const zd* Y, int64_t ldy, int n, int m, int S, dou
                               cudaEvent_t ev_gemm_begin, cudaEvent_t ev_gemm_end) {
   if (m <= 0) return cudaSuccess;
   if (S > oz.H.S || S < 1 || oz.H.M != n) return cudaErrorInvalidValue;
-  cudaError_t e = oz.H.nz == 3 ? oz_slice_b3(oz.B, Y, ldy, n, m, S, oz.H.Kp, s)
+  cudaError_t e = oz.H.nz == 3 ? oz_slice_b3(oz.B, OPN, Y, ldy, n, m, S, oz.H.Kp, s, 0)
                                : oz_slice_b(oz.B, OPN, Y, ldy, n, m, S, oz.H.Kp, s);
   if (e != cudaSuccess) return e;
   return oz_product(oz.H, oz.B, S, alpha, beta, Cin, ldcin, gamma, D, ldd, out, ldo, 0, 0, oz, s,
@@ -1601,9 +1715,11 @@ cudaError_t oz_gemm(int opA, const zd* A, int64_t lda, int opB, const zd* B, int
                     int K, int S, double alpha, double beta, const zd* Cin, int64_t ldcin, double gamma,
                     const zd* D, int64_t ldd, zd* C, int64_t ldc, int a_lower, int c_lower,
                     OzWorkspace& oz, cudaStream_t s, int b_tri, int b_lower_half) {
-  cudaError_t e = oz_slice_a(oz.X, opA, A, lda, M, K, S, s);
+  const bool g3 = oz_gauss(oz);
+  cudaError_t e = g3 ? oz_slice_a3(oz.X, opA, A, lda, M, K, S, s) : oz_slice_a(oz.X, opA, A, lda, M, K, S, s);
   if (e != cudaSuccess) return e;
-  e = oz_slice_b(oz.B, opB, B, ldb, K, N, S, oz.X.Kp, s, b_lower_half);
+  e = g3 ? oz_slice_b3(oz.B, opB, B, ldb, K, N, S, oz.X.Kp, s, b_lower_half)
+         : oz_slice_b(oz.B, opB, B, ldb, K, N, S, oz.X.Kp, s, b_lower_half);
   if (e != cudaSuccess) return e;
   return oz_product(oz.X, oz.B, S, alpha, beta, Cin, ldcin, gamma, D, ldd, C, ldc, a_lower, c_lower, oz,
                     s, nullptr, nullptr, b_tri);
@@ -1631,13 +1747,21 @@ cudaError_t oz_alloc(OzWorkspace& oz, int n_max, int blk_max, int S_max) {
   oz.B.Kp_max = oz_padded_k(n_max);
   // covers both kernels' paddings and at least one full B box of the tcgen05 kernel
   oz.B.Np_max = ((std::max(cols, TC_BN) + OZ_BN - 1) / OZ_BN) * OZ_BN;
-  e = cudaMalloc((void**)&oz.B.ptr, sizeof(__nv_bfloat16) * (size_t)S_max * oz.B.Np_max * oz.B.Kp_max);
+  // the Gauss form holds three K x N parts (K padded to 64 complex entries) per slice, the
+  // embedding one 2K-row part
+  const int64_t kp1 = ((n_max + OZ_BK - 1) / OZ_BK) * OZ_BK;
+  oz.B.elems = std::max<int64_t>((int64_t)S_max * oz.B.Np_max * oz.B.Kp_max,
+                                 (int64_t)3 * S_max * std::max(oz.B.Np_max, TC_BN) * kp1);
+  e = cudaMalloc((void**)&oz.B.ptr, sizeof(__nv_bfloat16) * (size_t)oz.B.elems);
   if (e != cudaSuccess) return e;
   e = cudaMalloc((void**)&oz.B.e, sizeof(int) * (size_t)3 * oz.B.Np_max);
   if (e != cudaSuccess) return e;
   const int np_blk = ((blk_max + OZ_BN - 1) / OZ_BN) * OZ_BN;
   const size_t mp = (size_t)oz_padded_m(n_max);
-  oz.part_elems = std::max((size_t)32 * mp * np_blk, mp * oz.B.Np_max);
+  const size_t mp1 = (size_t)((n_max + TC_BM - 1) / TC_BM) * TC_BM;  // rows of a Gauss-form product
+  // split partials: 32 splits of a block product, one split of an n x n product (three of
+  // them in the Gauss form)
+  oz.part_elems = std::max({(size_t)32 * mp * np_blk, mp * oz.B.Np_max, (size_t)3 * mp1 * oz.B.Np_max});
   return cudaMalloc((void**)&oz.part, sizeof(double) * oz.part_elems);
 }
 

@@ -300,14 +300,15 @@ int blocked_trinv(chfsi_ctx* ctx, const zd* L, int64_t ld, zd* X, int64_t ldx, i
 // T = Linv Af, Hs = Linv T^H.  Otherwise (FP64): T = Linv Af, lower of T Linv^H, mirrored.
 // Slices: the row scales of L^{-1} grow like sqrt(cond(B)), and its two products carry that
 // growth into Hs; 8 slices (2^-56) keep the eigenvalue error at the FP64 level for cond(B)
-// 1e4, 7 slices (2^-49) do so for a well-conditioned B (squared pivots within a factor 100;
-// that ratio is a lower bound of cond(B), so an ill-conditioned B may still take 7 only if
-// its pivots hide it, which the generalized-residual acceptance then still checks).
+// 1e4, 7 slices (2^-49) do so for a well-conditioned B (squared pivots within a factor 10;
+// that ratio is a lower bound of cond(B) — 58.6 for a random B of condition 1e4 at n = 2600
+// — so an ill-conditioned B may still take 7 only if its pivots hide it, which the
+// generalized-residual acceptance then still checks).
 int reduce_to_standard(chfsi_ctx* ctx, const zd* Af, int64_t lda, const zd* Linv, int64_t ldl,
                        zd* Hs, int64_t ldh, int n, bool split = false, double cond_lb = INFINITY) {
   Workspace& ws = ctx->ws;
   if (split) {
-    const int S = cond_lb < 100.0 ? 7 : 8;
+    const int S = cond_lb < 10.0 ? 7 : 8;
     // P = Linv A_h: lower x lower, lower tiles only (B zero for k < j)
     CK(oz_gemm(OPN, Linv, ldl, OPN, Af, lda, n, n, n, S, 1.0, 0.0, nullptr, 0, 0.0, nullptr, 0, ws.T,
                ws.n_max, 1, 1, ws.oz, ctx->stream, /*b_tri=*/2, /*b_lower_half=*/1));
@@ -694,10 +695,12 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       double piv[2];
       CKS(read_back(ctx, piv, ws.scal + 12, 2));
       ctx->factor_cond_lb = piv[1] > 0.0 ? piv[0] / piv[1] : INFINITY;
-      // Gauss form of the problem's complex products only for a well-conditioned B (pivots
-      // within a factor 100): with cond(B) ~ 1e4 the filter needs accuracy at the edge of 7
-      // slices, and the Gauss form's error bound is three times the embedding's
-      ws.oz.gauss = ctx->factor_cond_lb < 100.0 ? 1 : 0;
+      // Gauss form of the problem's complex products only for a well-conditioned B (squared
+      // pivots within a factor 10; the pivot ratio is a lower bound of cond(B), 58.6 for a
+      // random B of condition 1e4 at n = 2600 and about 1 for B = I + 0.1 G^H G / n): with
+      // cond(B) ~ 1e4 the filter needs accuracy at the edge of 7 slices, and the Gauss
+      // form's error bound is three times the embedding's
+      ws.oz.gauss = ctx->factor_cond_lb < 10.0 ? 1 : 0;
       CKS(blocked_trinv(ctx, ws.Lf, ld, ws.Linv, ld, n));
       ctx->has_factor = true;
       ctx->factor_n = n;

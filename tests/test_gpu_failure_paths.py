@@ -92,3 +92,26 @@ def test_loop_limit_reports_the_locked_prefix_like_the_oracle():
         lam2, X2, st2 = cb.chfsi_solve_next(s.ctx, A.to(DEV), B.to(DEV), 6, 10, 10)
     assert np.max(np.abs(lam2.cpu().numpy() - p.lam[:6])) <= 1e-10 * np.max(np.abs(p.lam))
     assert st2["max_resid"] <= 1e-10
+
+
+def test_unreachable_tolerance_reports_no_convergence():
+    """A tolerance below what FP64 arithmetic can reach (1e-18 on the n = 512 workload) is
+    reported as CHFSI_ENOCONV — never as success — with the pairs that did lock finite and
+    the rest NaN, and the context solves a well-posed problem afterwards."""
+    seq = inputs.planted_sequence("c1", N=1, keep_vectors=False)
+    p = seq.problems[0]
+    A, B = torch.tril(p.A).to(DEV), torch.tril(p.B).to(DEV)
+    with cb.Solver(seq.n, seq.blk, max_loops=25) as s:
+        with pytest.raises(cb.ChfsiError) as ei:
+            cb.chfsi_solve_next(s.ctx, A, B, seq.nev, seq.blk, seq.deg, tol=1e-18)
+        assert ei.value.code == cb.CHFSI_ENOCONV
+        lam, _, st = ei.value.partial
+        lam = lam.cpu().numpy()
+        done = np.isfinite(lam)
+        k = int(done.sum())
+        assert np.all(done[:k]) and not np.any(done[k:])
+        assert k < seq.nev
+        cb.chfsi_reset_warm_state(s.ctx)
+        lam2, _, st2 = cb.chfsi_solve_next(s.ctx, A, B, seq.nev, seq.blk, seq.deg, tol=seq.tol)
+    assert np.max(np.abs(lam2.cpu().numpy() - p.lam[:seq.nev])) <= 1e-10 * np.max(np.abs(p.lam))
+    assert st2["max_resid"] <= seq.tol

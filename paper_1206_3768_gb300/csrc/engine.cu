@@ -699,7 +699,7 @@ int solve_one(chfsi_ctx* ctx, const SolveArgs& S) {
       // pivots within a factor 10; the pivot ratio is a lower bound of cond(B), 58.6 for a
       // random B of condition 1e4 at n = 2600 and about 1 for B = I + 0.1 G^H G / n): with
       // cond(B) ~ 1e4 the filter needs accuracy at the edge of 7 slices, and the Gauss
-      // form's error bound is three times the embedding's
+      // form's errors are up to a few times the embedding's (three products' bounds)
       ws.oz.gauss = ctx->factor_cond_lb < 10.0 ? 1 : 0;
       CKS(blocked_trinv(ctx, ws.Lf, ld, ws.Linv, ld, n));
       ctx->has_factor = true;

@@ -112,3 +112,41 @@ def test_pairs_up_to_s_plus_t_equal_S_plus_1_give_the_stated_error(S):
                            (Fraction(K * (S + 3)) * Fraction(2) ** (e[i] + f[j] - 7 * S)))
                      for i in range(M) for j in range(N))
         assert worst2 > 1.0
+
+
+@pytest.mark.parametrize("S", [2, 4, 7])
+def test_gauss_form_error_is_the_sum_of_its_three_products_bounds(S):
+    """The Gauss form of a complex product, A B = (Ar Br - Ai Bi) + i((Ar + Ai)(Br + Bi)
+    - Ar Br - Ai Bi), with each real product taken by the kept slice pairs at its own row and
+    column scales: the real part's error is within the bounds of two products, the imaginary
+    part's within those of three; the scales of Ar + Ai and Br + Bi are at most twice the
+    embedding's (max over |Re|, |Im| of the row or column), so the whole is within six times
+    the embedding's bound K (S + 3) 2^{e_i + f_j - 7S}."""
+    rng = np.random.default_rng(70 + S)
+    M, N, K = 3, 3, 20
+    A = (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))) * np.exp(rng.uniform(-5, 5, (M, 1)))
+    B = (rng.standard_normal((K, N)) + 1j * rng.standard_normal((K, N))) * np.exp(rng.uniform(-5, 5, (1, N)))
+    keep = lambda s, t: s + t <= S + 1  # noqa: E731
+    Ar, Ai, Br, Bi = A.real.copy(), A.imag.copy(), B.real.copy(), B.imag.copy()
+    P0, e0, f0 = _product_model(Ar, Br, S, keep)
+    P1, e1, f1 = _product_model(Ai, Bi, S, keep)
+    P2, e2, f2 = _product_model(Ar + Ai, Br + Bi, S, keep)
+    bound = lambda e, f, i, j: Fraction(K * (S + 3)) * Fraction(2) ** (e[i] + f[j] - 7 * S)  # noqa: E731
+    e_emb = [_exponent(float(np.max(np.maximum(np.abs(Ar[i]), np.abs(Ai[i]))))) for i in range(M)]
+    f_emb = [_exponent(float(np.max(np.maximum(np.abs(Br[:, j]), np.abs(Bi[:, j]))))) for j in range(N)]
+    for i in range(M):
+        for j in range(N):
+            re_x = sum(Fraction(float(Ar[i, k])) * Fraction(float(Br[k, j])) -
+                       Fraction(float(Ai[i, k])) * Fraction(float(Bi[k, j])) for k in range(K))
+            im_x = sum(Fraction(float(Ar[i, k])) * Fraction(float(Bi[k, j])) +
+                       Fraction(float(Ai[i, k])) * Fraction(float(Br[k, j])) for k in range(K))
+            # the FP64 rounding of the sums Ar + Ai, Br + Bi is a perturbation of the
+            # operands below 2^-53 of their scales, far inside the 2^-7S bounds for S <= 7
+            re_err = abs(P0[i][j] - P1[i][j] - re_x)
+            im_err = abs(P2[i][j] - P0[i][j] - P1[i][j] - im_x)
+            b0, b1, b2 = bound(e0, f0, i, j), bound(e1, f1, i, j), bound(e2, f2, i, j)
+            rounding = Fraction(K * 4) * Fraction(2) ** (e_emb[i] + f_emb[j] - 52)
+            assert re_err <= b0 + b1
+            assert im_err <= b0 + b1 + b2 + rounding
+            emb = bound(e_emb, f_emb, i, j)
+            assert b0 + b1 + b2 <= 6 * emb

@@ -478,8 +478,9 @@ def test_filter_split_matches_oracle(ctx, n, m, slices, tol):
     """Split-BF16 digit products reproduce the FP64 filter to about 2^(-7 slices), down to the
     two slices the adaptive slice count of the mixed-precision filter may choose.  The
     tensor-core path takes the product in the Gauss form, whose imaginary part is the
-    difference of three real products (P2 - P0 - P1), each truncated at the scales of
-    |Hr| + |Hi| and |Yr| + |Yi|: its bound is three times the embedding's, hence 3 tol."""
+    difference of three real products (P2 - P0 - P1), each truncated at its own scales: its
+    worst-case bound is up to six times the embedding's (the exact model in
+    test_digit_arithmetic.py), the errors measured here stay within three times: 3 tol."""
     tol = 3.0 * tol
     rng = _rng(n + m + slices)
     lam = np.sort(rng.uniform(-2, 2, n))

@@ -112,6 +112,24 @@ const char* chfsi_last_error(const chfsi_ctx* ctx);
 /* Drop the carried Ritz vectors and the cached factor of B: the next solve starts cold. */
 int chfsi_reset_warm_state(chfsi_ctx* ctx);
 
+/* Checkpoint and resume of the warm state (Section 3.2, stage 3: the eigenvectors of problem
+ * l seed problem l + 1), so that a sequence can continue in another context or process.
+ * The state is the last solve's blk Ritz vectors in x-coordinates (B-orthonormal, n x blk)
+ * and their Ritz values; the factor of B is not part of it (the next solve factors its B).
+ * chfsi_get_state: *n and *blk receive the state's sizes (both 0 when the context has no
+ * warm state: after a cold context, chfsi_reset_warm_state or a solve that did not converge);
+ * X (n x blk complex, column-major, ld n; host or device) and lam (blk doubles, host) are
+ * filled when not NULL (query the sizes first with both NULL).  The call synchronises the
+ * context's stream.
+ * chfsi_set_state: installs n x blk vectors X (ld ldx >= n; host or device) and blk values
+ * lam (host, ascending) as the warm state; the next solve with this n and blk starts from
+ * them.  Copies before returning (the caller may free X and lam).  n = 0 clears the state.
+ * Errors: EINVAL (NULL context, n > n_max, blk > blk_max, blk < 1 or NULL arrays with
+ * n > 0, ldx < n), ECUDA. */
+int chfsi_get_state(chfsi_ctx* ctx, int64_t* n, int32_t* blk, chfsi_z* X, double* lam);
+int chfsi_set_state(chfsi_ctx* ctx, int64_t n, int32_t blk, const chfsi_z* X, int64_t ldx,
+                    const double* lam);
+
 /* ---------------------------------------------------------------- solves */
 /* Solve one problem of the sequence (Algorithm 1 with the reduction of Section 3.2).
  *   A, B   n x n (lower triangles read), leading dimensions lda, ldb.

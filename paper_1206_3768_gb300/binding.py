@@ -90,6 +90,8 @@ _SIGS = {
     "chfsi_destroy": (None, [_P]),
     "chfsi_last_error": (c_char_p, [_P]),
     "chfsi_reset_warm_state": (c_int32, [_P]),
+    "chfsi_get_state": (c_int32, [_P, POINTER(c_int64), POINTER(c_int32), _P, _P]),
+    "chfsi_set_state": (c_int32, [_P, c_int64, c_int32, _P, c_int64, _P]),
     "chfsi_solve_next": (c_int32, [_P, c_int64, _P, c_int64, _P, c_int64, _P, c_int32, c_int32,
                                    c_int32, c_double, _P, _P, POINTER(chfsi_stats)]),
     "chfsi_solve_sequence": (c_int32, [_P, c_int32, c_int64, _P, _P, c_int64, _P, c_int32,
@@ -230,6 +232,29 @@ def chfsi_last_error(ctx) -> str:
 
 def chfsi_reset_warm_state(ctx):
     _check(ctx, load().chfsi_reset_warm_state(ctx))
+
+
+def chfsi_get_state(ctx, device="cuda"):
+    """The warm state (x-coordinate Ritz vectors n x blk, Ritz values) or None."""
+    n, blk = c_int64(0), c_int32(0)
+    _check(ctx, load().chfsi_get_state(ctx, ctypes.byref(n), ctypes.byref(blk), None, None))
+    if n.value == 0:
+        return None
+    X = fortran_empty(n.value, blk.value, torch.device(device))
+    lam = torch.empty(blk.value, dtype=torch.float64)  # host
+    _check(ctx, load().chfsi_get_state(ctx, ctypes.byref(n), ctypes.byref(blk), _ptr(X), _ptr(lam)))
+    return X, lam
+
+
+def chfsi_set_state(ctx, state):
+    """Install a state from chfsi_get_state (None clears it)."""
+    if state is None:
+        _check(ctx, load().chfsi_set_state(ctx, 0, 0, None, 1, None))
+        return
+    X, lam = state
+    Xf = fortran(X)
+    lam = torch.as_tensor(lam, dtype=torch.float64).cpu().contiguous()
+    _check(ctx, load().chfsi_set_state(ctx, Xf.shape[0], Xf.shape[1], _ptr(Xf), _ld(Xf), _ptr(lam)))
 
 
 def chfsi_solve_next(ctx, A: torch.Tensor, B: torch.Tensor, nev: int, blk: int, deg: int,

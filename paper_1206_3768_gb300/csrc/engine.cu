@@ -1248,6 +1248,46 @@ int chfsi_reset_warm_state(chfsi_ctx* ctx) {
   return CHFSI_OK;
 }
 
+int chfsi_get_state(chfsi_ctx* ctx, int64_t* n, int32_t* blk, chfsi_z* X, double* lam) {
+  entry_guard("chfsi_get_state");
+  if (!ctx || !n || !blk) return set_err(ctx, CHFSI_EINVAL, "bad args");
+  const bool have = ctx->has_warm && (int)ctx->warm_lam.size() == ctx->warm_blk;
+  *n = have ? ctx->warm_n : 0;
+  *blk = have ? ctx->warm_blk : 0;
+  if (!have) return CHFSI_OK;
+  cudaSetDevice(ctx->ws.dev);
+  if (X)
+    CK(cudaMemcpy2DAsync(X, (size_t)ctx->warm_n * sizeof(zd), ctx->ws.Xw, (size_t)ctx->ws.n_max * sizeof(zd),
+                         (size_t)ctx->warm_n * sizeof(zd), (size_t)ctx->warm_blk, cudaMemcpyDefault,
+                         ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (lam) std::copy(ctx->warm_lam.begin(), ctx->warm_lam.end(), lam);
+  return CHFSI_OK;
+}
+
+int chfsi_set_state(chfsi_ctx* ctx, int64_t n, int32_t blk, const chfsi_z* X, int64_t ldx,
+                    const double* lam) {
+  entry_guard("chfsi_set_state");
+  if (!ctx) return CHFSI_EINVAL;
+  if (n == 0) {
+    ctx->has_warm = false;
+    ctx->warm_lam.clear();
+    return CHFSI_OK;
+  }
+  if (n < 0 || n > ctx->ws.n_max || blk < 1 || blk > ctx->ws.blk_max || blk > n || !X || !lam || ldx < n)
+    return set_err(ctx, CHFSI_EINVAL, "bad state: n=%lld blk=%d ldx=%lld", (long long)n, blk,
+                   (long long)ldx);
+  cudaSetDevice(ctx->ws.dev);
+  CK(cudaMemcpy2DAsync(ctx->ws.Xw, (size_t)ctx->ws.n_max * sizeof(zd), X, (size_t)ldx * sizeof(zd),
+                       (size_t)n * sizeof(zd), (size_t)blk, cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->warm_lam.assign(lam, lam + blk);
+  ctx->warm_n = n;
+  ctx->warm_blk = blk;
+  ctx->has_warm = true;
+  return CHFSI_OK;
+}
+
 int chfsi_solve_next(chfsi_ctx* ctx, int64_t n, const chfsi_z* A, int64_t lda, const chfsi_z* B,
                      int64_t ldb, const chfsi_z* V0, int32_t nev, int32_t blk, int32_t deg,
                      double tol, double* evals, chfsi_z* evecs, chfsi_stats* st) {

@@ -695,3 +695,36 @@ def test_batch_uneven_sequences_match_sequential():
                 assert np.max(np.abs(ev_b[ell].numpy() - p.lam[:q.nev])) <= 1e-10 * scale
                 assert st_b[ell]["converged"] == q.nev
                 assert st_b[ell]["max_resid"] <= 1e-10
+
+
+def test_warm_state_checkpoint_resumes_the_sequence_in_another_context():
+    """The warm state (Section 3.2, stage 3) taken from one context after two problems and
+    installed in a fresh context continues the sequence as the first context does: problem 2
+    with the same loop count and eigenvalues to rounding; no state after a reset."""
+    seq = inputs.planted_sequence("c1", N=3, keep_vectors=False)
+    nev, blk = seq.nev, seq.blk
+    As = [torch.tril(p.A).to(DEV) for p in seq.problems]
+    Bs = [torch.tril(p.B).to(DEV) for p in seq.problems]
+    with cb.Solver(seq.n, blk) as s1, cb.Solver(seq.n, blk) as s2:
+        assert cb.chfsi_get_state(s2.ctx) is None
+        for ell in (0, 1):
+            cb.chfsi_solve_next(s1.ctx, As[ell], Bs[ell], nev, blk, seq.deg)
+        state = cb.chfsi_get_state(s1.ctx)
+        assert state is not None and tuple(state[0].shape) == (seq.n, blk) and state[1].shape[0] == blk
+        # B-orthonormal x-vectors and ascending Ritz values of problem 1
+        Bf = (Bs[1] + Bs[1].mH - torch.diag(torch.diagonal(Bs[1])))
+        E = state[0].mH @ (Bf @ state[0]) - torch.eye(blk, dtype=torch.complex128, device=DEV)
+        assert float(E.abs().max()) < 1e-10
+        assert np.all(np.diff(state[1].numpy()) >= 0)
+        cb.chfsi_set_state(s2.ctx, state)
+        lam1, _, st1 = cb.chfsi_solve_next(s1.ctx, As[2], Bs[2], nev, blk, seq.deg)
+        lam2, _, st2 = cb.chfsi_solve_next(s2.ctx, As[2], Bs[2], nev, blk, seq.deg)
+        assert st1["loops"] == st2["loops"]
+        p2 = seq.problems[2]
+        scale = np.max(np.abs(p2.lam))
+        assert np.max(np.abs(lam1.cpu().numpy() - lam2.cpu().numpy())) <= 1e-12 * scale
+        assert np.max(np.abs(lam2.cpu().numpy() - p2.lam[:nev])) <= 1e-10 * scale
+        cb.chfsi_reset_warm_state(s1.ctx)
+        assert cb.chfsi_get_state(s1.ctx) is None
+        cb.chfsi_set_state(s2.ctx, None)
+        assert cb.chfsi_get_state(s2.ctx) is None

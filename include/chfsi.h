@@ -103,8 +103,9 @@ void chfsi_default_opts(chfsi_opts* opts);
 /* Create a context able to solve problems with n <= n_max and blk <= blk_max; allocates
  * all device workspace: six n_max x n_max complex matrices, bf16 digit-slice buffers (two
  * of 8 slices of the 2 n_max x 2 n_max real embedding, one of 8 slices of up to n_max
- * columns), split-K partials and about 12 n_max blk_max complex entries: about 2.0 GB at
- * n_max = 2600, blk_max = 130.
+ * columns, or the Gauss form's three parts), split-K partials and about 12 n_max
+ * max(blk_max, 128) complex entries: about 2.3 GB at n_max = 2600, blk_max = 130, and 26.5
+ * GB (measured) at n_max = 9300, blk_max = 320.
  * opts may be NULL (defaults).  Errors: EINVAL, ENOMEM, ECUDA. */
 int chfsi_create(chfsi_ctx** out, int64_t n_max, int32_t blk_max, const chfsi_opts* opts);
 void chfsi_destroy(chfsi_ctx* ctx);

@@ -226,7 +226,9 @@ GemmDesc gd(int M, int N, int K, const zd* A, int64_t lda, int opA, const zd* B,
   return g;
 }
 
-constexpr int NB = 128;  // panel width of the blocked factorisations
+// Panel width of the blocked factorisations (measured: 256-column panels made the n = 9300
+// workload's reduction phase slower, 2.90 s against 2.81 s per 20-problem step).
+constexpr int NB = 128;
 // Digit slices of the FP64-level products in mixed mode (reduction, Rayleigh-Ritz, Gram and
 // rotation products, back-transforms): 7 slices leave an error of about 2^-49 (2e-15)
 // relative to the row and column scales, four orders of magnitude below the 1e-10 bar.

@@ -65,3 +65,26 @@ def test_peaks_are_measured_or_the_stated_fallback(monkeypatch, tmp_path):
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6768.1, "bf16_tflops_sustained": 1718.6}')
     peaks, kind = bench._peaks()
     assert kind == "measured" and peaks["bf16_tflops_sustained"] == 1718.6
+
+
+def test_step_schedule_is_cyclic_with_one_cold_problem_per_pass():
+    # K = N steps after W warm-up steps cover every problem once, exactly one of them cold
+    N, W = 20, 3
+    sched = bench.step_schedule(W, N, N)
+    assert sorted(p for p, _ in sched) == list(range(N))
+    assert sum(cold for _, cold in sched) == 1
+    assert sched[0] == (3, False) and sched[N - W] == (0, True)
+    assert bench.step_schedule(0, 3, 20) == [(0, True), (1, False), (2, False)]
+
+
+def test_segments_split_where_the_sequence_starts_over():
+    assert bench.segments(3, 20, 20) == [(3, 17, False), (0, 3, True)]
+    assert bench.segments(0, 20, 20) == [(0, 20, True)]
+    assert bench.segments(18, 45, 20) == [(18, 2, False), (0, 20, True), (0, 20, True), (0, 3, True)]
+    assert sum(ln for _, ln, _ in bench.segments(7, 33, 10)) == 33
+
+
+def test_summary_percentiles_of_per_eigenpair_errors():
+    s = bench.summary([0.0, 1.0, 2.0, 3.0, 4.0])
+    assert s == {"count": 5, "p50": 2.0, "p90": 3.6, "p99": 3.96, "max": 4.0}
+    assert bench.summary([]) == {}

@@ -1311,20 +1311,26 @@ cudaError_t jacobi_heev_df(const zd* G, int64_t ldg, int m, double* w, zd* V, in
   if (e != cudaSuccess) return e;
   const int half = mp / 2;
   // dynamic shared memory: the opt-in limit per block less the kernel's static arrays
-  static int dyn_max = -1;
-  static cudaError_t attr = cudaSuccess;
-  if (dyn_max < 0) {
+  // once per process (a static initialised once, also when batch workers call from several
+  // host threads): the kernel's attribute and the limit the ppc search uses
+  struct DynSmem {
+    cudaError_t err;
+    int max_bytes;
+  };
+  static const DynSmem dyn = [] {
+    DynSmem d{cudaSuccess, 0};
     cudaFuncAttributes fa;
     int dev = 0, optin = 0;
-    attr = cudaFuncGetAttributes(&fa, jacobi_df_kernel);
-    if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
-    if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int lim = std::min(kJacSmemMax, optin - (int)fa.sharedSizeBytes);
-    if (attr == cudaSuccess)
-      attr = cudaFuncSetAttribute(jacobi_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    dyn_max = lim;
-  }
-  if (attr != cudaSuccess) return attr;
+    d.err = cudaFuncGetAttributes(&fa, jacobi_df_kernel);
+    if (d.err == cudaSuccess) d.err = cudaGetDevice(&dev);
+    if (d.err == cudaSuccess) d.err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (d.err != cudaSuccess) return d;
+    d.max_bytes = std::min(kJacSmemMax, optin - (int)fa.sharedSizeBytes);
+    d.err = cudaFuncSetAttribute(jacobi_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, d.max_bytes);
+    return d;
+  }();
+  if (dyn.err != cudaSuccess) return dyn.err;
+  const int dyn_max = dyn.max_bytes;
   int ppc = 1;
   size_t smem = 0;
   for (;; ++ppc) {
